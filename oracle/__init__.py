@@ -1,0 +1,161 @@
+"""FP64 CPU oracle of the splatting renderer and the point estimators.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product package imports this
+module; only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py`` may call it.  It shares no code with the CUDA path; the only
+module both sides use is ``scenes`` (seeded inputs, no method arithmetic).
+
+What each function follows (paper sections of arXiv 2409.16504):
+
+* :func:`project`       -- Sec. 3.1, Eq. 3-4 (EWA projection, 3-sigma bound)
+* :func:`bin_keys`      -- Sec. 3.1 depth ordering, written as the
+  (tile | depth) key list and its stable sort
+* :func:`render`        -- Sec. 3.1, Eq. 1-2 (front-to-back alpha blending of
+  colour, normal and depth)
+* :mod:`oracle.grad`    -- exact derivative of :func:`render` (the
+  differentiable splatting of Sec. 1 and 3.3)
+* :mod:`oracle.estimate` -- kNN-PCA covariance estimate (the local
+  covariance prior of Sec. 2.1) and the per-point MLP reference
+* :mod:`oracle.raycast` -- exact ground-truth views of the analytic scenes
+  (replaces the mesh rasterisation of Sec. 3.3)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "p2e_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+DEFAULT_CFG = dict(tile=16, alpha_floor=1.0 / 255.0, alpha_max=0.99, t_min=1e-4,
+                   lowpass=0.3, sigma_mult=3.0, bg=(0.0, 0.0, 0.0))
+# Knife-edge flag half-widths (power at the 3-sigma boundary, alpha at the
+# floor, transmittance at the cutoff); pixels within them are reported, not
+# compared, because fp32 and fp64 may take the discrete decision differently.
+DEFAULT_FLAGS = dict(flag_power=1e-4, flag_alpha=1e-6, flag_t=1e-7)
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle (gcc, OpenMP, no FMA contraction)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", "-fno-fast-math", "-o", _LIB + ".tmp", _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            _lib.or_emit_keys.restype = C.c_int64
+            _lib.or_num_threads.restype = C.c_int
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def cam_floats(cam: dict) -> np.ndarray:
+    v = np.asarray(cam["viewmat"], np.float32).reshape(12)
+    return np.concatenate([v, np.array([cam["fx"], cam["fy"], cam["cx"], cam["cy"],
+                                        cam["near"]], np.float32)]).astype(np.float32)
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())
+
+
+def project(g: dict, cam: dict, cfg: dict | None = None) -> dict:
+    """R1-R4 for every Gaussian of ``g`` under camera ``cam`` (Eq. 3-4)."""
+    cfg = {**DEFAULT_CFG, **(cfg or {})}
+    n = len(g["mean"])
+    mean = np.ascontiguousarray(g["mean"], np.float32)
+    scale = np.ascontiguousarray(g["scale"], np.float32)
+    quat = np.ascontiguousarray(g["quat"], np.float32)
+    out = dict(
+        vis=np.zeros(n, np.uint8), xyz=np.zeros((n, 3)), uv=np.zeros((n, 2)),
+        cov2=np.zeros((n, 3)), conic=np.zeros((n, 3)), prect=np.zeros((n, 4), np.int32),
+        trect=np.zeros((n, 4), np.int32), ntiles=np.zeros(n, np.int32),
+        zkey=np.zeros(n, np.float32))
+    cf = cam_floats(cam)
+    lib().or_project(C.c_int64(n), _p(mean), _p(scale), _p(quat), _p(cf),
+                     C.c_int(cam["width"]), C.c_int(cam["height"]),
+                     C.c_double(cfg["lowpass"]), C.c_double(cfg["sigma_mult"]),
+                     C.c_int(cfg["tile"]), _p(out["vis"]), _p(out["xyz"]), _p(out["uv"]),
+                     _p(out["cov2"]), _p(out["conic"]), _p(out["prect"]), _p(out["trect"]),
+                     _p(out["ntiles"]), _p(out["zkey"]))
+    return out
+
+
+def tiles_of(cam: dict, tile: int):
+    tx = -(-cam["width"] // tile)
+    ty = -(-cam["height"] // tile)
+    return tx, ty
+
+
+def bin_keys(projs: list, cams: list, cfg: dict | None = None):
+    """R5: (tile | depth) keys of every view, stably sorted, and per-tile
+    ranges.  View v's tile ids start at the sum of the tile counts of views
+    before it.  Returns ``(keys u64[K], vals u32[K], ranges u32[tiles,2])``.
+    """
+    cfg = {**DEFAULT_CFG, **(cfg or {})}
+    tile = cfg["tile"]
+    K = int(sum(int(p["ntiles"].sum()) for p in projs))
+    keys = np.zeros(max(K, 1), np.uint64)
+    vals = np.zeros(max(K, 1), np.uint32)
+    base = 0
+    off = 0
+    for p, cam in zip(projs, cams):
+        tx, ty = tiles_of(cam, tile)
+        n = len(p["ntiles"])
+        off += lib().or_emit_keys(C.c_int64(n), _p(p["trect"]), _p(p["ntiles"]), _p(p["zkey"]),
+                                  C.c_int(tx), C.c_int64(base), _p(keys), _p(vals),
+                                  C.c_int64(off))
+        base += tx * ty
+    assert off == K
+    ranges = np.zeros((base, 2), np.uint32)
+    lib().or_sort_ranges(C.c_int64(K), _p(keys), _p(vals), C.c_int64(base), _p(ranges))
+    return keys[:K], vals[:K], ranges
+
+
+def render(g: dict, cam: dict, cfg: dict | None = None, brute: bool = False,
+           proj: dict | None = None, flags: dict | None = None) -> dict:
+    """R6-R7 (Eq. 1-2): the FP64 image of one view.
+
+    Returns dict with ``rgb (3,H,W)``, ``normal (3,H,W)``, ``depth (H,W)``,
+    ``alpha (H,W)`` (float64), ``ncontrib``, ``last`` (Gaussian index of the
+    last contributor, -1 if none) and ``flag`` (knife-edge pixels).
+    """
+    cfg = {**DEFAULT_CFG, **(cfg or {})}
+    fl = {**DEFAULT_FLAGS, **(flags or {})}
+    if proj is None:
+        proj = project(g, cam, cfg)
+    n = len(g["mean"])
+    W, H = cam["width"], cam["height"]
+    img = np.zeros((8, H, W))
+    ncontrib = np.zeros((H, W), np.int32)
+    last = np.zeros((H, W), np.int32)
+    flag = np.zeros((H, W), np.uint8)
+    params = np.array([cfg["alpha_floor"], cfg["alpha_max"], cfg["t_min"], cfg["sigma_mult"],
+                       *cfg["bg"], fl["flag_power"], fl["flag_alpha"], fl["flag_t"]], np.float64)
+    opac = np.ascontiguousarray(g["opacity"], np.float32)
+    rgb = np.ascontiguousarray(g["rgb"], np.float32)
+    nrm = np.ascontiguousarray(g["normal"], np.float32)
+    lib().or_render(C.c_int64(n), C.c_int(W), C.c_int(H), _p(proj["vis"]), _p(proj["xyz"]),
+                    _p(proj["uv"]), _p(proj["conic"]), _p(proj["prect"]), _p(proj["zkey"]),
+                    _p(opac), _p(rgb), _p(nrm), _p(params), C.c_int(1 if brute else 0),
+                    _p(img), _p(ncontrib), _p(last), _p(flag))
+    return dict(rgb=img[0:3], normal=img[3:6], depth=img[6], alpha=img[7],
+                ncontrib=ncontrib, last=last, flag=flag.astype(bool), proj=proj)
