@@ -1,0 +1,238 @@
+/*
+ * p2e.h -- C ABI of libp2e.so, the GB300 (sm_103a) splatting renderer and
+ * point-to-ellipsoid estimator of "Low Latency Point Cloud Rendering with
+ * Learned Splatting" (arXiv 2409.16504).
+ *
+ * Problem statement (Sec. 3.1): a coloured point cloud P = {(p_i, c_i)} and a
+ * viewpoint in; RGB, normal and depth images out.  Each point becomes a 3D
+ * Gaussian <G(p, Sigma), o, c, n> (Sec. 3.1, 3.2); the Gaussians are splatted
+ * with the EWA screen covariance (Eq. 3-4), bounded at three standard
+ * deviations, depth-ordered and alpha-composited front to back (Eq. 1-2).
+ *
+ * Conventions shared by every call
+ *   * Ownership: every pointer is caller-owned.  Pointers named *_dev or
+ *     documented as "device" are CUDA device memory; structs passed by
+ *     pointer (p2e_camera, p2e_config and the descriptor structs themselves)
+ *     live in host memory.  The library never allocates or frees device
+ *     memory and keeps no state between calls.
+ *   * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *     Every call only enqueues work on it and returns without synchronising,
+ *     except p2e_bins_check (documented below).
+ *   * Errors: arguments are validated on the host before anything is
+ *     enqueued; an invalid argument returns P2E_ERR_INVALID_ARG and enqueues
+ *     nothing.  A failed launch returns P2E_ERR_CUDA.  Key-capacity overflow
+ *     is detected on the device (see p2e_sort_bin) and reported by
+ *     p2e_bins_check.  No call traps, asserts or spins without bound on the
+ *     device: bounded waits record P2E_ERR_TIMEOUT in a device status word.
+ *   * Layout: per-Gaussian arrays are float4 structure-of-arrays (16-byte
+ *     aligned, coalesced 16-byte loads).  Images are planar fp32, views
+ *     concatenated in order; view v occupies H_v*W_v pixels per plane.
+ */
+#ifndef P2E_H
+#define P2E_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    P2E_OK = 0,
+    P2E_ERR_INVALID_ARG = 1,
+    P2E_ERR_CAPACITY = 2,
+    P2E_ERR_CUDA = 3,
+    P2E_ERR_TIMEOUT = 4,
+    P2E_ERR_UNSUPPORTED = 5
+} p2e_status;
+
+#define P2E_MAX_VIEWS 64
+
+/* Pinhole camera (Sec. 3.1, Eq. 3-4), host memory.
+ * viewmat: row-major 3x4 [T | t] mapping world to camera coordinates
+ * (OpenCV axes: x right, y down, z forward).  fx, fy, cx, cy in pixels;
+ * pixel (i, j) has its centre at (i + 0.5, j + 0.5).  Gaussians with camera
+ * depth z <= near_z are culled.  1 <= width, height <= 8192. */
+typedef struct {
+    float viewmat[12];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float near_z;
+} p2e_camera;
+
+/* Renderer constants (host memory).  The paper fixes none of them; the
+ * defaults (p2e_default_config) are those of the 3D Gaussian splatting
+ * renderer the paper follows (Sec. 3.1):
+ *   tile        8, 16 or 32 pixels (square screen tiles for binning)
+ *   alpha_floor splats with alpha < alpha_floor are skipped   (1/255)
+ *   alpha_max   alpha = min(alpha_max, o exp(power))           (0.99)
+ *   t_min       compositing stops before T would drop below    (1e-4)
+ *   lowpass     px^2 added to the screen covariance diagonal   (0.3)
+ *   sigma_mult  splat boundary in standard deviations (Sec. 3.1: 3)
+ *   bg          background colour composited with the final T  (0,0,0) */
+typedef struct {
+    int32_t tile;
+    float alpha_floor, alpha_max, t_min, lowpass, sigma_mult;
+    float bg[3];
+} p2e_config;
+
+/* Gaussian set, device memory, n entries each (Sec. 3.1, 11 parameters plus
+ * colour and normal):
+ *   mean_op  float4 (x, y, z, opacity o in [0,1])
+ *   scale    float4 (sx, sy, sz, unused), linear standard deviations > 0
+ *   quat     float4 (w, x, y, z), any non-zero quaternion (normalised
+ *            inside; the zero quaternion culls the Gaussian).
+ *            Sigma = R diag(s^2) R^T, R the rotation of the unit quaternion.
+ *   rgb      float4 (r, g, b, unused)
+ *   normal   float4 (nx, ny, nz, unused) */
+typedef struct {
+    const float *mean_op;
+    const float *scale;
+    const float *quat;
+    const float *rgb;
+    const float *normal;
+    int64_t n;
+} p2e_gaussians;
+
+/* Projected splats, device memory, n_views * n entries (view-major):
+ *   xy_depth float4 (u - floor(u), v - floor(v), depth key, bits of
+ *            int16 floor(u) | int16 floor(v) << 16); floor(u), floor(v)
+ *            are clamped to [-32768, 32767].
+ *   conic_op float4 (A, B, C, o): Sigma_s^{-1} = [[A, B], [B, C]]
+ *   rect     ushort4 (tx0, ty0, tx1, ty1): inclusive tile rectangle
+ *   ntiles   uint32 number of tiles touched (0 = culled) */
+typedef struct {
+    float *xy_depth;
+    float *conic_op;
+    uint16_t *rect;
+    uint32_t *ntiles;
+} p2e_projected;
+
+/* Binning buffers, device memory, caller-owned.
+ *   keys[2], vals[2]  double buffers of `capacity` entries each
+ *   ranges            uint2 per tile of all views: [start, end) into the
+ *                     sorted arrays; empty tiles hold [0, 0)
+ *   scratch           p2e_scratch_bytes(P2E_SCRATCH_SORT, n*n_views,
+ *                     capacity) bytes, 256-byte aligned
+ *   n_keys_dev        int64: number of keys the views need (may exceed
+ *                     capacity, in which case nothing past capacity is
+ *                     written and the sorted result is invalid)
+ *   status_dev        int32 device status word (P2E_OK, or P2E_ERR_TIMEOUT
+ *                     when a bounded device wait gave up)
+ *   result            written by p2e_sort_bin (host field): index (0 or 1)
+ *                     of the buffer pair that holds the sorted keys/vals */
+typedef struct {
+    uint64_t *keys[2];
+    uint32_t *vals[2];
+    uint32_t *ranges;
+    void *scratch;
+    int64_t scratch_bytes;
+    int64_t capacity;
+    int64_t *n_keys_dev;
+    int32_t *status_dev;
+    int32_t result;
+} p2e_bins;
+
+enum { P2E_SCRATCH_SORT = 0, P2E_SCRATCH_ESTIMATE = 1, P2E_SCRATCH_BACKWARD = 2 };
+
+/* Defaults of p2e_config (see above). */
+p2e_config p2e_default_config(void);
+
+/* Total tile count of the views for a tile size (sum over views of
+ * ceil(W/tile) * ceil(H/tile)). Returns -1 on invalid input. */
+int64_t p2e_total_tiles(const p2e_camera *cams, int32_t n_views, int32_t tile);
+
+/* Bytes of device scratch a call needs (`which` = P2E_SCRATCH_*; n = number
+ * of Gaussians (times views for SORT), capacity = key capacity). */
+size_t p2e_scratch_bytes(int32_t which, int64_t n, int64_t capacity);
+
+/* p2e_project -- EWA projection (Sec. 3.1, Eq. 3-4) and 3-sigma footprint.
+ * For every view v and Gaussian g: camera transform, near cull,
+ * Sigma = R diag(s^2) R^T, Sigma_s = J T Sigma T^T J^T + lowpass I, conic,
+ * screen centre, and the tile rectangle of the exact bounding box of the
+ * sigma_mult ellipse.  Integer results (cull, rectangle, depth key =
+ * fp32 of the double-precision camera depth) equal those of an IEEE double
+ * evaluation: an fp32 fast path carries an error bound and hands ambiguous
+ * Gaussians to a double-precision path.
+ * Writes out->* for n_views * g->n entries. */
+p2e_status p2e_project(const p2e_gaussians *g, const p2e_camera *cams, int32_t n_views,
+                       const p2e_config *cfg, p2e_projected *out, void *stream);
+
+/* p2e_sort_bin -- duplication into (tile id | depth) keys, device radix sort
+ * and per-tile ranges (Sec. 3.1: splats covering a pixel sorted by depth).
+ * key = ((tile_base_v + ty * ceil(W_v/tile) + tx) << 32) | bits(depth key),
+ * val = g, emitted in (view, Gaussian) order; the LSD radix sort is stable
+ * and sorts only the 32 + ceil(log2(total tiles)) significant bits, so equal
+ * keys keep ascending Gaussian order.  n = g->n used by p2e_project.
+ * Writes io->n_keys_dev, the sorted pair io->keys/vals[io->result] and
+ * io->ranges.  If the key count exceeds io->capacity nothing is written past
+ * it and p2e_bins_check reports P2E_ERR_CAPACITY. */
+p2e_status p2e_sort_bin(const p2e_projected *proj, int64_t n, const p2e_camera *cams,
+                        int32_t n_views, const p2e_config *cfg, p2e_bins *io, void *stream);
+
+/* p2e_bins_check -- synchronises `stream`, copies the key count to
+ * *n_keys_host and returns P2E_ERR_CAPACITY if it exceeded io->capacity,
+ * P2E_ERR_TIMEOUT if a device wait gave up, else P2E_OK. */
+p2e_status p2e_bins_check(const p2e_bins *io, int64_t *n_keys_host, void *stream);
+
+/* p2e_render -- front-to-back alpha compositing (Sec. 3.1, Eq. 1-2) of
+ * colour, and by substitution of n_k and z_k for c_k, of normal and depth.
+ * Per pixel over its tile's depth-sorted list: splats with
+ * power = -0.5 d^T Sigma_s^{-1} d < -sigma_mult^2/2 are outside the splat;
+ * alpha = min(alpha_max, o exp(power)); alpha < alpha_floor skipped;
+ * compositing stops before a splat with T (1 - alpha) < t_min.
+ * Outputs (device, planar fp32, views concatenated):
+ *   rgb[3][H][W] = C + T bg, normal[3][H][W], depth[H][W], alpha[H][W] =
+ *   1 - T, last[H][W] uint32 = one past the position, in the pixel's tile
+ *   list, of the last contributing splat (0 = none).  Any output pointer
+ *   may be NULL except `last` when a backward pass will follow. */
+p2e_status p2e_render(const p2e_gaussians *g, const p2e_projected *proj, const p2e_bins *bins,
+                      const p2e_camera *cams, int32_t n_views, const p2e_config *cfg,
+                      float *rgb, float *normal, float *depth, float *alpha, uint32_t *last,
+                      void *stream);
+
+/* p2e_render_backward -- exact gradient of p2e_render's outputs with
+ * respect to the Gaussian parameters (the differentiable splatting used to
+ * train the estimator, Sec. 1 and 3.3), with the discrete decisions (cull,
+ * rectangle, 3-sigma test, floor, stop) held fixed.  Per tile the
+ * transmittance is recomputed back to front from the stored alpha image and
+ * `last`; no per-pixel lists are stored.
+ * Inputs: the forward's arguments and outputs plus the upstream gradients
+ * d_rgb[3][H][W], d_normal[3][H][W], d_depth[H][W], d_alpha[H][W] (any may
+ * be NULL = zero).  Outputs (device, written, not accumulated; n entries):
+ * d_mean[3n], d_scale[3n], d_quat[4n] (w.r.t. the raw quaternion),
+ * d_opacity[n], d_rgb_g[3n], d_normal_g[3n].  scratch: p2e_scratch_bytes(
+ * P2E_SCRATCH_BACKWARD, n * n_views, 0) bytes. */
+p2e_status p2e_render_backward(const p2e_gaussians *g, const p2e_projected *proj,
+                               const p2e_bins *bins, const p2e_camera *cams, int32_t n_views,
+                               const p2e_config *cfg, const float *alpha, const uint32_t *last,
+                               const float *d_rgb, const float *d_normal, const float *d_depth,
+                               const float *d_alpha, float *d_mean, float *d_scale, float *d_quat,
+                               float *d_opacity, float *d_rgb_g, float *d_normal_g,
+                               void *scratch, int64_t scratch_bytes, void *stream);
+
+/* p2e_estimate -- per-point ellipsoid estimation (Sec. 3.2 role: point cloud
+ * in, <G(p, Sigma), o, n> out).  xyz, rgb: device float4[n] (w unused).
+ * mode 0: closed-form kNN-PCA (k = 16 nearest neighbours, the local
+ *   covariance prior of Sec. 2.1): Sigma from the neighbours' covariance,
+ *   normal = smallest principal axis, opacity = pca_opacity.
+ * mode 1: the learned per-point MLP (16 x (offset, colour) -> 64 -> 64 -> 64
+ *   -> 8, bf16 weights, fp32 accumulation on tcgen05 tensor cores) predicting
+ *   corrections of the PCA frame, scale, rotation and opacity.
+ * mlp_weights: device blob from p2e_mlp_blob_bytes layout (mode 1), else
+ * NULL.  out: device Gaussian set (mean_op, scale, quat, rgb, normal) of n
+ * entries (the const qualifiers of p2e_gaussians are cast away for output).
+ * knn_idx (optional, may be NULL): device uint32[n*16] neighbour indices.
+ * scratch: p2e_scratch_bytes(P2E_SCRATCH_ESTIMATE, n, 0) bytes. */
+p2e_status p2e_estimate(const float *xyz, const float *rgb, int64_t n, int32_t mode,
+                        const void *mlp_weights, float pca_opacity, p2e_gaussians *out,
+                        uint32_t *knn_idx, void *scratch, int64_t scratch_bytes, void *stream);
+
+/* Human-readable name of a status code (static storage). */
+const char *p2e_status_string(p2e_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* P2E_H */

@@ -34,8 +34,11 @@ _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-DEFAULT_CFG = dict(tile=16, alpha_floor=1.0 / 255.0, alpha_max=0.99, t_min=1e-4,
-                   lowpass=0.3, sigma_mult=3.0, bg=(0.0, 0.0, 0.0))
+# Renderer constants are fp32 in the C ABI; the defaults are held at their
+# fp32 values so that every consumer sees the same numbers.
+DEFAULT_CFG = dict(tile=16, alpha_floor=float(np.float32(1.0 / 255.0)),
+                   alpha_max=float(np.float32(0.99)), t_min=float(np.float32(1e-4)),
+                   lowpass=float(np.float32(0.3)), sigma_mult=3.0, bg=(0.0, 0.0, 0.0))
 # Knife-edge flag half-widths (power at the 3-sigma boundary, alpha at the
 # floor, transmittance at the cutoff); pixels within them are reported, not
 # compared, because fp32 and fp64 may take the discrete decision differently.
@@ -61,6 +64,11 @@ def lib():
             _lib.or_emit_keys.restype = C.c_int64
             _lib.or_num_threads.restype = C.c_int
     return _lib
+
+
+def _f32(x) -> float:
+    """Renderer constants are fp32 inputs; the oracle widens them exactly."""
+    return float(np.float32(x))
 
 
 def _p(a):
@@ -92,7 +100,7 @@ def project(g: dict, cam: dict, cfg: dict | None = None) -> dict:
     cf = cam_floats(cam)
     lib().or_project(C.c_int64(n), _p(mean), _p(scale), _p(quat), _p(cf),
                      C.c_int(cam["width"]), C.c_int(cam["height"]),
-                     C.c_double(cfg["lowpass"]), C.c_double(cfg["sigma_mult"]),
+                     C.c_double(_f32(cfg["lowpass"])), C.c_double(_f32(cfg["sigma_mult"])),
                      C.c_int(cfg["tile"]), _p(out["vis"]), _p(out["xyz"]), _p(out["uv"]),
                      _p(out["cov2"]), _p(out["conic"]), _p(out["prect"]), _p(out["trect"]),
                      _p(out["ntiles"]), _p(out["zkey"]))
@@ -148,8 +156,9 @@ def render(g: dict, cam: dict, cfg: dict | None = None, brute: bool = False,
     ncontrib = np.zeros((H, W), np.int32)
     last = np.zeros((H, W), np.int32)
     flag = np.zeros((H, W), np.uint8)
-    params = np.array([cfg["alpha_floor"], cfg["alpha_max"], cfg["t_min"], cfg["sigma_mult"],
-                       *cfg["bg"], fl["flag_power"], fl["flag_alpha"], fl["flag_t"]], np.float64)
+    params = np.array([_f32(cfg["alpha_floor"]), _f32(cfg["alpha_max"]), _f32(cfg["t_min"]),
+                       _f32(cfg["sigma_mult"]), *[_f32(b) for b in cfg["bg"]],
+                       fl["flag_power"], fl["flag_alpha"], fl["flag_t"]], np.float64)
     opac = np.ascontiguousarray(g["opacity"], np.float32)
     rgb = np.ascontiguousarray(g["rgb"], np.float32)
     nrm = np.ascontiguousarray(g["normal"], np.float32)

@@ -1,0 +1,111 @@
+"""ctypes loader of libp2e.so and the C structs of include/p2e.h.
+
+The library is built in-tree (``paper_2409_16504_gb300/_build/libp2e.so``)
+by :func:`paper_2409_16504_gb300.build.build`.  There is no fallback: if the
+library cannot be loaded, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+P2E_OK, P2E_ERR_INVALID_ARG, P2E_ERR_CAPACITY, P2E_ERR_CUDA, P2E_ERR_TIMEOUT, P2E_ERR_UNSUPPORTED = range(6)
+P2E_MAX_VIEWS = 64
+P2E_SCRATCH_SORT, P2E_SCRATCH_ESTIMATE, P2E_SCRATCH_BACKWARD = 0, 1, 2
+
+# every symbol include/p2e.h declares
+EXPORTS = ("p2e_default_config", "p2e_total_tiles", "p2e_scratch_bytes", "p2e_project",
+           "p2e_sort_bin", "p2e_bins_check", "p2e_render", "p2e_render_backward", "p2e_estimate",
+           "p2e_status_string")
+
+
+class P2ECamera(C.Structure):
+    _fields_ = [("viewmat", C.c_float * 12), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("near_z", C.c_float)]
+
+
+class P2EConfig(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("alpha_floor", C.c_float), ("alpha_max", C.c_float),
+                ("t_min", C.c_float), ("lowpass", C.c_float), ("sigma_mult", C.c_float),
+                ("bg", C.c_float * 3)]
+
+
+class P2EGaussians(C.Structure):
+    _fields_ = [("mean_op", C.c_void_p), ("scale", C.c_void_p), ("quat", C.c_void_p),
+                ("rgb", C.c_void_p), ("normal", C.c_void_p), ("n", C.c_int64)]
+
+
+class P2EProjected(C.Structure):
+    _fields_ = [("xy_depth", C.c_void_p), ("conic_op", C.c_void_p), ("rect", C.c_void_p),
+                ("ntiles", C.c_void_p)]
+
+
+class P2EBins(C.Structure):
+    _fields_ = [("keys", C.c_void_p * 2), ("vals", C.c_void_p * 2), ("ranges", C.c_void_p),
+                ("scratch", C.c_void_p), ("scratch_bytes", C.c_int64), ("capacity", C.c_int64),
+                ("n_keys_dev", C.c_void_p), ("status_dev", C.c_void_p), ("result", C.c_int32)]
+
+
+class P2EError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        super().__init__(f"{fn}: {status_string(status)} (status {status})")
+
+
+def load(path: str | None = None):
+    """Load (building first if needed) libp2e.so."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib_path = path or _build.LIB
+        if not os.path.exists(lib_path):
+            _build.build()
+        lib = C.CDLL(lib_path)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        lib.p2e_default_config.restype = P2EConfig
+        lib.p2e_default_config.argtypes = []
+        lib.p2e_total_tiles.restype = i64
+        lib.p2e_total_tiles.argtypes = [C.POINTER(P2ECamera), i32, i32]
+        lib.p2e_scratch_bytes.restype = C.c_size_t
+        lib.p2e_scratch_bytes.argtypes = [i32, i64, i64]
+        lib.p2e_status_string.restype = C.c_char_p
+        lib.p2e_status_string.argtypes = [C.c_int]
+        lib.p2e_project.restype = C.c_int
+        lib.p2e_project.argtypes = [C.POINTER(P2EGaussians), C.POINTER(P2ECamera), i32,
+                                    C.POINTER(P2EConfig), C.POINTER(P2EProjected), vp]
+        lib.p2e_sort_bin.restype = C.c_int
+        lib.p2e_sort_bin.argtypes = [C.POINTER(P2EProjected), i64, C.POINTER(P2ECamera), i32,
+                                     C.POINTER(P2EConfig), C.POINTER(P2EBins), vp]
+        lib.p2e_bins_check.restype = C.c_int
+        lib.p2e_bins_check.argtypes = [C.POINTER(P2EBins), C.POINTER(C.c_int64), vp]
+        lib.p2e_render.restype = C.c_int
+        lib.p2e_render.argtypes = [C.POINTER(P2EGaussians), C.POINTER(P2EProjected),
+                                   C.POINTER(P2EBins), C.POINTER(P2ECamera), i32,
+                                   C.POINTER(P2EConfig), vp, vp, vp, vp, vp, vp]
+        lib.p2e_render_backward.restype = C.c_int
+        lib.p2e_render_backward.argtypes = [C.POINTER(P2EGaussians), C.POINTER(P2EProjected),
+                                            C.POINTER(P2EBins), C.POINTER(P2ECamera), i32,
+                                            C.POINTER(P2EConfig), vp, vp, vp, vp, vp, vp,
+                                            vp, vp, vp, vp, vp, vp, vp, i64, vp]
+        lib.p2e_estimate.restype = C.c_int
+        lib.p2e_estimate.argtypes = [vp, vp, i64, i32, vp, C.c_float, C.POINTER(P2EGaussians),
+                                     vp, vp, i64, vp]
+        _lib = lib
+        return lib
+
+
+def status_string(s: int) -> str:
+    return load().p2e_status_string(int(s)).decode()
+
+
+def check(fn: str, status: int):
+    if status != P2E_OK:
+        raise P2EError(fn, status)

@@ -1,0 +1,261 @@
+// C ABI of libp2e: host-side validation, per-view constants and launches.
+// Declarations and the contract of every entry point are in include/p2e.h.
+#include <math.h>
+#include <string.h>
+
+#include "common.cuh"
+
+namespace p2e {
+cudaError_t launch_project(const p2e_gaussians *g, const Views &P, p2e_projected *out, cudaStream_t st);
+cudaError_t launch_sort_bin(const p2e_projected *proj, const Views &P, p2e_bins *io, int num_sms,
+                            cudaStream_t st);
+cudaError_t launch_render(const p2e_gaussians *g, const p2e_projected *proj, const p2e_bins *bins,
+                          const Views &P, float *rgb, float *nrm, float *depth, float *alpha,
+                          uint32_t *last, cudaStream_t st);
+size_t sort_scratch_bytes(int64_t n_total, int64_t capacity);
+int sort_passes(int64_t total_tiles);
+size_t backward_scratch_bytes(int64_t n_total);
+size_t estimate_scratch_bytes(int64_t n);
+cudaError_t launch_render_backward(const p2e_gaussians *g, const p2e_projected *proj,
+                                   const p2e_bins *bins, const Views &P, const float *alpha,
+                                   const uint32_t *last, const float *d_rgb, const float *d_normal,
+                                   const float *d_depth, const float *d_alpha, float *d_mean,
+                                   float *d_scale, float *d_quat, float *d_opacity, float *d_rgb_g,
+                                   float *d_normal_g, void *scratch, cudaStream_t st);
+cudaError_t launch_estimate(const float *xyz, const float *rgb, int64_t n, int32_t mode,
+                            const void *mlp, float pca_opacity, p2e_gaussians *out,
+                            uint32_t *knn_idx, void *scratch, int num_sms, cudaStream_t st);
+
+int device_sms() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+    if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+    if (dev >= 0 && dev < 64) cache[dev] = sms;
+    return sms;
+}
+}  // namespace p2e
+
+using namespace p2e;
+
+static bool fin(float x) { return isfinite(x) != 0; }
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+static p2e_status fill_views(const p2e_camera *cams, int32_t n_views, const p2e_config *cfg,
+                             int64_t n, Views &P) {
+    if (!cams || !cfg || n_views < 1 || n_views > P2E_MAX_VIEWS || n < 0) return P2E_ERR_INVALID_ARG;
+    if (!(cfg->tile == 8 || cfg->tile == 16 || cfg->tile == 32)) return P2E_ERR_INVALID_ARG;
+    if (!fin(cfg->alpha_floor) || !fin(cfg->alpha_max) || !fin(cfg->t_min) || !fin(cfg->lowpass) ||
+        !fin(cfg->sigma_mult) || cfg->lowpass < 0.f || !(cfg->sigma_mult > 0.f) ||
+        cfg->alpha_floor < 0.f || !(cfg->alpha_max > 0.f) || cfg->alpha_max > 1.f ||
+        cfg->t_min < 0.f || !(cfg->t_min < 1.f))
+        return P2E_ERR_INVALID_ARG;
+    for (int c = 0; c < 3; ++c)
+        if (!fin(cfg->bg[c])) return P2E_ERR_INVALID_ARG;
+    memset(&P, 0, sizeof(P));
+    P.n_views = n_views;
+    P.tile = cfg->tile;
+    P.lowpass = cfg->lowpass;
+    P.sigma_mult = cfg->sigma_mult;
+    P.alpha_floor = cfg->alpha_floor;
+    P.alpha_max = cfg->alpha_max;
+    P.t_min = cfg->t_min;
+    for (int c = 0; c < 3; ++c) P.bg[c] = cfg->bg[c];
+    P.n = n;
+    int64_t tb = 0, pb = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const p2e_camera &c = cams[v];
+        if (c.width < 1 || c.height < 1 || c.width > 8192 || c.height > 8192) return P2E_ERR_INVALID_ARG;
+        for (int i = 0; i < 12; ++i)
+            if (!fin(c.viewmat[i])) return P2E_ERR_INVALID_ARG;
+        if (!fin(c.fx) || !fin(c.fy) || !fin(c.cx) || !fin(c.cy) || !fin(c.near_z) || c.near_z < 0.f)
+            return P2E_ERR_INVALID_ARG;
+        View &V = P.v[v];
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) V.T[3 * i + j] = c.viewmat[4 * i + j];
+            V.t[i] = c.viewmat[4 * i + 3];
+        }
+        V.fx = c.fx; V.fy = c.fy; V.cx = c.cx; V.cy = c.cy; V.near_z = c.near_z;
+        V.W = c.width; V.H = c.height;
+        V.tiles_x = (c.width + cfg->tile - 1) / cfg->tile;
+        V.tiles_y = (c.height + cfg->tile - 1) / cfg->tile;
+        V.tile_base = tb;
+        V.pix_base = pb;
+        tb += (int64_t)V.tiles_x * V.tiles_y;
+        pb += (int64_t)c.width * c.height;
+    }
+    P.total_tiles = tb;
+    if (tb >= (int64_t(1) << 31)) return P2E_ERR_INVALID_ARG;
+    return P2E_OK;
+}
+
+static p2e_status check_gaussians(const p2e_gaussians *g) {
+    if (!g || g->n < 0 || g->n >= (int64_t(1) << 31)) return P2E_ERR_INVALID_ARG;
+    if (g->n == 0) return P2E_OK;
+    const void *ps[5] = {g->mean_op, g->scale, g->quat, g->rgb, g->normal};
+    for (int i = 0; i < 5; ++i)
+        if (!ps[i] || !aligned16(ps[i])) return P2E_ERR_INVALID_ARG;
+    return P2E_OK;
+}
+
+static p2e_status check_proj(const p2e_projected *p) {
+    if (!p || !p->xy_depth || !p->conic_op || !p->rect || !p->ntiles) return P2E_ERR_INVALID_ARG;
+    if (!aligned16(p->xy_depth) || !aligned16(p->conic_op) || ((uintptr_t)p->rect & 7u) ||
+        ((uintptr_t)p->ntiles & 3u))
+        return P2E_ERR_INVALID_ARG;
+    return P2E_OK;
+}
+
+extern "C" {
+
+p2e_config p2e_default_config(void) {
+    p2e_config c;
+    c.tile = 16;
+    c.alpha_floor = 1.0f / 255.0f;
+    c.alpha_max = 0.99f;
+    c.t_min = 1e-4f;
+    c.lowpass = 0.3f;
+    c.sigma_mult = 3.0f;
+    c.bg[0] = c.bg[1] = c.bg[2] = 0.0f;
+    return c;
+}
+
+int64_t p2e_total_tiles(const p2e_camera *cams, int32_t n_views, int32_t tile) {
+    p2e_config c = p2e_default_config();
+    c.tile = tile;
+    Views P;
+    if (fill_views(cams, n_views, &c, 0, P) != P2E_OK) return -1;
+    return P.total_tiles;
+}
+
+size_t p2e_scratch_bytes(int32_t which, int64_t n, int64_t capacity) {
+    if (n < 0 || capacity < 0) return 0;
+    switch (which) {
+        case P2E_SCRATCH_SORT: return sort_scratch_bytes(n, capacity);
+        case P2E_SCRATCH_ESTIMATE: return estimate_scratch_bytes(n);
+        case P2E_SCRATCH_BACKWARD: return backward_scratch_bytes(n);
+        default: return 0;
+    }
+}
+
+const char *p2e_status_string(p2e_status s) {
+    switch (s) {
+        case P2E_OK: return "ok";
+        case P2E_ERR_INVALID_ARG: return "invalid argument";
+        case P2E_ERR_CAPACITY: return "key capacity exceeded";
+        case P2E_ERR_CUDA: return "CUDA error";
+        case P2E_ERR_TIMEOUT: return "device wait timed out";
+        case P2E_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+p2e_status p2e_project(const p2e_gaussians *g, const p2e_camera *cams, int32_t n_views,
+                       const p2e_config *cfg, p2e_projected *out, void *stream) {
+    p2e_status s = check_gaussians(g);
+    if (s != P2E_OK) return s;
+    Views P;
+    if ((s = fill_views(cams, n_views, cfg, g->n, P)) != P2E_OK) return s;
+    if (g->n > 0 && (s = check_proj(out)) != P2E_OK) return s;
+    return launch_project(g, P, out, (cudaStream_t)stream) == cudaSuccess ? P2E_OK : P2E_ERR_CUDA;
+}
+
+p2e_status p2e_sort_bin(const p2e_projected *proj, int64_t n, const p2e_camera *cams, int32_t n_views,
+                        const p2e_config *cfg, p2e_bins *io, void *stream) {
+    Views P;
+    p2e_status s = fill_views(cams, n_views, cfg, n, P);
+    if (s != P2E_OK) return s;
+    if (n < 0 || n >= (int64_t(1) << 31) || !io) return P2E_ERR_INVALID_ARG;
+    if (n > 0 && (s = check_proj(proj)) != P2E_OK) return s;
+    if (io->capacity < 0 || io->capacity >= (int64_t(1) << 30)) return P2E_ERR_INVALID_ARG;
+    if (!io->ranges || !io->n_keys_dev || !io->status_dev || !io->scratch) return P2E_ERR_INVALID_ARG;
+    if (io->capacity > 0 && (!io->keys[0] || !io->keys[1] || !io->vals[0] || !io->vals[1]))
+        return P2E_ERR_INVALID_ARG;
+    if (((uintptr_t)io->scratch & 255u) || ((uintptr_t)io->ranges & 7u)) return P2E_ERR_INVALID_ARG;
+    if (io->scratch_bytes < (int64_t)sort_scratch_bytes(n * n_views, io->capacity))
+        return P2E_ERR_INVALID_ARG;
+    if (sort_passes(P.total_tiles) > 8) return P2E_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(io->status_dev, 0, sizeof(int32_t), st) != cudaSuccess) return P2E_ERR_CUDA;
+    return launch_sort_bin(proj, P, io, device_sms(), st) == cudaSuccess ? P2E_OK : P2E_ERR_CUDA;
+}
+
+p2e_status p2e_bins_check(const p2e_bins *io, int64_t *n_keys_host, void *stream) {
+    if (!io || !io->n_keys_dev || !io->status_dev) return P2E_ERR_INVALID_ARG;
+    int64_t k = 0;
+    int32_t st = 0;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return P2E_ERR_CUDA;
+    if (cudaMemcpy(&k, io->n_keys_dev, sizeof k, cudaMemcpyDeviceToHost) != cudaSuccess) return P2E_ERR_CUDA;
+    if (cudaMemcpy(&st, io->status_dev, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess) return P2E_ERR_CUDA;
+    if (n_keys_host) *n_keys_host = k;
+    if (st != 0) return (p2e_status)st;
+    return k > io->capacity ? P2E_ERR_CAPACITY : P2E_OK;
+}
+
+p2e_status p2e_render(const p2e_gaussians *g, const p2e_projected *proj, const p2e_bins *bins,
+                      const p2e_camera *cams, int32_t n_views, const p2e_config *cfg, float *rgb,
+                      float *normal, float *depth, float *alpha, uint32_t *last, void *stream) {
+    p2e_status s = check_gaussians(g);
+    if (s != P2E_OK) return s;
+    Views P;
+    if ((s = fill_views(cams, n_views, cfg, g->n, P)) != P2E_OK) return s;
+    if (g->n > 0 && (s = check_proj(proj)) != P2E_OK) return s;
+    if (!bins || !bins->ranges || (bins->result != 0 && bins->result != 1)) return P2E_ERR_INVALID_ARG;
+    if (bins->capacity > 0 && !bins->vals[bins->result]) return P2E_ERR_INVALID_ARG;
+    return launch_render(g, proj, bins, P, rgb, normal, depth, alpha, last, (cudaStream_t)stream) ==
+                   cudaSuccess
+               ? P2E_OK
+               : P2E_ERR_CUDA;
+}
+
+p2e_status p2e_render_backward(const p2e_gaussians *g, const p2e_projected *proj,
+                               const p2e_bins *bins, const p2e_camera *cams, int32_t n_views,
+                               const p2e_config *cfg, const float *alpha, const uint32_t *last,
+                               const float *d_rgb, const float *d_normal, const float *d_depth,
+                               const float *d_alpha, float *d_mean, float *d_scale, float *d_quat,
+                               float *d_opacity, float *d_rgb_g, float *d_normal_g, void *scratch,
+                               int64_t scratch_bytes, void *stream) {
+    p2e_status s = check_gaussians(g);
+    if (s != P2E_OK) return s;
+    Views P;
+    if ((s = fill_views(cams, n_views, cfg, g->n, P)) != P2E_OK) return s;
+    if (g->n > 0 && (s = check_proj(proj)) != P2E_OK) return s;
+    if (!bins || !bins->ranges || (bins->result != 0 && bins->result != 1)) return P2E_ERR_INVALID_ARG;
+    if (!alpha || !last) return P2E_ERR_INVALID_ARG;
+    if (g->n > 0 && (!d_mean || !d_scale || !d_quat || !d_opacity || !d_rgb_g || !d_normal_g))
+        return P2E_ERR_INVALID_ARG;
+    if (scratch_bytes < (int64_t)backward_scratch_bytes(g->n * n_views) ||
+        (scratch_bytes > 0 && (!scratch || ((uintptr_t)scratch & 255u))))
+        return P2E_ERR_INVALID_ARG;
+    return launch_render_backward(g, proj, bins, P, alpha, last, d_rgb, d_normal, d_depth, d_alpha,
+                                  d_mean, d_scale, d_quat, d_opacity, d_rgb_g, d_normal_g, scratch,
+                                  (cudaStream_t)stream) == cudaSuccess
+               ? P2E_OK
+               : P2E_ERR_CUDA;
+}
+
+p2e_status p2e_estimate(const float *xyz, const float *rgb, int64_t n, int32_t mode,
+                        const void *mlp_weights, float pca_opacity, p2e_gaussians *out,
+                        uint32_t *knn_idx, void *scratch, int64_t scratch_bytes, void *stream) {
+    if (n < 0 || n >= (int64_t(1) << 31) || !out || (mode != 0 && mode != 1)) return P2E_ERR_INVALID_ARG;
+    if (!fin(pca_opacity) || pca_opacity < 0.f || pca_opacity > 1.f) return P2E_ERR_INVALID_ARG;
+    if (mode == 1 && !mlp_weights) return P2E_ERR_INVALID_ARG;
+    if (n == 0) return P2E_OK;
+    if (n < 17) return P2E_ERR_INVALID_ARG;  // 16 neighbours need 17 points
+    if (!xyz || !rgb || !aligned16(xyz) || !aligned16(rgb)) return P2E_ERR_INVALID_ARG;
+    if (!out->mean_op || !out->scale || !out->quat || !out->rgb || !out->normal) return P2E_ERR_INVALID_ARG;
+    if (!aligned16(out->mean_op) || !aligned16(out->scale) || !aligned16(out->quat) ||
+        !aligned16(out->rgb) || !aligned16(out->normal))
+        return P2E_ERR_INVALID_ARG;
+    if (scratch_bytes < (int64_t)estimate_scratch_bytes(n) || !scratch || ((uintptr_t)scratch & 255u))
+        return P2E_ERR_INVALID_ARG;
+    cudaError_t e = launch_estimate(xyz, rgb, n, mode, mlp_weights, pca_opacity, out, knn_idx, scratch,
+                                    device_sms(), (cudaStream_t)stream);
+    if (e == cudaErrorNotSupported) return P2E_ERR_UNSUPPORTED;
+    return e == cudaSuccess ? P2E_OK : P2E_ERR_CUDA;
+}
+
+}  // extern "C"

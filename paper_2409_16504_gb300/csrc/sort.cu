@@ -1,0 +1,404 @@
+// K2-K5: duplication into (tile id | depth) keys, LSD radix sort, tile
+// ranges.  Depth ordering of the splats that cover a pixel (Sec. 3.1) is
+// realised per screen tile: keys are ((tile id) << 32 | fp32 depth bits), so
+// one stable sort on the significant bits orders every tile's list by
+// depth, ties by Gaussian index (keys are emitted in index order).
+//
+// K2+K3  scan_emit:  single-pass exclusive scan of the per-Gaussian tile
+//        counts (decoupled look-back) fused with key emission.
+// K4     radix sort: a global digit histogram pass, then one kernel per
+//        8-bit digit: stable warp-level multisplit ranking in shared memory,
+//        decoupled look-back across tiles for the digit offsets, and a
+//        shared-memory staged scatter so that writes are runs of equal digit.
+// K5     tile_ranges: [start, end) of every tile in the sorted keys.
+//
+// All device waits are bounded (kSpinLimit); a wait that gives up writes
+// P2E_ERR_TIMEOUT to the status word and the kernel finishes without
+// further waiting.
+#include "common.cuh"
+
+namespace p2e {
+
+// ---------------------------------------------------------------------------
+// scratch layout (see sort_scratch_bytes)
+// ---------------------------------------------------------------------------
+constexpr int kScanItems = 4;
+constexpr int kScanThreads = 256;
+constexpr int kScanTile = kScanItems * kScanThreads;
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kRadix = 256;
+constexpr int kMaxPasses = 8;
+
+struct SortScratch {
+    uint32_t *hist;        // [kMaxPasses][256] digit totals
+    uint32_t *tickets;     // [16]: [0] scan, [1 + p] sort pass p
+    uint64_t *scan_state;  // [scan tiles] look-back words (flag << 62 | value)
+    uint32_t *sort_state;  // [kMaxPasses][sort tiles][256] (flag << 30 | count)
+    int64_t scan_tiles, sort_tiles;
+};
+
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t sort_scratch_bytes(int64_t n_total, int64_t capacity) {
+    const int64_t st = (n_total + kScanTile - 1) / kScanTile;
+    const int64_t kt = (capacity + kSortTile - 1) / kSortTile;
+    return align256(kMaxPasses * kRadix * 4) + align256(16 * 4) + align256((size_t)(st + 1) * 8) +
+           align256((size_t)kMaxPasses * (size_t)(kt + 1) * kRadix * 4);
+}
+
+static SortScratch carve(void *base, int64_t n_total, int64_t capacity) {
+    SortScratch s;
+    char *p = (char *)base;
+    s.scan_tiles = (n_total + kScanTile - 1) / kScanTile;
+    s.sort_tiles = (capacity + kSortTile - 1) / kSortTile;
+    s.hist = (uint32_t *)p;
+    p += align256(kMaxPasses * kRadix * 4);
+    s.tickets = (uint32_t *)p;
+    p += align256(16 * 4);
+    s.scan_state = (uint64_t *)p;
+    p += align256((size_t)(s.scan_tiles + 1) * 8);
+    s.sort_state = (uint32_t *)p;
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// K2+K3: scan of tile counts fused with key emission
+// ---------------------------------------------------------------------------
+constexpr uint64_t kFlagAgg = 1ull << 62, kFlagPre = 2ull << 62, kValMask = (1ull << 62) - 1;
+
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(uint64_t *p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Block-wide exclusive sum of one value per thread (256 threads).
+template <int NT>
+__device__ __forceinline__ uint64_t block_excl_sum(uint64_t v, uint64_t &total, uint64_t *sm /*NT/32*/) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sm[wid] = x;
+    __syncthreads();
+    uint64_t wpre = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) {
+        const uint64_t s = sm[w];
+        if (w < wid) wpre += s;
+        tot += s;
+    }
+    __syncthreads();
+    total = tot;
+    return wpre + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_emit_kernel(
+    const uint32_t *__restrict__ ntiles, const ushort4 *__restrict__ rect,
+    const float4 *__restrict__ xy_depth, int64_t n_total, uint64_t *__restrict__ keys,
+    uint32_t *__restrict__ vals, int64_t capacity, SortScratch S, int64_t *n_keys_dev,
+    int32_t *status, __grid_constant__ const Views P) {
+    __shared__ uint64_t sm[kScanThreads / 32];
+    __shared__ uint32_t s_tile;
+    __shared__ uint64_t s_prefix;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&S.tickets[0], 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t cnt[kScanItems];
+    uint64_t local = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t e = base + i;
+        cnt[i] = e < n_total ? __ldg(ntiles + e) : 0u;
+        local += cnt[i];
+    }
+    uint64_t total;
+    const uint64_t texcl = block_excl_sum<kScanThreads>(local, total, sm);
+    // decoupled look-back (one thread; tiles usually find their predecessor's
+    // inclusive prefix immediately)
+    if (threadIdx.x == 0) {
+        uint64_t prefix = 0;
+        if (tile == 0) {
+            st_release_u64(&S.scan_state[0], kFlagPre | total);
+        } else {
+            st_release_u64(&S.scan_state[tile], kFlagAgg | total);
+            int64_t p = tile - 1;
+            uint32_t spins = 0;
+            while (p >= 0) {
+                const uint64_t w = ld_acquire_u64(&S.scan_state[p]);
+                if ((w >> 62) == 0) {
+                    if (++spins > kSpinLimit) { atomicExch(status, (int32_t)P2E_ERR_TIMEOUT); break; }
+                    backoff(spins);
+                    continue;
+                }
+                prefix += w & kValMask;
+                if ((w >> 62) == 2) break;
+                --p;
+            }
+            st_release_u64(&S.scan_state[tile], kFlagPre | (prefix + total));
+        }
+        s_prefix = prefix;
+        if (tile == S.scan_tiles - 1) *n_keys_dev = (int64_t)(prefix + total);
+    }
+    __syncthreads();
+    uint64_t off = s_prefix + texcl;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t e = base + i;
+        if (cnt[i] != 0u) {
+            const int vi = (int)(e / P.n);
+            const View &V = P.v[vi];
+            const int64_t g = e - (int64_t)vi * P.n;
+            const ushort4 r = __ldg(rect + e);
+            const uint32_t zb = __float_as_uint(__ldg(&xy_depth[e].z));
+            uint64_t o = off;
+            for (int ty = r.y; ty <= r.w; ++ty) {
+                const int64_t rowid = V.tile_base + (int64_t)ty * V.tiles_x;
+                for (int tx = r.x; tx <= r.z; ++tx, ++o) {
+                    if ((int64_t)o < capacity) {
+                        keys[o] = ((uint64_t)(rowid + tx) << 32) | zb;
+                        vals[o] = (uint32_t)g;
+                    }
+                }
+            }
+        }
+        off += cnt[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K4: radix sort
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t sort_count(const int64_t *n_keys_dev, int64_t capacity) {
+    const int64_t k = *n_keys_dev;
+    return k < capacity ? k : capacity;
+}
+
+__global__ void __launch_bounds__(256) digit_hist_kernel(const uint64_t *__restrict__ keys,
+                                                         const int64_t *n_keys_dev, int64_t capacity,
+                                                         int passes, uint32_t *__restrict__ hist) {
+    __shared__ uint32_t sh[kMaxPasses * kRadix];
+    for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const int64_t K = sort_count(n_keys_dev, capacity);
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < K; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < K;
+        const uint64_t k = valid ? keys[i] : 0ull;
+        for (int p = 0; p < passes; ++p) {
+            const uint32_t d = valid ? (uint32_t)(k >> (8 * p)) & 255u : 256u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (valid && lane == 31 - __clz(peers)) atomicAdd(&sh[p * kRadix + d], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+constexpr uint32_t kSFlagAgg = 1u << 30, kSFlagPre = 2u << 30, kSValMask = (1u << 30) - 1;
+
+struct __align__(16) SortSmem {
+    uint64_t keys[kSortTile];
+    uint32_t vals[kSortTile];
+    uint32_t warp_hist[kSortWarps][kRadix];
+    uint32_t block_excl[kRadix];
+    uint64_t digit_out[kRadix];  // global position of the digit's first key in this tile
+    uint64_t scan_tmp[kSortThreads / 32];
+    uint32_t tile;
+};
+
+__global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
+    const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+    uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const int64_t *n_keys_dev,
+    int64_t capacity, int shift, const uint32_t *__restrict__ hist, uint32_t *sort_state,
+    uint32_t *ticket, int32_t *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SortSmem &sm = *reinterpret_cast<SortSmem *>(smem_raw);
+    const int64_t K = sort_count(n_keys_dev, capacity);
+    const int64_t ntiles = (K + kSortTile - 1) / kSortTile;
+    if (threadIdx.x == 0) sm.tile = atomicAdd(ticket, 1u);
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&sm.warp_hist[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t tile = sm.tile;
+    if (tile >= ntiles) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int64_t wbase = tile * kSortTile + (int64_t)wid * (32 * kSortItems);
+
+    uint64_t k[kSortItems];
+    uint32_t v[kSortItems];
+    uint32_t rank[kSortItems];
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const int64_t idx = wbase + j * 32 + lane;
+        const bool valid = idx < K;
+        k[j] = valid ? keys_in[idx] : 0ull;
+        v[j] = valid ? vals_in[idx] : 0u;
+        rank[j] = valid ? 0u : 0xffffffffu;
+    }
+    // stable warp-level multisplit: element order within a warp is (j, lane)
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const bool valid = rank[j] != 0xffffffffu;
+        const uint32_t d = valid ? (uint32_t)(k[j] >> shift) & 255u : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = 0;
+        if (valid) before = sm.warp_hist[wid][d];
+        __syncwarp();
+        if (valid) {
+            rank[j] = before + __popc(peers & lt_mask);
+            if (lane == 31 - __clz(peers)) sm.warp_hist[wid][d] = before + __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: exclusive offsets across warps, tile count, look-back
+    const int d = threadIdx.x;
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t c = sm.warp_hist[w][d];
+        sm.warp_hist[w][d] = cnt;
+        cnt += c;
+    }
+    uint64_t tot;
+    const uint64_t bexcl = block_excl_sum<kSortThreads>(cnt, tot, sm.scan_tmp);
+    sm.block_excl[d] = (uint32_t)bexcl;
+    uint64_t gtot;
+    const uint64_t gexcl = block_excl_sum<kSortThreads>(hist[d], gtot, sm.scan_tmp);
+    uint32_t *st = sort_state + (size_t)tile * kRadix + d;
+    uint64_t prefix = 0;
+    if (tile == 0) {
+        st_release_u32(st, kSFlagPre | cnt);
+    } else {
+        st_release_u32(st, kSFlagAgg | cnt);
+        int64_t p = tile - 1;
+        uint32_t spins = 0;
+        while (p >= 0) {
+            const uint32_t w = ld_acquire_u32(sort_state + (size_t)p * kRadix + d);
+            if ((w >> 30) == 0) {
+                if (++spins > kSpinLimit) { atomicExch(status, (int32_t)P2E_ERR_TIMEOUT); break; }
+                backoff(spins);
+                continue;
+            }
+            prefix += w & kSValMask;
+            if ((w >> 30) == 2) break;
+            --p;
+        }
+        st_release_u32(st, kSFlagPre | (uint32_t)(prefix + cnt));
+    }
+    sm.digit_out[d] = gexcl + prefix;
+    __syncthreads();
+    // stage in shared memory in block-sorted order
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        if (rank[j] != 0xffffffffu) {
+            const uint32_t dd = (uint32_t)(k[j] >> shift) & 255u;
+            const uint32_t pos = sm.block_excl[dd] + sm.warp_hist[wid][dd] + rank[j];
+            sm.keys[pos] = k[j];
+            sm.vals[pos] = v[j];
+        }
+    }
+    __syncthreads();
+    const int64_t tcount = (K - tile * kSortTile) < kSortTile ? (K - tile * kSortTile) : kSortTile;
+    for (int i = threadIdx.x; i < tcount; i += kSortThreads) {
+        const uint64_t kk = sm.keys[i];
+        const uint32_t dd = (uint32_t)(kk >> shift) & 255u;
+        const uint64_t o = sm.digit_out[dd] + (uint64_t)(i - sm.block_excl[dd]);
+        if (o < (uint64_t)K) {  // always true unless a look-back gave up
+            keys_out[o] = kk;
+            vals_out[o] = sm.vals[i];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K5: tile ranges
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) tile_ranges_kernel(const uint64_t *__restrict__ keys,
+                                                          const int64_t *n_keys_dev, int64_t capacity,
+                                                          int64_t total_tiles, uint2 *__restrict__ ranges) {
+    const int64_t K = sort_count(n_keys_dev, capacity);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t t = keys[i] >> 32;
+        if (t >= (uint64_t)total_tiles) continue;
+        if (i == 0 || (keys[i - 1] >> 32) != t) ranges[t].x = (uint32_t)i;
+        if (i == K - 1 || (keys[i + 1] >> 32) != t) ranges[t].y = (uint32_t)(i + 1);
+    }
+}
+
+int sort_passes(int64_t total_tiles) {
+    int tb = 0;
+    while ((int64_t(1) << tb) < total_tiles) ++tb;
+    return (32 + tb + 7) / 8;
+}
+
+cudaError_t launch_sort_bin(const p2e_projected *proj, const Views &P, p2e_bins *io,
+                            int num_sms, cudaStream_t st) {
+    const int64_t n_total = P.n * P.n_views;
+    SortScratch S = carve(io->scratch, n_total, io->capacity);
+    const int passes = sort_passes(P.total_tiles);
+    cudaError_t e;
+    // one memset clears histograms, tickets and every look-back word
+    e = cudaMemsetAsync(io->scratch, 0, sort_scratch_bytes(n_total, io->capacity), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(io->ranges, 0, (size_t)P.total_tiles * sizeof(uint2), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(io->n_keys_dev, 0, sizeof(int64_t), st);
+    if (e != cudaSuccess) return e;
+    if (n_total > 0) {
+        const unsigned g = (unsigned)S.scan_tiles;
+        scan_emit_kernel<<<g, kScanThreads, 0, st>>>(proj->ntiles, (const ushort4 *)proj->rect,
+                                                     (const float4 *)proj->xy_depth, n_total,
+                                                     io->keys[0], io->vals[0], io->capacity, S,
+                                                     io->n_keys_dev, io->status_dev, P);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // digit histograms of every pass in one read of the keys
+    digit_hist_kernel<<<num_sms * 4, 256, 0, st>>>(io->keys[0], io->n_keys_dev, io->capacity,
+                                                   passes, S.hist);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t smem = sizeof(SortSmem);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(radix_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+    }
+    const unsigned sort_grid = (unsigned)(S.sort_tiles > 0 ? S.sort_tiles : 1);
+    for (int p = 0; p < passes; ++p) {
+        const int src = p & 1, dst = src ^ 1;
+        radix_pass_kernel<<<sort_grid, kSortThreads, smem, st>>>(
+            io->keys[src], io->vals[src], io->keys[dst], io->vals[dst], io->n_keys_dev, io->capacity,
+            8 * p, S.hist + p * kRadix, S.sort_state + (size_t)p * (S.sort_tiles + 1) * kRadix,
+            S.tickets + 1 + p, io->status_dev);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    io->result = passes & 1;
+    tile_ranges_kernel<<<num_sms * 8, 256, 0, st>>>(io->keys[io->result], io->n_keys_dev, io->capacity,
+                                                    P.total_tiles, (uint2 *)io->ranges);
+    return cudaGetLastError();
+}
+
+}  // namespace p2e

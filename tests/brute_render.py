@@ -15,8 +15,11 @@ import numpy as np
 from scipy.spatial.transform import Rotation
 
 
-def brute_render(g, cam, lowpass=0.3, k=3.0, alpha_floor=1 / 255, alpha_max=0.99,
-                 t_min=1e-4, bg=(0.0, 0.0, 0.0)):
+F32 = lambda x: float(np.float32(x))  # noqa: E731  (constants are fp32 inputs)
+
+
+def brute_render(g, cam, lowpass=F32(0.3), k=3.0, alpha_floor=F32(1 / 255), alpha_max=F32(0.99),
+                 t_min=F32(1e-4), bg=(0.0, 0.0, 0.0)):
     W, H = cam["width"], cam["height"]
     V = np.asarray(cam["viewmat"], np.float64)
     T, t = V[:, :3], V[:, 3]

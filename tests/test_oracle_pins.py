@@ -43,8 +43,8 @@ def test_p1_isotropic_closed_form(quat):
     s2 = (f * sig / z0) ** 2 + CFG["lowpass"]
     ii, jj = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
     r2 = (ii - W / 2) ** 2 + (jj - H / 2) ** 2
-    al = np.minimum(0.99, o * np.exp(-r2 / (2 * s2)))
-    on = (r2 <= 9 * s2) & (al >= 1 / 255)
+    al = np.minimum(CFG["alpha_max"], o * np.exp(-r2 / (2 * s2)))
+    on = (r2 <= 9 * s2) & (al >= CFG["alpha_floor"])
     al = np.where(on, al, 0.0)
     exp_rgb = np.asarray(bg)[:, None, None] + al * (c - np.asarray(bg))[:, None, None]
     ok = ~r["flag"]
@@ -91,7 +91,8 @@ def test_p2_quaternion_convention():
     p = oracle.project(one_gauss((0, 0, z), s, (h, 0, 0, h)), ident_cam(128, 128, f))
     k = (f / z) ** 2
     s32 = np.float32(s).astype(np.float64)
-    np.testing.assert_allclose(p["cov2"][0], [k * s32[1] ** 2 + 0.3, 0.0, k * s32[0] ** 2 + 0.3],
+    lp = CFG["lowpass"]
+    np.testing.assert_allclose(p["cov2"][0], [k * s32[1] ** 2 + lp, 0.0, k * s32[0] ** 2 + lp],
                                rtol=1e-7, atol=1e-12)
 
 
@@ -118,7 +119,7 @@ def test_projection_vs_library_rotation():
         R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
         Sig = R @ np.diag(g["scale"][i].astype(np.float64) ** 2) @ R.T
         J = np.array([[f / z, 0, -x * f / z ** 2], [0, f / z, -y * f / z ** 2]])
-        Ss = J @ T @ Sig @ T.T @ J.T + 0.3 * np.eye(2)
+        Ss = J @ T @ Sig @ T.T @ J.T + CFG["lowpass"] * np.eye(2)
         np.testing.assert_allclose(p["cov2"][i], [Ss[0, 0], Ss[0, 1], Ss[1, 1]],
                                    rtol=1e-10, atol=1e-12)
 
