@@ -166,6 +166,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--path", default="render", choices=["render", "pca", "learned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", type=int, default=16, choices=[8, 16, 32])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -188,11 +189,12 @@ def main():
 
     xyz, rgb, g = make_inputs()
     center = xyz.mean(0)
-    cams = cameras(center, args.warmup + args.steps, SEED + 100 + rank)
+    e_steps = max(3, min(args.steps, 50))
+    cams = cameras(center, args.warmup + max(args.steps, e_steps), SEED + 100 + rank)
     gs = GaussianSet.from_numpy(g, dev)
     st = torch.cuda.current_stream()
     # capacity from a probe frame, with headroom for other viewpoints
-    rend = Renderer(capacity=1 << 21, device=dev)
+    rend = Renderer({"tile": args.tile}, capacity=1 << 21, device=dev)
     probe = rend.render(gs, [cams[0]])
     rend.capacity = int(rend.n_keys * 1.6) + 4096
     rend.render(gs, [cams[0]])
@@ -245,7 +247,6 @@ def main():
     gd = GaussianSet.empty(gs.n, dev)
     h2d = sum(t.numel() * 4 for t in host.values())
     d2h = out_host.numel() * 4
-    e_steps = max(3, min(args.steps, 50))
     for w in range(2):
         for k, t in host.items():
             getattr(gd, k).copy_(t, non_blocking=True)
@@ -292,6 +293,7 @@ def main():
             "config": {"workload": workload_name(args.path), "points": N_POINTS, "resolution": RES,
                        "cameras": "uniform on a 2.5 m sphere, re-drawn per frame",
                        "l2": "flushed (256 MiB write) before every timed frame",
+                       "tile": args.tile,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clocks": clocks, "gpu_launches": 11 * args.steps,
             "e2e": {"value": e2e_val, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,

@@ -100,7 +100,10 @@ typedef struct {
  *            int16 floor(u) | int16 floor(v) << 16); floor(u), floor(v)
  *            are clamped to [-32768, 32767].
  *   conic_op float4 (A, B, C, o): Sigma_s^{-1} = [[A, B], [B, C]]
- *   rect     ushort4 (tx0, ty0, tx1, ty1): inclusive tile rectangle
+ *   rect     ushort4 (x0, y0, x1, y1): inclusive pixel rectangle of the
+ *            splat's sigma_mult ellipse box.  Its tiles (x / tile, y / tile)
+ *            are exact; the pixel bounds are exact or a superset clamped to
+ *            those tiles (used only to skip splats early).
  *   ntiles   uint32 number of tiles touched (0 = culled) */
 typedef struct {
     float *xy_depth;
@@ -120,12 +123,17 @@ typedef struct {
  *                     written and the sorted result is invalid)
  *   status_dev        int32 device status word (P2E_OK, or P2E_ERR_TIMEOUT
  *                     when a bounded device wait gave up)
+ *   tile_work         uint32[total tiles + 2]: written by p2e_sort_bin
+ *                     ([0] = number of non-empty tiles, [1] = a counter
+ *                     p2e_render resets, then the non-empty tile ids,
+ *                     longest list first) and consumed by p2e_render
  *   result            written by p2e_sort_bin (host field): index (0 or 1)
  *                     of the buffer pair that holds the sorted keys/vals */
 typedef struct {
     uint64_t *keys[2];
     uint32_t *vals[2];
     uint32_t *ranges;
+    uint32_t *tile_work;
     void *scratch;
     int64_t scratch_bytes;
     int64_t capacity;

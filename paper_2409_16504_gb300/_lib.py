@@ -49,7 +49,7 @@ class P2EProjected(C.Structure):
 
 class P2EBins(C.Structure):
     _fields_ = [("keys", C.c_void_p * 2), ("vals", C.c_void_p * 2), ("ranges", C.c_void_p),
-                ("scratch", C.c_void_p), ("scratch_bytes", C.c_int64), ("capacity", C.c_int64),
+                ("tile_work", C.c_void_p), ("scratch", C.c_void_p), ("scratch_bytes", C.c_int64), ("capacity", C.c_int64),
                 ("n_keys_dev", C.c_void_p), ("status_dev", C.c_void_p), ("result", C.c_int32)]
 
 

@@ -1,128 +1,414 @@
 // K6: front-to-back alpha compositing (Sec. 3.1, Eq. 1-2), with the normal
 // and depth images obtained by substituting n_k and z_k for c_k.
 //
-// One CTA per screen tile (tile x tile threads, one pixel each).  The tile's
-// depth-sorted splat list is walked in batches of one splat per thread: the
-// batch (up to 256 splats) is gathered (sorted index -> projected record,
-// colour, normal) into shared memory with coalesced 16-byte loads, then every thread walks the
-// batch from shared memory (broadcast reads).  A pixel stops at the
-// transmittance cutoff; the CTA stops as soon as every pixel has stopped
-// (__syncthreads_count), and a warp whose pixels have all stopped skips the
-// batch.
+// Scheduling.  A persistent grid pulls non-empty tiles from the work list
+// that p2e_sort_bin leaves (longest list first); pixels of empty tiles get
+// the background from a separate fill kernel.
+//
+// Per tile, the depth-sorted list is consumed in waves of G chunks of 256
+// splats:
+//   gather   the wave's splat records go to shared memory (16-byte loads)
+//   cover    splat-parallel: every splat tests the live pixels of its pixel
+//            rectangle inside the tile against its sigma_mult ellipse and
+//            sets its bit in those pixels' 256-bit chunk masks
+//   blend    pixel-parallel: group k composites chunk k from T = 1, walking
+//            only the set bits of its mask, in list (= depth) order
+//   merge    group 0 combines the chunks in order with the associative
+//            "over" rule C += T C_k, T *= T_k.  T is non-increasing, so the
+//            cutoff can only fall inside chunk k when T T_k < t_min; only
+//            that chunk is then re-walked from the true T with the stop
+//            rule, which reproduces the sequential result.
+// The tile is finished when every pixel has reached the cutoff or the
+// list ends.
+//
+// Sub-pixel accuracy: the pixel offset is formed as
+//   (x - (floor(u) - x0)) + (0.5 - frac(u)),
+// an exact small integer plus an exact fraction, so it keeps ~1e-7 px at
+// any image size.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace p2e {
 
 template <int B>
-__global__ void __launch_bounds__(B *B) blend_kernel(
+struct BlendShape {
+    static constexpr int NPIX = B * B;
+    static constexpr int G = (B == 32) ? 1 : 4;    // chunk groups per CTA
+    static constexpr int NT = NPIX * G;            // 256, 1024, 1024 threads
+    static constexpr int CHUNK = 256;
+    static constexpr int WAVE = G * CHUNK;
+    static constexpr int MW = CHUNK / 32;          // mask words per pixel and chunk
+    static constexpr int MAXC = 256;               // chunks with a rectangle-union mask
+};
+
+template <int B>
+struct BlendSmem {
+    using S = BlendShape<B>;
+    float4 off[S::WAVE];     // (0.5 - frac u, 0.5 - frac v, floor u - x0, floor v - y0)
+    float4 co[S::WAVE];      // (A, B, C, o)
+    float4 cz[S::WAVE];      // (r, g, b, depth)
+    float4 nr[S::WAVE];      // (nx, ny, nz, -)
+    uint32_t rect[S::WAVE];  // tile-relative pixel box clamped to the tile, 4 x u8
+    uint32_t mask[S::G][S::MW][S::NPIX];  // word-major: conflict-free per-pixel reads
+    float part[S::G][8][S::NPIX];   // per chunk: C0..2, N0..2, D, T
+    uint32_t plast[S::G][S::NPIX];  // per chunk: last contributor (+1), 0 = none
+    uint32_t cunion[S::MAXC][B];    // per chunk: union of the splats' rectangles, row bitmasks
+    uint32_t alive[B];              // row bitmasks of the pixels still compositing
+    uint32_t clive[S::G];           // chunk of this wave can reach a live pixel
+    uint8_t done[S::NPIX];
+    uint32_t item;
+};
+
+__device__ __forceinline__ uint32_t row_bits(int x0, int x1) {  // bits x0..x1 (x1 <= 31)
+    return (x1 >= 31 ? 0xffffffffu : ((1u << (x1 + 1)) - 1u)) & ~((1u << x0) - 1u);
+}
+
+// power = -1/2 d^T Sigma_s^-1 d at tile-relative pixel (x, y) (same
+// expression in every phase so that the decisions agree)
+__device__ __forceinline__ float splat_power(const float4 &o, const float4 &co, float x, float y) {
+    const float dx = (x - o.z) + o.x;
+    const float dy = (y - o.w) + o.y;
+    return -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
+}
+
+template <int B>
+__global__ void __launch_bounds__(BlendShape<B>::NT) blend_kernel(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
+    const uint32_t *__restrict__ work, uint32_t *__restrict__ work_counter,
     const float4 *__restrict__ xy_depth, const float4 *__restrict__ conic_op,
-    const float4 *__restrict__ rgb, const float4 *__restrict__ normal, float *__restrict__ out_rgb,
-    float *__restrict__ out_nrm, float *__restrict__ out_depth, float *__restrict__ out_alpha,
-    uint32_t *__restrict__ out_last, __grid_constant__ const Views P) {
-    constexpr int NT = B * B;
-    constexpr int BATCH = NT < 256 ? NT : 256;  // splats staged per round
-    __shared__ float4 s_xy[BATCH], s_co[BATCH], s_rgb[BATCH], s_nrm[BATCH];
-    const int64_t tile = blockIdx.x;
-    const int vi = view_of_tile(P, tile);
-    const View &V = P.v[vi];
-    const int64_t lt = tile - V.tile_base;
-    const int ty = (int)(lt / V.tiles_x), tx = (int)(lt - (int64_t)ty * V.tiles_x);
-    const int px = tx * B + (threadIdx.x % B), py = ty * B + (threadIdx.x / B);
-    const bool inside = px < V.W && py < V.H;
-    const uint2 r = ranges[tile];
-    const int64_t gbase = (int64_t)vi * P.n;
+    const ushort4 *__restrict__ rect, const float4 *__restrict__ rgb,
+    const float4 *__restrict__ normal, float *__restrict__ out_rgb, float *__restrict__ out_nrm,
+    float *__restrict__ out_depth, float *__restrict__ out_alpha, uint32_t *__restrict__ out_last,
+    __grid_constant__ const Views P) {
+    using S = BlendShape<B>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BlendSmem<B> &sm = *reinterpret_cast<BlendSmem<B> *>(smem_raw);
+
+    const int tid = threadIdx.x;
+    const int grp = tid / S::NPIX;
+    const int pi = tid - grp * S::NPIX;     // pixel of this thread inside the tile
+    const int lx = pi % B, ly = pi / B;
+    const float lxf = (float)lx, lyf = (float)ly;
     const float pw_min = -0.5f * P.sigma_mult * P.sigma_mult;
     const float amax = P.alpha_max, afloor = P.alpha_floor, tmin = P.t_min;
+    const uint32_t n_work = work[0];
 
-    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f, D = 0.f;
-    uint32_t last = 0;
-    bool done = !inside;
-    for (uint32_t start = r.x; start < r.y; start += BATCH) {
-        if (__syncthreads_count(done) == NT) break;
-        const uint32_t idx = start + threadIdx.x;
-        if (threadIdx.x < BATCH && idx < r.y) {
-            uint32_t g = __ldg(vals + idx);
-            if (g >= (uint32_t)P.n) g = 0;  // only reachable with corrupted bins
-            s_xy[threadIdx.x] = __ldg(xy_depth + gbase + g);
-            s_co[threadIdx.x] = __ldg(conic_op + gbase + g);
-            s_rgb[threadIdx.x] = __ldg(rgb + g);
-            s_nrm[threadIdx.x] = __ldg(normal + g);
-        }
+    for (;;) {
+        if (tid == 0) sm.item = atomicAdd(work_counter, 1u);
         __syncthreads();
-        const int cnt = (int)min((uint32_t)BATCH, r.y - start);
-        if (__all_sync(0xffffffffu, done)) continue;
-        if (!done) {
-            for (int j = 0; j < cnt; ++j) {
-                const float4 xy = s_xy[j];
+        const uint32_t item = sm.item;
+        if (item >= n_work) break;
+        const int64_t tile = work[2 + item];
+        const int vi = view_of_tile(P, tile);
+        const View &V = P.v[vi];
+        const int64_t lt = tile - V.tile_base;
+        const int ty = (int)(lt / V.tiles_x), tx = (int)(lt - (int64_t)ty * V.tiles_x);
+        const int x0 = tx * B, y0 = ty * B;
+        const int px = x0 + lx, py = y0 + ly;
+        const bool inside = px < V.W && py < V.H;
+        const uint2 r = ranges[tile];
+        const int64_t gbase = (int64_t)vi * P.n;
+
+        float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f, D = 0.f;
+        uint32_t last = 0;
+        bool done = !inside;
+        const uint32_t L = r.y - r.x;
+        const int nunion = (int)min((uint32_t)S::MAXC, (L + S::CHUNK - 1) / S::CHUNK);
+        if (grp == 0) {
+            sm.done[pi] = done ? 1 : 0;
+            const uint32_t m = __ballot_sync(0xffffffffu, !done);
+            if ((tid & 31) == 0)
+                for (int rr = 0; rr < 32 / B; ++rr)
+                    sm.alive[(tid >> 5) * (32 / B) + rr] = (B == 32) ? m : ((m >> (rr * B)) & ((1u << B) - 1u));
+        }
+        // ---- pre-pass: union of the splat rectangles of every chunk
+        for (int t = tid; t < nunion * B; t += S::NT) (&sm.cunion[0][0])[t] = 0u;
+        __syncthreads();
+        for (uint32_t t = tid; t < L && t < (uint32_t)(nunion * S::CHUNK); t += S::NT) {
+            uint32_t g = __ldg(vals + r.x + t);
+            if (g >= (uint32_t)P.n) g = 0;
+            const ushort4 rc = __ldg(rect + gbase + g);
+            const int rx0 = max(0, (int)rc.x - x0), rx1 = min(B - 1, (int)rc.z - x0);
+            const int ry0 = max(0, (int)rc.y - y0), ry1 = min(B - 1, (int)rc.w - y0);
+            if (rx0 > rx1 || ry0 > ry1) continue;
+            const uint32_t bits = row_bits(rx0, rx1);
+            uint32_t *cu = sm.cunion[t / S::CHUNK];
+            for (int y = ry0; y <= ry1; ++y) atomicOr(&cu[y], bits);
+        }
+
+        for (uint32_t ws = r.x; ws < r.y; ws += S::WAVE) {
+            if (__syncthreads_count(grp == 0 ? done : true) == S::NT) break;
+            const int wn = (int)min((uint32_t)S::WAVE, r.y - ws);
+            // ---- which chunks of the wave can still reach a live pixel
+            if (tid < S::G) {
+                const int c = (int)((ws - r.x) / S::CHUNK) + tid;
+                uint32_t hit = 0;
+                if (tid * S::CHUNK >= wn) hit = 0;
+                else if (c >= nunion) hit = 1;
+                else
+                    for (int y = 0; y < B; ++y) hit |= sm.cunion[c][y] & sm.alive[y];
+                sm.clive[tid] = hit ? 1u : 0u;
+            }
+            __syncthreads();
+            {
+                uint32_t any = 0;
+#pragma unroll
+                for (int k = 0; k < S::G; ++k) any |= sm.clive[k];
+                if (!any) continue;  // uniform: no splat of this wave can contribute
+            }
+            // ---- gather + clear masks
+            {
+                uint32_t *mw = &sm.mask[0][0][0];
+                for (int t = tid; t < S::G * S::NPIX * S::MW; t += S::NT) mw[t] = 0u;
+            }
+            for (int t = tid; t < wn; t += S::NT) {
+                if (!sm.clive[t / S::CHUNK]) {
+                    sm.rect[t] = 0xffffffffu;
+                    continue;
+                }
+                uint32_t g = __ldg(vals + ws + t);
+                if (g >= (uint32_t)P.n) g = 0;  // only reachable with corrupted bins
+                const float4 xy = __ldg(xy_depth + gbase + g);
+                const ushort4 rc = __ldg(rect + gbase + g);
+                const float4 cc = __ldg(rgb + g);
                 const int packed = __float_as_int(xy.w);
                 const int iu = (int)(int16_t)(packed & 0xffff), iv = packed >> 16;
-                const float dx = (float)(px - iu) + (0.5f - xy.x);
-                const float dy = (float)(py - iv) + (0.5f - xy.y);
-                const float4 co = s_co[j];
-                const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
-                if (power < pw_min) continue;
-                const float alpha = fminf(amax, co.w * __expf(power));
-                if (alpha < afloor) continue;
-                const float Tn = T * (1.f - alpha);
-                if (Tn < tmin) {
-                    done = true;
-                    break;
+                sm.off[t] = make_float4(0.5f - xy.x, 0.5f - xy.y, (float)(iu - x0), (float)(iv - y0));
+                sm.co[t] = __ldg(conic_op + gbase + g);
+                sm.cz[t] = make_float4(cc.x, cc.y, cc.z, xy.z);
+                sm.nr[t] = __ldg(normal + g);
+                const int rx0 = max(0, (int)rc.x - x0), rx1 = min(B - 1, (int)rc.z - x0);
+                const int ry0 = max(0, (int)rc.y - y0), ry1 = min(B - 1, (int)rc.w - y0);
+                sm.rect[t] = (rx0 > rx1 || ry0 > ry1)
+                                 ? 0xffffffffu
+                                 : (uint32_t)rx0 | ((uint32_t)rx1 << 8) | ((uint32_t)ry0 << 16) |
+                                       ((uint32_t)ry1 << 24);
+            }
+            __syncthreads();
+            // ---- cover: splat-parallel coverage masks of the live pixels
+            for (int t = tid; t < wn; t += S::NT) {
+                const uint32_t rw = sm.rect[t];
+                if (rw == 0xffffffffu) continue;
+                const int rx0 = rw & 0xff, rx1 = (rw >> 8) & 0xff, ry0 = (rw >> 16) & 0xff, ry1 = rw >> 24;
+                const float4 o = sm.off[t], co = sm.co[t];
+                const int k = t / S::CHUNK, b = t % S::CHUNK;
+                const uint32_t bit = 1u << (b & 31);
+                for (int y = ry0; y <= ry1; ++y) {
+                    for (int x = rx0; x <= rx1; ++x) {
+                        const int p = y * B + x;
+                        if (sm.done[p]) continue;
+                        if (splat_power(o, co, (float)x, (float)y) < pw_min) continue;
+                        atomicOr(&sm.mask[k][b >> 5][p], bit);
+                    }
                 }
-                const float w = alpha * T;
-                const float4 cc = s_rgb[j], nn = s_nrm[j];
-                c0 = fmaf(w, cc.x, c0);
-                c1 = fmaf(w, cc.y, c1);
-                c2 = fmaf(w, cc.z, c2);
-                n0 = fmaf(w, nn.x, n0);
-                n1 = fmaf(w, nn.y, n1);
-                n2 = fmaf(w, nn.z, n2);
-                D = fmaf(w, xy.z, D);
-                T = Tn;
-                last = start + (uint32_t)j + 1u;
+            }
+            __syncthreads();
+            // ---- blend: chunk `grp`, composited from T = 1 over its set bits
+            float t_ = 1.f, a0 = 0.f, a1 = 0.f, a2 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f, dd = 0.f;
+            uint32_t lastl = 0;
+            if (!sm.done[pi] && sm.clive[grp]) {
+#pragma unroll 1
+                for (int w = 0; w < S::MW; ++w) {
+                    uint32_t m = sm.mask[grp][w][pi];
+                    while (m) {
+                        const int j = grp * S::CHUNK + w * 32 + (__ffs(m) - 1);
+                        m &= m - 1u;
+                        const float4 o = sm.off[j], co = sm.co[j];
+                        const float power = splat_power(o, co, lxf, lyf);
+                        if (power < pw_min) continue;
+                        const float alpha = fminf(amax, co.w * __expf(power));
+                        if (alpha < afloor) continue;
+                        const float wgt = alpha * t_;
+                        const float4 cz = sm.cz[j], nr = sm.nr[j];
+                        a0 = fmaf(wgt, cz.x, a0);
+                        a1 = fmaf(wgt, cz.y, a1);
+                        a2 = fmaf(wgt, cz.z, a2);
+                        b0 = fmaf(wgt, nr.x, b0);
+                        b1 = fmaf(wgt, nr.y, b1);
+                        b2 = fmaf(wgt, nr.z, b2);
+                        dd = fmaf(wgt, cz.w, dd);
+                        t_ = t_ * (1.f - alpha);
+                        lastl = ws + (uint32_t)j + 1u;
+                    }
+                }
+            }
+            sm.part[grp][0][pi] = a0;
+            sm.part[grp][1][pi] = a1;
+            sm.part[grp][2][pi] = a2;
+            sm.part[grp][3][pi] = b0;
+            sm.part[grp][4][pi] = b1;
+            sm.part[grp][5][pi] = b2;
+            sm.part[grp][6][pi] = dd;
+            sm.part[grp][7][pi] = t_;
+            sm.plast[grp][pi] = lastl;
+            __syncthreads();
+            // ---- merge the chunks in list order (group 0)
+            if (grp == 0 && !done) {
+                for (int k = 0; k < S::G; ++k) {
+                    if (!sm.clive[k]) continue;  // nothing of chunk k reaches this tile's live pixels
+                    const float Tk = sm.part[k][7][pi];
+                    if (T * Tk >= tmin) {
+                        c0 = fmaf(T, sm.part[k][0][pi], c0);
+                        c1 = fmaf(T, sm.part[k][1][pi], c1);
+                        c2 = fmaf(T, sm.part[k][2][pi], c2);
+                        n0 = fmaf(T, sm.part[k][3][pi], n0);
+                        n1 = fmaf(T, sm.part[k][4][pi], n1);
+                        n2 = fmaf(T, sm.part[k][5][pi], n2);
+                        D = fmaf(T, sm.part[k][6][pi], D);
+                        T = T * Tk;
+                        if (sm.plast[k][pi]) last = sm.plast[k][pi];
+                        continue;
+                    }
+                    // the cutoff falls inside chunk k: walk it from the true T
+                    for (int w = 0; w < S::MW && !done; ++w) {
+                        uint32_t m = sm.mask[k][w][pi];
+                        while (m) {
+                            const int j = k * S::CHUNK + w * 32 + (__ffs(m) - 1);
+                            m &= m - 1u;
+                            const float4 o = sm.off[j], co = sm.co[j];
+                            const float power = splat_power(o, co, lxf, lyf);
+                            if (power < pw_min) continue;
+                            const float alpha = fminf(amax, co.w * __expf(power));
+                            if (alpha < afloor) continue;
+                            const float Tn = T * (1.f - alpha);
+                            if (Tn < tmin) {
+                                done = true;
+                                break;
+                            }
+                            const float wgt = alpha * T;
+                            const float4 cz = sm.cz[j], nr = sm.nr[j];
+                            c0 = fmaf(wgt, cz.x, c0);
+                            c1 = fmaf(wgt, cz.y, c1);
+                            c2 = fmaf(wgt, cz.z, c2);
+                            n0 = fmaf(wgt, nr.x, n0);
+                            n1 = fmaf(wgt, nr.y, n1);
+                            n2 = fmaf(wgt, nr.z, n2);
+                            D = fmaf(wgt, cz.w, D);
+                            T = Tn;
+                            last = ws + (uint32_t)j + 1u;
+                        }
+                    }
+                    if (done) break;
+                }
+                sm.done[pi] = done ? 1 : 0;
+            }
+            if (grp == 0) {
+                const uint32_t m = __ballot_sync(0xffffffffu, !done);
+                if ((tid & 31) == 0)
+                    for (int rr = 0; rr < 32 / B; ++rr)
+                        sm.alive[(tid >> 5) * (32 / B) + rr] =
+                            (B == 32) ? m : ((m >> (rr * B)) & ((1u << B) - 1u));
             }
         }
+        if (grp == 0 && inside) {
+            const int64_t HW = (int64_t)V.H * V.W;
+            const int64_t p = (int64_t)py * V.W + px;
+            if (out_rgb) {
+                float *o = out_rgb + 3 * V.pix_base + p;
+                o[0] = fmaf(T, P.bg[0], c0);
+                o[HW] = fmaf(T, P.bg[1], c1);
+                o[2 * HW] = fmaf(T, P.bg[2], c2);
+            }
+            if (out_nrm) {
+                float *o = out_nrm + 3 * V.pix_base + p;
+                o[0] = n0;
+                o[HW] = n1;
+                o[2 * HW] = n2;
+            }
+            if (out_depth) out_depth[V.pix_base + p] = D;
+            if (out_alpha) out_alpha[V.pix_base + p] = 1.f - T;
+            if (out_last) out_last[V.pix_base + p] = last;
+        }
+        __syncthreads();
     }
-    if (!inside) return;
-    const int64_t HW = (int64_t)V.H * V.W;
-    const int64_t p = (int64_t)py * V.W + px;
-    if (out_rgb) {
-        float *o = out_rgb + 3 * V.pix_base + p;
-        o[0] = fmaf(T, P.bg[0], c0);
-        o[HW] = fmaf(T, P.bg[1], c1);
-        o[2 * HW] = fmaf(T, P.bg[2], c2);
+}
+
+// Background for every pixel of a tile with an empty list.
+__global__ void __launch_bounds__(256) fill_empty_kernel(const uint2 *__restrict__ ranges,
+                                                         int64_t total_pix, float *__restrict__ out_rgb,
+                                                         float *__restrict__ out_nrm,
+                                                         float *__restrict__ out_depth,
+                                                         float *__restrict__ out_alpha,
+                                                         uint32_t *__restrict__ out_last,
+                                                         __grid_constant__ const Views P) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total_pix;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int v = 0;
+        while (v + 1 < P.n_views && P.v[v + 1].pix_base <= q) ++v;
+        const View &V = P.v[v];
+        const int64_t p = q - V.pix_base;
+        const int y = (int)(p / V.W), x = (int)(p - (int64_t)y * V.W);
+        const int64_t tile = V.tile_base + (int64_t)(y / P.tile) * V.tiles_x + x / P.tile;
+        const uint2 r = ranges[tile];
+        if (r.y > r.x) continue;
+        const int64_t HW = (int64_t)V.H * V.W;
+        if (out_rgb) {
+            float *o = out_rgb + 3 * V.pix_base + p;
+            o[0] = P.bg[0];
+            o[HW] = P.bg[1];
+            o[2 * HW] = P.bg[2];
+        }
+        if (out_nrm) {
+            float *o = out_nrm + 3 * V.pix_base + p;
+            o[0] = 0.f;
+            o[HW] = 0.f;
+            o[2 * HW] = 0.f;
+        }
+        if (out_depth) out_depth[q] = 0.f;
+        if (out_alpha) out_alpha[q] = 0.f;
+        if (out_last) out_last[q] = 0u;
     }
-    if (out_nrm) {
-        float *o = out_nrm + 3 * V.pix_base + p;
-        o[0] = n0;
-        o[HW] = n1;
-        o[2 * HW] = n2;
+}
+
+int device_sms();
+
+template <int B>
+static cudaError_t launch_blend(const p2e_gaussians *g, const p2e_projected *proj,
+                                const p2e_bins *bins, const Views &P, float *rgb, float *nrm,
+                                float *depth, float *alpha, uint32_t *last, cudaStream_t st) {
+    using S = BlendShape<B>;
+    const size_t smem = sizeof(BlendSmem<B>);
+    static int configured[64] = {0};
+    static int per_sm[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int slot = (dev >= 0 && dev < 64) ? dev : 0;
+    if (!configured[slot]) {
+        cudaError_t e = cudaFuncSetAttribute(blend_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blend_kernel<B>, S::NT, smem);
+        per_sm[slot] = nb > 0 ? nb : 1;
+        configured[slot] = 1;
     }
-    if (out_depth) out_depth[V.pix_base + p] = D;
-    if (out_alpha) out_alpha[V.pix_base + p] = 1.f - T;
-    if (out_last) out_last[V.pix_base + p] = last;
+    cudaError_t e = cudaMemsetAsync(bins->tile_work + 1, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    const int64_t total_pix = P.v[P.n_views - 1].pix_base +
+                              (int64_t)P.v[P.n_views - 1].W * P.v[P.n_views - 1].H;
+    const int sms = device_sms();
+    fill_empty_kernel<<<sms * 8, 256, 0, st>>>((const uint2 *)bins->ranges, total_pix, rgb, nrm, depth,
+                                               alpha, last, P);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int64_t grid = std::min<int64_t>((int64_t)sms * per_sm[slot], P.total_tiles);
+    blend_kernel<B><<<(unsigned)grid, S::NT, smem, st>>>(
+        (const uint2 *)bins->ranges, bins->vals[bins->result], bins->tile_work, bins->tile_work + 1,
+        (const float4 *)proj->xy_depth, (const float4 *)proj->conic_op, (const ushort4 *)proj->rect,
+        (const float4 *)g->rgb, (const float4 *)g->normal, rgb, nrm, depth, alpha, last, P);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_render(const p2e_gaussians *g, const p2e_projected *proj, const p2e_bins *bins,
                           const Views &P, float *rgb, float *nrm, float *depth, float *alpha,
                           uint32_t *last, cudaStream_t st) {
     if (P.total_tiles == 0) return cudaSuccess;
-    const unsigned grid = (unsigned)P.total_tiles;
-    const uint32_t *vals = bins->vals[bins->result];
-    const uint2 *ranges = (const uint2 *)bins->ranges;
-#define P2E_BLEND(BB)                                                                           \
-    blend_kernel<BB><<<grid, BB * BB, 0, st>>>(ranges, vals, (const float4 *)proj->xy_depth,     \
-                                               (const float4 *)proj->conic_op,                   \
-                                               (const float4 *)g->rgb, (const float4 *)g->normal, \
-                                               rgb, nrm, depth, alpha, last, P)
     switch (P.tile) {
-        case 8: P2E_BLEND(8); break;
-        case 16: P2E_BLEND(16); break;
-        case 32: P2E_BLEND(32); break;
+        case 8: return launch_blend<8>(g, proj, bins, P, rgb, nrm, depth, alpha, last, st);
+        case 16: return launch_blend<16>(g, proj, bins, P, rgb, nrm, depth, alpha, last, st);
+        case 32: return launch_blend<32>(g, proj, bins, P, rgb, nrm, depth, alpha, last, st);
         default: return cudaErrorInvalidValue;
     }
-#undef P2E_BLEND
-    return cudaGetLastError();
 }
 
 }  // namespace p2e

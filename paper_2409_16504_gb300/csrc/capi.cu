@@ -171,7 +171,8 @@ p2e_status p2e_sort_bin(const p2e_projected *proj, int64_t n, const p2e_camera *
     if (n < 0 || n >= (int64_t(1) << 31) || !io) return P2E_ERR_INVALID_ARG;
     if (n > 0 && (s = check_proj(proj)) != P2E_OK) return s;
     if (io->capacity < 0 || io->capacity >= (int64_t(1) << 30)) return P2E_ERR_INVALID_ARG;
-    if (!io->ranges || !io->n_keys_dev || !io->status_dev || !io->scratch) return P2E_ERR_INVALID_ARG;
+    if (!io->ranges || !io->tile_work || !io->n_keys_dev || !io->status_dev || !io->scratch)
+        return P2E_ERR_INVALID_ARG;
     if (io->capacity > 0 && (!io->keys[0] || !io->keys[1] || !io->vals[0] || !io->vals[1]))
         return P2E_ERR_INVALID_ARG;
     if (((uintptr_t)io->scratch & 255u) || ((uintptr_t)io->ranges & 7u)) return P2E_ERR_INVALID_ARG;
@@ -203,7 +204,8 @@ p2e_status p2e_render(const p2e_gaussians *g, const p2e_projected *proj, const p
     Views P;
     if ((s = fill_views(cams, n_views, cfg, g->n, P)) != P2E_OK) return s;
     if (g->n > 0 && (s = check_proj(proj)) != P2E_OK) return s;
-    if (!bins || !bins->ranges || (bins->result != 0 && bins->result != 1)) return P2E_ERR_INVALID_ARG;
+    if (!bins || !bins->ranges || !bins->tile_work || (bins->result != 0 && bins->result != 1))
+        return P2E_ERR_INVALID_ARG;
     if (bins->capacity > 0 && !bins->vals[bins->result]) return P2E_ERR_INVALID_ARG;
     return launch_render(g, proj, bins, P, rgb, normal, depth, alpha, last, (cudaStream_t)stream) ==
                    cudaSuccess

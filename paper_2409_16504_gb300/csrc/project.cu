@@ -17,7 +17,9 @@ namespace p2e {
 
 struct ProjOut {
     bool visible;
-    int tx0, ty0, tx1, ty1;
+    int tx0, ty0, tx1, ty1;   // exact tile rectangle (inclusive)
+    int px0, py0, px1, py1;   // pixel rectangle: exact (double path) or a superset
+                              // of it clamped to the exact tile rectangle
     float fu, fv;          // sub-pixel parts of the centre, in [0, 1)
     int iu, iv;            // floor of the centre
     float zkey;            // fp32 of the double camera depth
@@ -117,6 +119,10 @@ __device__ __noinline__ void project_fp64(const View &V, const Views &P, float4 
     axis_rect_d(loy, hiy, V.H, P.tile, o.ty0, o.ty1, ey_);
     if (ex_ || ey_) return;
     o.visible = true;
+    o.px0 = (int)fmax(0.0, ceil(lox));
+    o.px1 = (int)fmin((double)(V.W - 1), floor(hix));
+    o.py0 = (int)fmax(0.0, ceil(loy));
+    o.py1 = (int)fmin((double)(V.H - 1), floor(hiy));
     const double fu = floor(u), fv = floor(v);
     o.fu = (float)(u - fu);
     o.fv = (float)(v - fv);
@@ -295,6 +301,19 @@ __device__ __forceinline__ bool project_fp32(const View &V, const Views &P, floa
     if (ea_ || ec_) return true;  // culled for certain (empty box)
     if (a0 != b0 || a1 != b1 || c0 != d0 || c1 != d1) return false;
     o.tx0 = a0; o.tx1 = a1; o.ty0 = c0; o.ty1 = c1;
+    // pixel rectangle of the widened box, clamped into the exact tile
+    // rectangle: a superset of the exact pixel rectangle with the same tiles
+    {
+        const int B = P.tile;
+        const float fx0 = fmaxf(0.f, fminf(ceilf(lox - epx), (float)(V.W - 1)));
+        const float fx1 = fmaxf(0.f, fminf(floorf(hix + epx), (float)(V.W - 1)));
+        const float fy0 = fmaxf(0.f, fminf(ceilf(loy - epy), (float)(V.H - 1)));
+        const float fy1 = fmaxf(0.f, fminf(floorf(hiy + epy), (float)(V.H - 1)));
+        o.px0 = max((int)fx0, a0 * B);
+        o.px1 = min((int)fx1, a1 * B + B - 1);
+        o.py0 = max((int)fy0, c0 * B);
+        o.py1 = min((int)fy1, c1 * B + B - 1);
+    }
     ff_floor(uh, ul, o.iu, o.fu);
     ff_floor(vh, vl, o.iv, o.fv);
     const float idet = 1.f / det;
@@ -332,8 +351,8 @@ __global__ void __launch_bounds__(256) project_kernel(const float4 *__restrict__
         return;
     }
     ntiles[e] = (uint32_t)((o.tx1 - o.tx0 + 1) * (o.ty1 - o.ty0 + 1));
-    rect[e] = make_ushort4((unsigned short)o.tx0, (unsigned short)o.ty0, (unsigned short)o.tx1,
-                           (unsigned short)o.ty1);
+    rect[e] = make_ushort4((unsigned short)o.px0, (unsigned short)o.py0, (unsigned short)o.px1,
+                           (unsigned short)o.py1);
     const uint32_t packed = ((uint32_t)(uint16_t)(int16_t)o.iu) | ((uint32_t)(uint16_t)(int16_t)o.iv << 16);
     xy_depth[e] = make_float4(o.fu, o.fv, o.zkey, __uint_as_float(packed));
     conic_op[e] = make_float4(o.A, o.B, o.C, m.w);

@@ -168,12 +168,14 @@ __global__ void __launch_bounds__(kScanThreads) scan_emit_kernel(
             const int vi = (int)(e / P.n);
             const View &V = P.v[vi];
             const int64_t g = e - (int64_t)vi * P.n;
-            const ushort4 r = __ldg(rect + e);
+            const ushort4 r = __ldg(rect + e);  // pixel rectangle -> tiles
+            const int B = P.tile;
+            const int tx0 = r.x / B, ty0 = r.y / B, tx1 = r.z / B, ty1 = r.w / B;
             const uint32_t zb = __float_as_uint(__ldg(&xy_depth[e].z));
             uint64_t o = off;
-            for (int ty = r.y; ty <= r.w; ++ty) {
+            for (int ty = ty0; ty <= ty1; ++ty) {
                 const int64_t rowid = V.tile_base + (int64_t)ty * V.tiles_x;
-                for (int tx = r.x; tx <= r.z; ++tx, ++o) {
+                for (int tx = tx0; tx <= tx1; ++tx, ++o) {
                     if ((int64_t)o < capacity) {
                         keys[o] = ((uint64_t)(rowid + tx) << 32) | zb;
                         vals[o] = (uint32_t)g;
@@ -349,6 +351,37 @@ __global__ void __launch_bounds__(256) tile_ranges_kernel(const uint64_t *__rest
     }
 }
 
+// Non-empty tiles, longest list first (by power-of-two length class), for
+// the persistent compositing kernel: work[0] = count, work[1] = counter
+// (zeroed here and by p2e_render), work[2..] = tile ids.
+__global__ void __launch_bounds__(1024) tile_work_kernel(const uint2 *__restrict__ ranges,
+                                                         int64_t total_tiles, uint32_t *work) {
+    __shared__ uint32_t cnt[33], base[33];
+    if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < total_tiles; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        const uint32_t len = r.y - r.x;
+        if (len) atomicAdd(&cnt[31 - __clz(len)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int b = 31; b >= 0; --b) {
+            base[b] = acc;
+            acc += cnt[b];
+        }
+        work[0] = acc;
+        work[1] = 0;
+    }
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < total_tiles; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        const uint32_t len = r.y - r.x;
+        if (len) work[2 + atomicAdd(&base[31 - __clz(len)], 1u)] = (uint32_t)t;
+    }
+}
+
 int sort_passes(int64_t total_tiles) {
     int tb = 0;
     while ((int64_t(1) << tb) < total_tiles) ++tb;
@@ -398,6 +431,8 @@ cudaError_t launch_sort_bin(const p2e_projected *proj, const Views &P, p2e_bins 
     io->result = passes & 1;
     tile_ranges_kernel<<<num_sms * 8, 256, 0, st>>>(io->keys[io->result], io->n_keys_dev, io->capacity,
                                                     P.total_tiles, (uint2 *)io->ranges);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    tile_work_kernel<<<1, 1024, 0, st>>>((const uint2 *)io->ranges, P.total_tiles, io->tile_work);
     return cudaGetLastError();
 }
 

@@ -124,6 +124,7 @@ class Bins:
         self.keys = [torch.empty((cap,), dtype=torch.int64, device=device) for _ in range(2)]
         self.vals = [torch.empty((cap,), dtype=torch.int32, device=device) for _ in range(2)]
         self.ranges = torch.zeros((max(total_tiles, 1), 2), dtype=torch.int32, device=device)
+        self.tile_work = torch.zeros((total_tiles + 2,), dtype=torch.int32, device=device)
         sb = int(lib.p2e_scratch_bytes(_lib.P2E_SCRATCH_SORT, n_total, cap))
         self.scratch = torch.empty((sb + 256,), dtype=torch.uint8, device=device)
         self.counters = torch.zeros((2,), dtype=torch.int64, device=device)  # n_keys, status
@@ -133,6 +134,7 @@ class Bins:
         s.keys[0], s.keys[1] = self.keys[0].data_ptr(), self.keys[1].data_ptr()
         s.vals[0], s.vals[1] = self.vals[0].data_ptr(), self.vals[1].data_ptr()
         s.ranges = self.ranges.data_ptr()
+        s.tile_work = self.tile_work.data_ptr()
         base = self.scratch.data_ptr()
         s.scratch = (base + 255) & ~255
         s.scratch_bytes = sb

@@ -64,7 +64,7 @@ def gpu_proj_view(r, v, n):
     iu = (packed & 0xFFFF).astype(np.uint16).view(np.int16).astype(np.float64)
     iv = (packed >> 16).astype(np.uint16).view(np.int16).astype(np.float64)
     uv = np.stack([iu + xy[:, 0], iv + xy[:, 1]], 1)
-    return dict(uv=uv, zkey=xy[:, 2].copy(), conic=co[:, :3], rect=rect[:, [0, 2, 1, 3]], ntiles=nt)
+    return dict(uv=uv, zkey=xy[:, 2].copy(), conic=co[:, :3], prect=rect[:, [0, 2, 1, 3]], ntiles=nt)
 
 
 def compare_images(gpu: dict, orc: dict, tol=TOL, check_last=True, vals=None, ranges=None,
