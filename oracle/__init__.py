@@ -168,3 +168,53 @@ def render(g: dict, cam: dict, cfg: dict | None = None, brute: bool = False,
                     _p(img), _p(ncontrib), _p(last), _p(flag))
     return dict(rgb=img[0:3], normal=img[3:6], depth=img[6], alpha=img[7],
                 ncontrib=ncontrib, last=last, flag=flag.astype(bool), proj=proj)
+
+
+GRAD_KEYS = ("mean", "scale", "quat", "opacity", "rgb", "normal")
+
+
+def render_grad(g: dict, cams: list, up: list, cfg: dict | None = None) -> dict:
+    """R8: exact FP64 gradient of L = sum_v <up_v, images_v> with respect to
+    the raw inputs (mean, scale, quaternion, opacity, rgb, normal), every
+    discrete decision held fixed.  ``up[v]`` is an (8, H, W) array of the
+    upstream weights of view v: rgb(3), normal(3), depth, alpha."""
+    cfg = {**DEFAULT_CFG, **(cfg or {})}
+    n = len(g["mean"])
+    mean = np.ascontiguousarray(g["mean"], np.float32)
+    scale = np.ascontiguousarray(g["scale"], np.float32)
+    quat = np.ascontiguousarray(g["quat"], np.float32)
+    opac = np.ascontiguousarray(g["opacity"], np.float32)
+    rgb = np.ascontiguousarray(g["rgb"], np.float32)
+    nrm = np.ascontiguousarray(g["normal"], np.float32)
+    out = dict(mean=np.zeros((n, 3)), scale=np.zeros((n, 3)), quat=np.zeros((n, 4)),
+               opacity=np.zeros(n), rgb=np.zeros((n, 3)), normal=np.zeros((n, 3)))
+    params = np.array([_f32(cfg["alpha_floor"]), _f32(cfg["alpha_max"]), _f32(cfg["t_min"]),
+                       _f32(cfg["sigma_mult"]), *[_f32(b) for b in cfg["bg"]], 0, 0, 0], np.float64)
+    for cam, u in zip(cams, up):
+        p = project(g, cam, cfg)
+        g2d = np.zeros((n, 13))
+        upc = np.ascontiguousarray(u, np.float64)
+        lib().or_render_grad(C.c_int64(n), C.c_int(cam["width"]), C.c_int(cam["height"]),
+                             _p(p["vis"]), _p(p["xyz"]), _p(p["uv"]), _p(p["conic"]),
+                             _p(p["prect"]), _p(p["zkey"]), _p(opac), _p(rgb), _p(nrm),
+                             _p(params), _p(upc), _p(g2d))
+        cf = cam_floats(cam)
+        lib().or_project_grad(C.c_int64(n), _p(mean), _p(scale), _p(quat), _p(cf),
+                              C.c_int(cam["width"]), C.c_int(cam["height"]),
+                              C.c_double(_f32(cfg["lowpass"])), _p(p["vis"]), _p(g2d),
+                              _p(out["mean"]), _p(out["scale"]), _p(out["quat"]),
+                              _p(out["opacity"]), _p(out["rgb"]), _p(out["normal"]))
+    return out
+
+
+def linear_loss(g: dict, cams: list, up: list, cfg: dict | None = None):
+    """L = sum_v <up_v, images_v> and the per-view renders (for finite
+    differences of :func:`render_grad`)."""
+    tot = 0.0
+    rs = []
+    for cam, u in zip(cams, up):
+        r = render(g, cam, cfg)
+        img = np.concatenate([r["rgb"], r["normal"], r["depth"][None], r["alpha"][None]])
+        tot += float((img * u).sum())
+        rs.append(r)
+    return tot, rs

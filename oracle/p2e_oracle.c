@@ -417,3 +417,219 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Gradient (R8): exact derivative of one view's images with respect to the  */
+/* raw inputs, holding every discrete decision (cull, rectangle, 3-sigma      */
+/* test, floor, stop) fixed.  The images are linearised by upstream weights:  */
+/*   L = sum gC . rgb + gN . normal + gD depth + gA alpha.                    */
+/* ------------------------------------------------------------------------ */
+
+/* per-Gaussian screen-space gradient slots */
+enum { GU = 0, GV, GA, GB, GC, GO, GZ, GR, GG, GBL, GNX, GNY, GNZ, G2D };
+
+typedef struct { int64_t g; double alpha, T, power, dx, dy; } contrib_t;
+
+/* Forward + backward of one pixel; adds into g2d[n][G2D]. */
+static void grad_pixel(int i, int j, const int64_t *list, int64_t m, const uint8_t *vis,
+                       const double *uv, const double *conic, const int32_t *prect,
+                       const double *xyz, const float *opac, const float *rgb, const float *nrm,
+                       const blend_cfg_t *bc, const double up[8], double *g2d,
+                       contrib_t **buf, int64_t *cap)
+{
+    double T = 1.0;
+    int64_t nk = 0;
+    const double pw_min = -0.5 * bc->k * bc->k;
+    const double px = i + 0.5, py = j + 0.5;
+    for (int64_t q = 0; q < m; ++q) {
+        const int64_t g = list[q];
+        if (!vis[g]) continue;
+        const int32_t *r = prect + 4 * g;
+        if (i < r[0] || i > r[1] || j < r[2] || j > r[3]) continue;
+        const double dx = px - uv[2 * g], dy = py - uv[2 * g + 1];
+        const double A = conic[3 * g], B = conic[3 * g + 1], C = conic[3 * g + 2];
+        const double power = -0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy;
+        if (power < pw_min) continue;
+        double alpha = (double)opac[g] * exp(power);
+        if (alpha > bc->alpha_max) alpha = bc->alpha_max;
+        if (alpha < bc->alpha_floor) continue;
+        const double Tn = T * (1.0 - alpha);
+        if (Tn < bc->t_min) break;
+        if (nk == *cap) {
+            *cap = *cap ? 2 * *cap : 64;
+            *buf = (contrib_t *)realloc(*buf, sizeof(contrib_t) * (size_t)*cap);
+        }
+        contrib_t c = {g, alpha, T, power, dx, dy};
+        (*buf)[nk++] = c;
+        T = Tn;
+    }
+    /* up = gC[3], gN[3], gD, gA */
+    const double bgterm = up[0] * bc->bg[0] + up[1] * bc->bg[1] + up[2] * bc->bg[2];
+    double acc = T * (bgterm - up[7]);
+    for (int64_t q = nk - 1; q >= 0; --q) {
+        const contrib_t *c = &(*buf)[q];
+        const int64_t g = c->g;
+        const double w = c->alpha * c->T;
+        const double f = up[0] * rgb[3 * g] + up[1] * rgb[3 * g + 1] + up[2] * rgb[3 * g + 2] +
+                         up[3] * nrm[3 * g] + up[4] * nrm[3 * g + 1] + up[5] * nrm[3 * g + 2] +
+                         up[6] * xyz[3 * g + 2];
+        double *G = g2d + G2D * g;
+        G[GR] += w * up[0]; G[GG] += w * up[1]; G[GBL] += w * up[2];
+        G[GNX] += w * up[3]; G[GNY] += w * up[4]; G[GNZ] += w * up[5];
+        G[GZ] += w * up[6];
+        const double dalpha = c->T * f - acc / (1.0 - c->alpha);
+        acc += w * f;
+        /* alpha = o exp(power) unless clamped at alpha_max */
+        if ((double)opac[g] * exp(c->power) > bc->alpha_max) continue;
+        const double e = exp(c->power);
+        G[GO] += dalpha * e;
+        const double dp = dalpha * c->alpha;
+        const double A = conic[3 * g], B = conic[3 * g + 1], C = conic[3 * g + 2];
+        G[GA] += dp * (-0.5 * c->dx * c->dx);
+        G[GC] += dp * (-0.5 * c->dy * c->dy);
+        G[GB] += dp * (-c->dx * c->dy);
+        G[GU] += dp * (A * c->dx + B * c->dy);
+        G[GV] += dp * (B * c->dx + C * c->dy);
+    }
+}
+
+/*
+ * or_render_grad: screen-space gradients of one view (single thread, for
+ * test scenes).  up_img: 8 planes (gC[3], gN[3], gD, gA) of H*W doubles.
+ * Writes g2d[n][13] (u, v, A, B, C, o, z, r, g, b, nx, ny, nz).
+ */
+void or_render_grad(int64_t n, int W, int H, const uint8_t *vis, const double *xyz,
+                    const double *uv, const double *conic, const int32_t *prect,
+                    const float *zkey, const float *opac, const float *rgb, const float *nrm,
+                    const double *params, const double *up_img, double *g2d)
+{
+    blend_cfg_t bc;
+    bc.alpha_floor = params[0]; bc.alpha_max = params[1]; bc.t_min = params[2];
+    bc.k = params[3]; bc.bg[0] = params[4]; bc.bg[1] = params[5]; bc.bg[2] = params[6];
+    const int64_t HW = (int64_t)H * W;
+    int64_t nv = 0;
+    for (int64_t g = 0; g < n; ++g) nv += vis[g] ? 1 : 0;
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (nv > 0 ? nv : 1));
+    nv = 0;
+    for (int64_t g = 0; g < n; ++g) if (vis[g]) order[nv++] = g;
+    g_sort_z = zkey;
+    qsort(order, (size_t)nv, sizeof(int64_t), ord_cmp);
+    for (int64_t q = 0; q < n * G2D; ++q) g2d[q] = 0.0;
+    contrib_t *buf = NULL;
+    int64_t cap = 0;
+    for (int j = 0; j < H; ++j)
+        for (int i = 0; i < W; ++i) {
+            const int64_t pix = (int64_t)j * W + i;
+            double up[8];
+            for (int ch = 0; ch < 8; ++ch) up[ch] = up_img[ch * HW + pix];
+            grad_pixel(i, j, order, nv, vis, uv, conic, prect, xyz, opac, rgb, nrm, &bc, up, g2d,
+                       &buf, &cap);
+        }
+    free(buf);
+    free(order);
+}
+
+/*
+ * or_project_grad: chain rule from the screen-space gradients g2d[n][13]
+ * of one view to the raw inputs (Eq. 3-4 backwards): adds into
+ * d_mean[3n], d_scale[3n], d_quat[4n], d_opac[n], d_rgb[3n], d_nrm[3n].
+ */
+void or_project_grad(int64_t n, const float *mean, const float *scale, const float *quat,
+                     const float *cam, int W, int H, double lowpass, const uint8_t *vis,
+                     const double *g2d, double *d_mean, double *d_scale, double *d_quat,
+                     double *d_opac, double *d_rgb, double *d_nrm)
+{
+    cam_t cm;
+    load_cam(&cm, cam, W, H);
+    (void)lowpass;
+    for (int64_t g = 0; g < n; ++g) {
+        const double *G = g2d + G2D * g;
+        d_opac[g] += G[GO];
+        for (int c = 0; c < 3; ++c) {
+            d_rgb[3 * g + c] += G[GR + c];
+            d_nrm[3 * g + c] += G[GNX + c];
+        }
+        if (!vis[g]) continue;
+        const double mx = mean[3 * g], my = mean[3 * g + 1], mz = mean[3 * g + 2];
+        double p[3];
+        for (int i = 0; i < 3; ++i)
+            p[i] = cm.T[i][0] * mx + cm.T[i][1] * my + cm.T[i][2] * mz + cm.t[i];
+        const double x = p[0], y = p[1], z = p[2];
+        const double qw = quat[4 * g], qx = quat[4 * g + 1], qy = quat[4 * g + 2], qz = quat[4 * g + 3];
+        const double qn = sqrt(qw * qw + qx * qx + qy * qy + qz * qz);
+        const double w = qw / qn, a = qx / qn, b = qy / qn, c = qz / qn;
+        double R[3][3];
+        R[0][0] = 1 - 2 * (b * b + c * c); R[0][1] = 2 * (a * b - w * c); R[0][2] = 2 * (a * c + w * b);
+        R[1][0] = 2 * (a * b + w * c); R[1][1] = 1 - 2 * (a * a + c * c); R[1][2] = 2 * (b * c - w * a);
+        R[2][0] = 2 * (a * c - w * b); R[2][1] = 2 * (b * c + w * a); R[2][2] = 1 - 2 * (a * a + b * b);
+        const double s[3] = {scale[3 * g], scale[3 * g + 1], scale[3 * g + 2]};
+        double Wm[3][3], V[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) {
+                Wm[i][k] = cm.T[i][0] * R[0][k] + cm.T[i][1] * R[1][k] + cm.T[i][2] * R[2][k];
+                V[i][k] = Wm[i][k] * s[k];
+            }
+        const double fx = cm.fx, fy = cm.fy;
+        double J[2][3] = {{fx / z, 0, -fx * x / (z * z)}, {0, fy / z, -fy * y / (z * z)}};
+        double M[2][3];
+        for (int r = 0; r < 2; ++r)
+            for (int k = 0; k < 3; ++k) M[r][k] = J[r][0] * V[0][k] + J[r][1] * V[1][k] + J[r][2] * V[2][k];
+        const double sa = M[0][0] * M[0][0] + M[0][1] * M[0][1] + M[0][2] * M[0][2] + lowpass;
+        const double sb = M[0][0] * M[1][0] + M[0][1] * M[1][1] + M[0][2] * M[1][2];
+        const double sc = M[1][0] * M[1][0] + M[1][1] * M[1][1] + M[1][2] * M[1][2] + lowpass;
+        const double det = sa * sc - sb * sb;
+        const double Q[2][2] = {{sc / det, -sb / det}, {-sb / det, sa / det}};
+        /* dL/dQ as a symmetric matrix: B enters twice in the quadratic form */
+        const double Gq[2][2] = {{G[GA], 0.5 * G[GB]}, {0.5 * G[GB], G[GC]}};
+        double QG[2][2], GM[2][2];
+        for (int r = 0; r < 2; ++r)
+            for (int k = 0; k < 2; ++k) QG[r][k] = Q[r][0] * Gq[0][k] + Q[r][1] * Gq[1][k];
+        for (int r = 0; r < 2; ++r)
+            for (int k = 0; k < 2; ++k) GM[r][k] = -(QG[r][0] * Q[0][k] + QG[r][1] * Q[1][k]);
+        const double ga = GM[0][0], gc = GM[1][1], gb = GM[0][1] + GM[1][0];
+        double dM[2][3];
+        for (int k = 0; k < 3; ++k) {
+            dM[0][k] = 2 * ga * M[0][k] + gb * M[1][k];
+            dM[1][k] = 2 * gc * M[1][k] + gb * M[0][k];
+        }
+        double dJ[2][3], dV[3][3];
+        for (int r = 0; r < 2; ++r)
+            for (int i = 0; i < 3; ++i) dJ[r][i] = dM[r][0] * V[i][0] + dM[r][1] * V[i][1] + dM[r][2] * V[i][2];
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) dV[i][k] = J[0][i] * dM[0][k] + J[1][i] * dM[1][k];
+        double dW[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) {
+                d_scale[3 * g + k] += dV[i][k] * Wm[i][k];
+                dW[i][k] = dV[i][k] * s[k];
+            }
+        double dR[3][3];
+        for (int l = 0; l < 3; ++l)
+            for (int k = 0; k < 3; ++k) dR[l][k] = cm.T[0][l] * dW[0][k] + cm.T[1][l] * dW[1][k] + cm.T[2][l] * dW[2][k];
+        /* R(w, a, b, c) -> gradient w.r.t. the unit quaternion */
+        const double dw = 2 * (-c * dR[0][1] + b * dR[0][2] + c * dR[1][0] - a * dR[1][2] - b * dR[2][0] + a * dR[2][1]);
+        const double da = 2 * (b * dR[0][1] + c * dR[0][2] + b * dR[1][0] - 2 * a * dR[1][1] - w * dR[1][2] +
+                               c * dR[2][0] + w * dR[2][1] - 2 * a * dR[2][2]);
+        const double db = 2 * (-2 * b * dR[0][0] + a * dR[0][1] + w * dR[0][2] + a * dR[1][0] + c * dR[1][2] -
+                               w * dR[2][0] + c * dR[2][1] - 2 * b * dR[2][2]);
+        const double dc = 2 * (-2 * c * dR[0][0] - w * dR[0][1] + a * dR[0][2] + w * dR[1][0] - 2 * c * dR[1][1] +
+                               b * dR[1][2] + a * dR[2][0] + b * dR[2][1]);
+        const double qh[4] = {w, a, b, c}, dq[4] = {dw, da, db, dc};
+        const double dot = qh[0] * dq[0] + qh[1] * dq[1] + qh[2] * dq[2] + qh[3] * dq[3];
+        for (int k = 0; k < 4; ++k) d_quat[4 * g + k] += (dq[k] - qh[k] * dot) / qn;
+        /* camera-space centre: through u, v, the depth image and J */
+        double dx_ = 0, dy_ = 0, dz_ = 0;
+        dx_ += G[GU] * fx / z;
+        dz_ += G[GU] * (-fx * x / (z * z));
+        dy_ += G[GV] * fy / z;
+        dz_ += G[GV] * (-fy * y / (z * z));
+        dz_ += G[GZ];
+        dz_ += dJ[0][0] * (-fx / (z * z)) + dJ[1][1] * (-fy / (z * z));
+        dx_ += dJ[0][2] * (-fx / (z * z));
+        dz_ += dJ[0][2] * (2 * fx * x / (z * z * z));
+        dy_ += dJ[1][2] * (-fy / (z * z));
+        dz_ += dJ[1][2] * (2 * fy * y / (z * z * z));
+        for (int k = 0; k < 3; ++k)
+            d_mean[3 * g + k] += cm.T[0][k] * dx_ + cm.T[1][k] * dy_ + cm.T[2][k] * dz_;
+    }
+}

@@ -1,12 +1,341 @@
-// K7/K8: backward of the renderer (filled in below the forward path).
-#include "common.cuh"
+// K7 + K8: gradient of the compositing (Eq. 1-2) and of the EWA projection
+// (Eq. 3-4) with respect to the raw Gaussian parameters, with every discrete
+// decision of the forward pass held fixed (differentiable splatting, used
+// to train the estimator end to end, Sec. 1 and 3.3).
+//
+// K7 (per tile, persistent over the non-empty-tile list): each pixel walks
+// its tile list back to front from the forward's `last`, re-deciding
+// contribution with the forward's exact arithmetic (splat.cuh).  The
+// transmittance is recovered backwards, T_k = T_{k+1} / (1 - alpha_k), from
+// the final T = 1 - alpha; no per-pixel lists are stored.  With
+// f_k = gC.c_k + gN.n_k + gD z_k and the running tail
+//   S_k = sum_{j>k} alpha_j T_j f_j + T_final (gC.bg - gA),
+// dL/dalpha_k = T_k f_k - S_k / (1 - alpha_k).  Per-splat screen-space
+// gradients (u, v, A, B, C, o, z, rgb, normal) are reduced over the warp,
+// then over the CTA in shared memory, then added to global memory.
+//
+// K8 (per Gaussian): chain rule through conic = Sigma_s^-1,
+// Sigma_s = M M^T + lowpass I, M = J T R S, R(q / |q|), and the centre
+// u = fx x / z + cx (and v), summed over the views.
+#include "splat.cuh"
 
 namespace p2e {
-size_t backward_scratch_bytes(int64_t) { return 0; }
-cudaError_t launch_render_backward(const p2e_gaussians *, const p2e_projected *, const p2e_bins *,
-                                   const Views &, const float *, const uint32_t *, const float *,
-                                   const float *, const float *, const float *, float *, float *,
-                                   float *, float *, float *, float *, void *, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+constexpr int kG2D = 16;  // floats per (view, Gaussian) screen-space gradient slot
+enum { QU = 0, QV, QA, QB, QC, QO, QZ, QR, QG, QBL, QNX, QNY, QNZ, QN };
+
+size_t backward_scratch_bytes(int64_t n_total) {
+    return ((size_t)n_total * kG2D * sizeof(float) + 255) & ~size_t(255);
 }
+
+template <int B>
+struct BwdShape {
+    static constexpr int NT = B * B;
+    static constexpr int BATCH = NT < 256 ? NT : 256;
+};
+
+template <int B>
+__global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
+    const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
+    const uint32_t *__restrict__ work, uint32_t *__restrict__ work_counter,
+    const float4 *__restrict__ xy_depth, const float4 *__restrict__ conic_op,
+    const float4 *__restrict__ rgb, const float4 *__restrict__ normal,
+    const float *__restrict__ alpha_img, const uint32_t *__restrict__ last_img,
+    const float *__restrict__ d_rgb, const float *__restrict__ d_nrm, const float *__restrict__ d_depth,
+    const float *__restrict__ d_alpha, float *__restrict__ g2d, __grid_constant__ const Views P) {
+    constexpr int NT = BwdShape<B>::NT, BATCH = BwdShape<B>::BATCH;
+    __shared__ float4 s_off[BATCH], s_co[BATCH], s_cz[BATCH], s_nr[BATCH];
+    __shared__ uint32_t s_g[BATCH];
+    __shared__ float s_acc[BATCH][QN];
+    __shared__ uint32_t s_item, s_end;
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int lx = tid % B, ly = tid / B;
+    const float lxf = (float)lx, lyf = (float)ly;
+    const float pw_min = -0.5f * P.sigma_mult * P.sigma_mult;
+    const float amax = P.alpha_max, afloor = P.alpha_floor;
+    const uint32_t n_work = work[0];
+
+    for (;;) {
+        if (tid == 0) {
+            s_item = atomicAdd(work_counter, 1u);
+            s_end = 0;
+        }
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= n_work) break;
+        const int64_t tile = work[2 + item];
+        const int vi = view_of_tile(P, tile);
+        const View &V = P.v[vi];
+        const int64_t lt = tile - V.tile_base;
+        const int ty = (int)(lt / V.tiles_x), tx = (int)(lt - (int64_t)ty * V.tiles_x);
+        const int x0 = tx * B, y0 = ty * B;
+        const int px = x0 + lx, py = y0 + ly;
+        const bool inside = px < V.W && py < V.H;
+        const uint2 r = ranges[tile];
+        const int64_t gbase = (int64_t)vi * P.n;
+        const int64_t HW = (int64_t)V.H * V.W;
+        const int64_t pix = (int64_t)py * V.W + px;
+
+        float up[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        float T = 1.f;
+        uint32_t lastp = 0;
+        if (inside) {
+            if (d_rgb)
+                for (int c = 0; c < 3; ++c) up[c] = d_rgb[3 * V.pix_base + c * HW + pix];
+            if (d_nrm)
+                for (int c = 0; c < 3; ++c) up[3 + c] = d_nrm[3 * V.pix_base + c * HW + pix];
+            if (d_depth) up[6] = d_depth[V.pix_base + pix];
+            if (d_alpha) up[7] = d_alpha[V.pix_base + pix];
+            T = 1.f - alpha_img[V.pix_base + pix];
+            lastp = last_img[V.pix_base + pix];
+            if (lastp > r.y) lastp = r.y;  // only reachable with mismatched inputs
+            atomicMax(&s_end, lastp);
+        }
+        float acc = T * (up[0] * P.bg[0] + up[1] * P.bg[1] + up[2] * P.bg[2] - up[7]);
+        __syncthreads();
+        const uint32_t end = s_end;
+        for (uint32_t bend = end; bend > r.x; bend = (bend - r.x > (uint32_t)BATCH) ? bend - BATCH : r.x) {
+            const uint32_t bstart = (bend - r.x > (uint32_t)BATCH) ? bend - BATCH : r.x;
+            const int cnt = (int)(bend - bstart);
+            for (int t = tid; t < cnt * QN; t += NT) (&s_acc[0][0])[t] = 0.f;
+            if (tid < cnt) {
+                uint32_t g = __ldg(vals + bstart + tid);
+                if (g >= (uint32_t)P.n) g = 0;
+                const float4 xy = __ldg(xy_depth + gbase + g);
+                const float4 cc = __ldg(rgb + g);
+                s_off[tid] = splat_offset(xy, x0, y0);
+                s_co[tid] = __ldg(conic_op + gbase + g);
+                s_cz[tid] = make_float4(cc.x, cc.y, cc.z, xy.z);
+                s_nr[tid] = __ldg(normal + g);
+                s_g[tid] = g;
+            }
+            __syncthreads();
+            for (int j = cnt - 1; j >= 0; --j) {
+                float q[QN];
+#pragma unroll
+                for (int c = 0; c < QN; ++c) q[c] = 0.f;
+                bool contrib = false;
+                if (inside && bstart + (uint32_t)j < lastp) {
+                    const float4 o = s_off[j], co = s_co[j];
+                    float dx, dy;
+                    splat_delta(o, lxf, lyf, dx, dy);
+                    const float power = splat_power_d(co, dx, dy);
+                    if (power >= pw_min) {
+                        float e;
+                        bool fr;
+                        const float alpha = splat_alpha(co.w, power, amax, e, fr);
+                        if (alpha >= afloor) {
+                            contrib = true;
+                            const float4 cz = s_cz[j], nr = s_nr[j];
+                            const float om = 1.f - alpha;
+                            const float Tk = T / om;
+                            const float w = alpha * Tk;
+                            const float f = up[0] * cz.x + up[1] * cz.y + up[2] * cz.z + up[3] * nr.x +
+                                            up[4] * nr.y + up[5] * nr.z + up[6] * cz.w;
+                            const float dal = Tk * f - acc / om;
+                            acc = fmaf(w, f, acc);
+                            T = Tk;
+                            q[QR] = w * up[0];
+                            q[QG] = w * up[1];
+                            q[QBL] = w * up[2];
+                            q[QNX] = w * up[3];
+                            q[QNY] = w * up[4];
+                            q[QNZ] = w * up[5];
+                            q[QZ] = w * up[6];
+                            if (fr) {
+                                q[QO] = dal * e;
+                                const float dp = dal * alpha;
+                                q[QA] = -0.5f * dp * dx * dx;
+                                q[QC] = -0.5f * dp * dy * dy;
+                                q[QB] = -dp * dx * dy;
+                                q[QU] = dp * (co.x * dx + co.y * dy);
+                                q[QV] = dp * (co.y * dx + co.z * dy);
+                            }
+                        }
+                    }
+                }
+                if (__any_sync(0xffffffffu, contrib)) {
+#pragma unroll
+                    for (int c = 0; c < QN; ++c) {
+                        float v = q[c];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        q[c] = v;
+                    }
+                    if (lane == 0)
+#pragma unroll
+                        for (int c = 0; c < QN; ++c)
+                            if (q[c] != 0.f) atomicAdd(&s_acc[j][c], q[c]);
+                }
+            }
+            __syncthreads();
+            for (int t = tid; t < cnt * QN; t += NT) {
+                const int j = t / QN, c = t - j * QN;
+                const float v = s_acc[j][c];
+                if (v != 0.f) atomicAdd(&g2d[(gbase + s_g[j]) * kG2D + c], v);
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+    }
+}
+
+// K8: screen-space gradients -> raw parameters, summed over the views.
+__global__ void __launch_bounds__(256) project_bwd_kernel(
+    const float4 *__restrict__ mean_op, const float4 *__restrict__ scale,
+    const float4 *__restrict__ quat, const float *__restrict__ g2d, float *__restrict__ d_mean,
+    float *__restrict__ d_scale, float *__restrict__ d_quat, float *__restrict__ d_opacity,
+    float *__restrict__ d_rgb_g, float *__restrict__ d_normal_g, __grid_constant__ const Views P) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= P.n) return;
+    const float4 m = mean_op[g], s4 = scale[g], q4 = quat[g];
+    float dm[3] = {0, 0, 0}, ds[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0};
+    float dop = 0.f, dc[3] = {0, 0, 0}, dn[3] = {0, 0, 0};
+    const float qn = sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+    const float iq = qn > 0.f ? 1.f / qn : 0.f;
+    const float w = q4.x * iq, a = q4.y * iq, b = q4.z * iq, c = q4.w * iq;
+    float R[3][3];
+    R[0][0] = 1.f - 2.f * (b * b + c * c); R[0][1] = 2.f * (a * b - w * c); R[0][2] = 2.f * (a * c + w * b);
+    R[1][0] = 2.f * (a * b + w * c); R[1][1] = 1.f - 2.f * (a * a + c * c); R[1][2] = 2.f * (b * c - w * a);
+    R[2][0] = 2.f * (a * c - w * b); R[2][1] = 2.f * (b * c + w * a); R[2][2] = 1.f - 2.f * (a * a + b * b);
+    const float s[3] = {s4.x, s4.y, s4.z};
+    float dR[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int vi = 0; vi < P.n_views; ++vi) {
+        const float *G = g2d + ((int64_t)vi * P.n + g) * kG2D;
+        const float4 g0 = *reinterpret_cast<const float4 *>(G);
+        const float4 g1 = *reinterpret_cast<const float4 *>(G + 4);
+        const float4 g2 = *reinterpret_cast<const float4 *>(G + 8);
+        const float g12 = G[12];
+        dop += g1.y;
+        dc[0] += g1.w; dc[1] += g2.x; dc[2] += g2.y;
+        dn[0] += g2.z; dn[1] += g2.w; dn[2] += g12;
+        if (g0.x == 0.f && g0.y == 0.f && g0.z == 0.f && g0.w == 0.f && g1.x == 0.f && g1.z == 0.f)
+            continue;  // no geometric gradient from this view
+        const View &V = P.v[vi];
+        const float *T = V.T;
+        const float x = T[0] * m.x + T[1] * m.y + T[2] * m.z + V.t[0];
+        const float y = T[3] * m.x + T[4] * m.y + T[5] * m.z + V.t[1];
+        const float z = T[6] * m.x + T[7] * m.y + T[8] * m.z + V.t[2];
+        float Wm[3][3], Vm[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) {
+                Wm[i][k] = T[3 * i] * R[0][k] + T[3 * i + 1] * R[1][k] + T[3 * i + 2] * R[2][k];
+                Vm[i][k] = Wm[i][k] * s[k];
+            }
+        const float iz = 1.f / z;
+        const float J00 = V.fx * iz, J02 = -V.fx * x * iz * iz, J11 = V.fy * iz, J12 = -V.fy * y * iz * iz;
+        float M0[3], M1[3];
+        for (int k = 0; k < 3; ++k) {
+            M0[k] = J00 * Vm[0][k] + J02 * Vm[2][k];
+            M1[k] = J11 * Vm[1][k] + J12 * Vm[2][k];
+        }
+        const float sa = M0[0] * M0[0] + M0[1] * M0[1] + M0[2] * M0[2] + P.lowpass;
+        const float sb = M0[0] * M1[0] + M0[1] * M1[1] + M0[2] * M1[2];
+        const float sc = M1[0] * M1[0] + M1[1] * M1[1] + M1[2] * M1[2] + P.lowpass;
+        const float idet = 1.f / (sa * sc - sb * sb);
+        const float Q00 = sc * idet, Q01 = -sb * idet, Q11 = sa * idet;
+        // dL/dSigma_s = -Q G Q with G = [[gA, gB/2], [gB/2, gC]]
+        const float GA = g0.z, GB = 0.5f * g0.w, GC = g1.x;
+        const float t00 = Q00 * GA + Q01 * GB, t01 = Q00 * GB + Q01 * GC;
+        const float t10 = Q01 * GA + Q11 * GB, t11 = Q01 * GB + Q11 * GC;
+        const float ga = -(t00 * Q00 + t01 * Q01);
+        const float gc = -(t10 * Q01 + t11 * Q11);
+        const float gb = -2.f * (t00 * Q01 + t01 * Q11);
+        float dM0[3], dM1[3];
+        for (int k = 0; k < 3; ++k) {
+            dM0[k] = 2.f * ga * M0[k] + gb * M1[k];
+            dM1[k] = 2.f * gc * M1[k] + gb * M0[k];
+        }
+        // M = J V
+        const float dJ00 = dM0[0] * Vm[0][0] + dM0[1] * Vm[0][1] + dM0[2] * Vm[0][2];
+        const float dJ02 = dM0[0] * Vm[2][0] + dM0[1] * Vm[2][1] + dM0[2] * Vm[2][2];
+        const float dJ11 = dM1[0] * Vm[1][0] + dM1[1] * Vm[1][1] + dM1[2] * Vm[1][2];
+        const float dJ12 = dM1[0] * Vm[2][0] + dM1[1] * Vm[2][1] + dM1[2] * Vm[2][2];
+        float dV[3][3];
+        for (int k = 0; k < 3; ++k) {
+            dV[0][k] = J00 * dM0[k];
+            dV[1][k] = J11 * dM1[k];
+            dV[2][k] = J02 * dM0[k] + J12 * dM1[k];
+        }
+        float dW[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) {
+                ds[k] += dV[i][k] * Wm[i][k];
+                dW[i][k] = dV[i][k] * s[k];
+            }
+        for (int l = 0; l < 3; ++l)
+            for (int k = 0; k < 3; ++k) dR[l][k] += T[l] * dW[0][k] + T[3 + l] * dW[1][k] + T[6 + l] * dW[2][k];
+        // centre, depth image and Jacobian -> camera coordinates -> mean
+        float dx = g0.x * V.fx * iz + dJ02 * (-V.fx * iz * iz);
+        float dy = g0.y * V.fy * iz + dJ12 * (-V.fy * iz * iz);
+        float dz = g0.x * (-V.fx * x * iz * iz) + g0.y * (-V.fy * y * iz * iz) + g1.z +
+                   dJ00 * (-V.fx * iz * iz) + dJ11 * (-V.fy * iz * iz) +
+                   dJ02 * (2.f * V.fx * x * iz * iz * iz) + dJ12 * (2.f * V.fy * y * iz * iz * iz);
+        for (int k = 0; k < 3; ++k) dm[k] += T[k] * dx + T[3 + k] * dy + T[6 + k] * dz;
+    }
+    // R(w, a, b, c) -> unit quaternion -> raw quaternion
+    const float gw = 2.f * (-c * dR[0][1] + b * dR[0][2] + c * dR[1][0] - a * dR[1][2] - b * dR[2][0] + a * dR[2][1]);
+    const float gx = 2.f * (b * dR[0][1] + c * dR[0][2] + b * dR[1][0] - 2.f * a * dR[1][1] - w * dR[1][2] +
+                            c * dR[2][0] + w * dR[2][1] - 2.f * a * dR[2][2]);
+    const float gy = 2.f * (-2.f * b * dR[0][0] + a * dR[0][1] + w * dR[0][2] + a * dR[1][0] + c * dR[1][2] -
+                            w * dR[2][0] + c * dR[2][1] - 2.f * b * dR[2][2]);
+    const float gz = 2.f * (-2.f * c * dR[0][0] - w * dR[0][1] + a * dR[0][2] + w * dR[1][0] - 2.f * c * dR[1][1] +
+                            b * dR[1][2] + a * dR[2][0] + b * dR[2][1]);
+    const float dot = w * gw + a * gx + b * gy + c * gz;
+    dq[0] = (gw - w * dot) * iq;
+    dq[1] = (gx - a * dot) * iq;
+    dq[2] = (gy - b * dot) * iq;
+    dq[3] = (gz - c * dot) * iq;
+    for (int k = 0; k < 3; ++k) {
+        d_mean[3 * g + k] = dm[k];
+        d_scale[3 * g + k] = ds[k];
+        d_rgb_g[3 * g + k] = dc[k];
+        d_normal_g[3 * g + k] = dn[k];
+    }
+    for (int k = 0; k < 4; ++k) d_quat[4 * g + k] = dq[k];
+    d_opacity[g] = dop;
+}
+
+int device_sms();
+
+template <int B>
+static cudaError_t launch_bwd(const p2e_gaussians *g, const p2e_projected *proj, const p2e_bins *bins,
+                              const Views &P, const float *alpha, const uint32_t *last,
+                              const float *d_rgb, const float *d_normal, const float *d_depth,
+                              const float *d_alpha, float *g2d, cudaStream_t st) {
+    const int grid = device_sms() * (B == 8 ? 8 : (B == 16 ? 2 : 1));
+    blend_bwd_kernel<B><<<grid, BwdShape<B>::NT, 0, st>>>(
+        (const uint2 *)bins->ranges, bins->vals[bins->result], bins->tile_work, bins->tile_work + 1,
+        (const float4 *)proj->xy_depth, (const float4 *)proj->conic_op, (const float4 *)g->rgb,
+        (const float4 *)g->normal, alpha, last, d_rgb, d_normal, d_depth, d_alpha, g2d, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_backward(const p2e_gaussians *g, const p2e_projected *proj,
+                                   const p2e_bins *bins, const Views &P, const float *alpha,
+                                   const uint32_t *last, const float *d_rgb, const float *d_normal,
+                                   const float *d_depth, const float *d_alpha, float *d_mean,
+                                   float *d_scale, float *d_quat, float *d_opacity, float *d_rgb_g,
+                                   float *d_normal_g, void *scratch, cudaStream_t st) {
+    if (P.n == 0) return cudaSuccess;
+    float *g2d = (float *)scratch;
+    cudaError_t e = cudaMemsetAsync(g2d, 0, (size_t)P.n * P.n_views * kG2D * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    if (P.total_tiles > 0) {
+        if ((e = cudaMemsetAsync(bins->tile_work + 1, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+        switch (P.tile) {
+            case 8: e = launch_bwd<8>(g, proj, bins, P, alpha, last, d_rgb, d_normal, d_depth, d_alpha, g2d, st); break;
+            case 16: e = launch_bwd<16>(g, proj, bins, P, alpha, last, d_rgb, d_normal, d_depth, d_alpha, g2d, st); break;
+            case 32: e = launch_bwd<32>(g, proj, bins, P, alpha, last, d_rgb, d_normal, d_depth, d_alpha, g2d, st); break;
+            default: return cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    project_bwd_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, st>>>(
+        (const float4 *)g->mean_op, (const float4 *)g->scale, (const float4 *)g->quat, g2d, d_mean,
+        d_scale, d_quat, d_opacity, d_rgb_g, d_normal_g, P);
+    return cudaGetLastError();
+}
+
 }  // namespace p2e

@@ -27,7 +27,7 @@
 // any image size.
 #include <algorithm>
 
-#include "common.cuh"
+#include "splat.cuh"
 
 namespace p2e {
 
@@ -62,14 +62,6 @@ struct BlendSmem {
 
 __device__ __forceinline__ uint32_t row_bits(int x0, int x1) {  // bits x0..x1 (x1 <= 31)
     return (x1 >= 31 ? 0xffffffffu : ((1u << (x1 + 1)) - 1u)) & ~((1u << x0) - 1u);
-}
-
-// power = -1/2 d^T Sigma_s^-1 d at tile-relative pixel (x, y) (same
-// expression in every phase so that the decisions agree)
-__device__ __forceinline__ float splat_power(const float4 &o, const float4 &co, float x, float y) {
-    const float dx = (x - o.z) + o.x;
-    const float dy = (y - o.w) + o.y;
-    return -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
 }
 
 template <int B>
@@ -172,9 +164,7 @@ __global__ void __launch_bounds__(BlendShape<B>::NT) blend_kernel(
                 const float4 xy = __ldg(xy_depth + gbase + g);
                 const ushort4 rc = __ldg(rect + gbase + g);
                 const float4 cc = __ldg(rgb + g);
-                const int packed = __float_as_int(xy.w);
-                const int iu = (int)(int16_t)(packed & 0xffff), iv = packed >> 16;
-                sm.off[t] = make_float4(0.5f - xy.x, 0.5f - xy.y, (float)(iu - x0), (float)(iv - y0));
+                sm.off[t] = splat_offset(xy, x0, y0);
                 sm.co[t] = __ldg(conic_op + gbase + g);
                 sm.cz[t] = make_float4(cc.x, cc.y, cc.z, xy.z);
                 sm.nr[t] = __ldg(normal + g);
@@ -217,7 +207,9 @@ __global__ void __launch_bounds__(BlendShape<B>::NT) blend_kernel(
                         const float4 o = sm.off[j], co = sm.co[j];
                         const float power = splat_power(o, co, lxf, lyf);
                         if (power < pw_min) continue;
-                        const float alpha = fminf(amax, co.w * __expf(power));
+                        float e;
+                        bool fr;
+                        const float alpha = splat_alpha(co.w, power, amax, e, fr);
                         if (alpha < afloor) continue;
                         const float wgt = alpha * t_;
                         const float4 cz = sm.cz[j], nr = sm.nr[j];
@@ -269,7 +261,9 @@ __global__ void __launch_bounds__(BlendShape<B>::NT) blend_kernel(
                             const float4 o = sm.off[j], co = sm.co[j];
                             const float power = splat_power(o, co, lxf, lyf);
                             if (power < pw_min) continue;
-                            const float alpha = fminf(amax, co.w * __expf(power));
+                            float e;
+                            bool fr;
+                            const float alpha = splat_alpha(co.w, power, amax, e, fr);
                             if (alpha < afloor) continue;
                             const float Tn = T * (1.f - alpha);
                             if (Tn < tmin) {

@@ -261,3 +261,67 @@ class Renderer:
             self.capacity = int(k * 1.5) + 1024
             self._ensure(g.n * len(cams), tt)
         raise _lib.P2EError("p2e_sort_bin", _lib.P2E_ERR_CAPACITY)
+
+
+# ---------------------------------------------------------------- backward
+def p2e_render_backward(g: GaussianSet, proj: Projected, bins: Bins, cams: list, cfg: dict | None,
+                        alpha: torch.Tensor, last: torch.Tensor, d_rgb=None, d_normal=None,
+                        d_depth=None, d_alpha=None, stream=None) -> dict:
+    """Gradients (w.r.t. mean, scale, raw quaternion, opacity, rgb, normal)
+    of <upstream, images> for the render that produced ``alpha``/``last``."""
+    lib = _lib.load()
+    ca = make_cameras(cams)
+    gs, ps, cf = g.c_struct(), proj.c_struct(), make_config(cfg)
+    n = g.n
+    dev = g.mean_op.device
+    out = dict(mean=torch.empty((n, 3), dtype=torch.float32, device=dev),
+               scale=torch.empty((n, 3), dtype=torch.float32, device=dev),
+               quat=torch.empty((n, 4), dtype=torch.float32, device=dev),
+               opacity=torch.empty((n,), dtype=torch.float32, device=dev),
+               rgb=torch.empty((n, 3), dtype=torch.float32, device=dev),
+               normal=torch.empty((n, 3), dtype=torch.float32, device=dev))
+    sb = int(lib.p2e_scratch_bytes(_lib.P2E_SCRATCH_BACKWARD, n * len(cams), 0))
+    scratch = torch.empty((sb + 256,), dtype=torch.uint8, device=dev)
+    sp = (scratch.data_ptr() + 255) & ~255
+    check("p2e_render_backward", lib.p2e_render_backward(
+        C.byref(gs), C.byref(ps), C.byref(bins.struct), ca, len(cams), C.byref(cf), _ptr(alpha),
+        _ptr(last), _ptr(d_rgb), _ptr(d_normal), _ptr(d_depth), _ptr(d_alpha), _ptr(out["mean"]),
+        _ptr(out["scale"]), _ptr(out["quat"]), _ptr(out["opacity"]), _ptr(out["rgb"]),
+        _ptr(out["normal"]), C.c_void_p(sp), sb, _stream(stream)))
+    return out
+
+
+class _RenderFn(torch.autograd.Function):
+    """Differentiable render of float4-SoA Gaussian tensors (see
+    :func:`render_differentiable`)."""
+
+    @staticmethod
+    def forward(ctx, mean_op, scale, quat, rgb, normal, cams, cfg):
+        gs = GaussianSet(mean_op.detach().contiguous(), scale.detach().contiguous(),
+                         quat.detach().contiguous(), rgb.detach().contiguous(),
+                         normal.detach().contiguous())
+        r = Renderer(cfg, capacity=max(1 << 16, 4 * gs.n * len(cams)), device=mean_op.device)
+        img = r.render(gs, cams)
+        ctx.state = (gs, r, img, cams, cfg)
+        return img.rgb, img.normal, img.depth, img.alpha
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_normal, g_depth, g_alpha):
+        gs, r, img, cams, cfg = ctx.state
+        c = lambda t: None if t is None else t.contiguous()  # noqa: E731
+        d = p2e_render_backward(gs, r.proj, r.bins, cams, r.cfg, img.alpha, img.last, c(g_rgb),
+                                c(g_normal), c(g_depth), c(g_alpha))
+        z = torch.zeros((gs.n, 1), dtype=torch.float32, device=gs.mean_op.device)
+        ctx.state = None
+        return (torch.cat([d["mean"], d["opacity"][:, None]], 1), torch.cat([d["scale"], z], 1),
+                d["quat"], torch.cat([d["rgb"], z], 1), torch.cat([d["normal"], z], 1), None, None)
+
+
+def render_differentiable(mean_op, scale, quat, rgb, normal, cams: list, cfg: dict | None = None):
+    """Render views from float4-SoA Gaussian tensors with autograd support.
+
+    Returns planar (rgb, normal, depth, alpha) tensors, views concatenated
+    (see :class:`Images`).  Gradients flow to all five inputs (the opacity
+    is column 3 of ``mean_op``; the unused fourth columns get zeros).
+    """
+    return _RenderFn.apply(mean_op, scale, quat, rgb, normal, cams, {**DEFAULT_CONFIG, **(cfg or {})})
