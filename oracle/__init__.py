@@ -29,7 +29,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "p2e_oracle.c")
+_SRCS = [os.path.join(_HERE, "p2e_oracle.c"), os.path.join(_HERE, "knn_pca.c")]
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -48,9 +48,10 @@ DEFAULT_FLAGS = dict(flag_power=1e-4, flag_alpha=1e-6, flag_t=1e-7)
 def build(force: bool = False) -> str:
     """Compile the C oracle (gcc, OpenMP, no FMA contraction)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    stale = not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(s) for s in _SRCS)
+    if force or stale:
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-               "-ffp-contract=off", "-fno-fast-math", "-o", _LIB + ".tmp", _SRC, "-lm"]
+               "-ffp-contract=off", "-fno-fast-math", "-o", _LIB + ".tmp", *_SRCS, "-lm"]
         subprocess.check_call(cmd)
         os.replace(_LIB + ".tmp", _LIB)
     return _LIB
@@ -218,3 +219,50 @@ def linear_loss(g: dict, cams: list, up: list, cfg: dict | None = None):
         tot += float((img * u).sum())
         rs.append(r)
     return tot, rs
+
+
+# ---------------------------------------------------------------- kNN-PCA
+def knn(xyz) -> tuple:
+    """Exact 16 nearest other points (FP64 distance, ties by index).
+    Returns ``(idx int64 (n,16), d2 float64 (n,16))``."""
+    p = np.ascontiguousarray(xyz, np.float32)
+    n = len(p)
+    idx = np.zeros((n, 16), np.int64)
+    d2 = np.zeros((n, 16))
+    lib().or_knn(C.c_int64(n), _p(p), _p(idx), _p(d2))
+    return idx, d2
+
+
+def pca(xyz, idx, kappa: float = 1.0, flat: float = 0.1) -> dict:
+    """Neighbour covariance, its eigen-decomposition and the Gaussian it
+    implies (scale, unit quaternion, normal)."""
+    p = np.ascontiguousarray(xyz, np.float32)
+    n = len(p)
+    ix = np.ascontiguousarray(idx, np.int64)
+    out = dict(cov=np.zeros((n, 6)), lam=np.zeros((n, 3)), scale=np.zeros((n, 3)),
+               quat=np.zeros((n, 4)), normal=np.zeros((n, 3)))
+    lib().or_pca(C.c_int64(n), _p(p), _p(ix), C.c_double(kappa), C.c_double(flat), _p(out["cov"]),
+                 _p(out["lam"]), _p(out["scale"]), _p(out["quat"]), _p(out["normal"]))
+    return out
+
+
+def estimate_pca(xyz, rgb, opacity: float = 0.9, kappa: float = 1.0, flat: float = 0.1) -> dict:
+    """kNN-PCA Gaussian set of a coloured point cloud (fp32, renderer input)."""
+    idx, _ = knn(xyz)
+    e = pca(xyz, idx, kappa, flat)
+    n = len(xyz)
+    return dict(mean=np.asarray(xyz, np.float32), scale=e["scale"].astype(np.float32),
+                quat=e["quat"].astype(np.float32), opacity=np.full(n, opacity, np.float32),
+                rgb=np.asarray(rgb, np.float32), normal=e["normal"].astype(np.float32))
+
+
+def sigma_of(scale, quat) -> np.ndarray:
+    """Sigma = R diag(s^2) R^T for each row (quaternions normalised)."""
+    q = np.asarray(quat, np.float64)
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    R = np.stack([np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+                  np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+                  np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], 1)
+    s2 = np.asarray(scale, np.float64) ** 2
+    return np.einsum("nij,nj,nkj->nik", R, s2, R)
