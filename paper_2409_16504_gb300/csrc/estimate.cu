@@ -1,10 +1,483 @@
-// K9-K11: point-to-ellipsoid estimation (filled in below the renderer).
+// K9 + K10: per-point Gaussian estimation from the point cloud (the
+// "preprocess" stage: point cloud in, one elliptical Gaussian per point out,
+// Sec. 3.1-3.2).  The closed-form path sizes each splat from the local
+// covariance of its 16 nearest neighbours (the prior splatting practice the
+// paper contrasts with, Sec. 2.1); the learned path (mlp.cu) then corrects
+// that frame with a per-point network.
+//
+//   bbox      one reduction: bounding box and centroid of the cloud
+//   grid      uniform cells (about two cells per point at most), counting
+//             sort of the points by cell (count, scan, scatter)
+//   knn+pca   one thread per point, points taken in cell order: exact 16
+//             nearest other points by searching rings of cells until the
+//             16th distance is below the distance to the next ring (ties by
+//             index); then the neighbours' covariance, a cyclic Jacobi
+//             eigen-decomposition, scale = sqrt(lambda) (smallest axis at
+//             least 0.1 of the middle one), proper rotation -> quaternion
+//             (Shepperd), normal = smallest axis turned away from the
+//             centroid.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace p2e {
-size_t estimate_scratch_bytes(int64_t) { return 256; }
-cudaError_t launch_estimate(const float *, const float *, int64_t, int32_t, const void *, float,
-                            p2e_gaussians *, uint32_t *, void *, int, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+constexpr int kK = 16;
+
+struct GridParams {
+    float lo[3];
+    float h, inv_h;
+    int dim[3];
+    int64_t ncell;
+    float cen[3];
+};
+
+struct EstScratch {
+    int *bbox;            // 6 ordered-int min/max
+    double *sum;          // 3
+    GridParams *gp;
+    uint32_t *cell;       // n
+    uint32_t *order;      // n
+    uint32_t *counts;     // ncell_max
+    uint32_t *fill;       // ncell_max
+    uint32_t *start;      // ncell_max + 1
+    uint64_t *scan_state; // scan tiles + 1
+    uint32_t *ticket;
+    uint32_t *knn;        // n * 16 (when the caller passes none)
+    void *mlp_scratch;    // see mlp.cu
+    int64_t ncell_max, scan_tiles;
+};
+
+__host__ __device__ inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+static int64_t ncell_cap(int64_t n) { return std::max<int64_t>(2 * n, 1 << 16); }
+constexpr int kScanT = 1024;
+size_t mlp_scratch_bytes(int64_t n);
+
+static size_t est_layout(int64_t n, void *base, EstScratch *S) {
+    const int64_t nc = ncell_cap(n);
+    const int64_t st = (nc + 1 + kScanT - 1) / kScanT;
+    size_t off = 0;
+    char *b = (char *)base;
+    auto take = [&](size_t bytes) {
+        void *p = b ? (void *)(b + off) : nullptr;
+        off += al256(bytes);
+        return p;
+    };
+    EstScratch s;
+    s.bbox = (int *)take(6 * sizeof(int));
+    s.sum = (double *)take(3 * sizeof(double));
+    s.gp = (GridParams *)take(sizeof(GridParams));
+    s.cell = (uint32_t *)take((size_t)n * 4);
+    s.order = (uint32_t *)take((size_t)n * 4);
+    s.counts = (uint32_t *)take((size_t)nc * 4);
+    s.fill = (uint32_t *)take((size_t)nc * 4);
+    s.start = (uint32_t *)take((size_t)(nc + 1) * 4);
+    s.scan_state = (uint64_t *)take((size_t)(st + 1) * 8);
+    s.ticket = (uint32_t *)take(64);
+    s.knn = (uint32_t *)take((size_t)n * kK * 4);
+    s.mlp_scratch = take(mlp_scratch_bytes(n));
+    s.ncell_max = nc;
+    s.scan_tiles = st;
+    if (S) *S = s;
+    return off;
 }
+
+size_t estimate_scratch_bytes(int64_t n) { return est_layout(n, nullptr, nullptr); }
+
+__device__ __forceinline__ int ord_of(float f) {
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float float_of(int o) { return __int_as_float(o >= 0 ? o : o ^ 0x7fffffff); }
+
+__global__ void __launch_bounds__(256) bbox_kernel(const float4 *__restrict__ xyz, int64_t n, EstScratch S) {
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float sm[3] = {0, 0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 p = __ldg(xyz + i);
+        const float v[3] = {p.x, p.y, p.z};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            mn[k] = fminf(mn[k], v[k]);
+            mx[k] = fmaxf(mx[k], v[k]);
+            sm[k] += v[k];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[k] = fminf(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
+            mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
+            sm[k] += __shfl_xor_sync(0xffffffffu, sm[k], o);
+        }
+    __shared__ float s_mn[8][3], s_mx[8][3], s_sm[8][3];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < 3; ++k) { s_mn[w][k] = mn[k]; s_mx[w][k] = mx[k]; s_sm[w][k] = sm[k]; }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        const int k = threadIdx.x;
+        float a = INFINITY, b = -INFINITY;
+        double c = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            a = fminf(a, s_mn[q][k]);
+            b = fmaxf(b, s_mx[q][k]);
+            c += s_sm[q][k];
+        }
+        atomicMin(&S.bbox[k], ord_of(a));
+        atomicMax(&S.bbox[3 + k], ord_of(b));
+        atomicAdd(&S.sum[k], c);
+    }
+}
+
+__global__ void grid_setup_kernel(int64_t n, EstScratch S) {
+    GridParams g;
+    float ext[3], emax = 0.f;
+    for (int k = 0; k < 3; ++k) {
+        g.lo[k] = float_of(S.bbox[k]);
+        ext[k] = float_of(S.bbox[3 + k]) - g.lo[k];
+        emax = fmaxf(emax, ext[k]);
+        g.cen[k] = (float)(S.sum[k] / (double)n);
+    }
+    emax = fmaxf(emax, 1e-30f);
+    double vol = 1.0;
+    for (int k = 0; k < 3; ++k) vol *= fmax((double)ext[k], 1e-3 * (double)emax);
+    // about two cells per point: half the spacing of 4 points per cell
+    double h = 0.5 * cbrt(vol * 4.0 / (double)n);
+    for (int it = 0; it < 64; ++it) {
+        double cells = 1.0;
+        for (int k = 0; k < 3; ++k) {
+            double d = floor(ext[k] / h) + 1.0;
+            if (d > 1024.0) d = 1024.0;
+            cells *= d;
+        }
+        bool fits = cells <= (double)S.ncell_max;
+        for (int k = 0; k < 3; ++k) fits = fits && (ext[k] / h) < 1023.0;
+        if (fits) break;
+        h *= 1.25;
+    }
+    g.h = (float)h;
+    g.inv_h = (float)(1.0 / h);
+    g.ncell = 1;
+    for (int k = 0; k < 3; ++k) {
+        g.dim[k] = (int)fmin(1024.0, floor(ext[k] * g.inv_h) + 1.0);
+        g.ncell *= g.dim[k];
+    }
+    *S.gp = g;
+}
+
+__device__ __forceinline__ void cell_of(const GridParams &g, float x, float y, float z, int c[3]) {
+    const float v[3] = {x, y, z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int q = (int)floorf((v[k] - g.lo[k]) * g.inv_h);
+        c[k] = min(max(q, 0), g.dim[k] - 1);
+    }
+}
+
+__global__ void __launch_bounds__(256) cell_count_kernel(const float4 *__restrict__ xyz, int64_t n, EstScratch S) {
+    const GridParams g = *S.gp;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 p = __ldg(xyz + i);
+        int c[3];
+        cell_of(g, p.x, p.y, p.z, c);
+        const uint32_t id = (uint32_t)(((int64_t)c[2] * g.dim[1] + c[1]) * g.dim[0] + c[0]);
+        S.cell[i] = id;
+        atomicAdd(&S.counts[id], 1u);
+    }
+}
+
+__device__ __forceinline__ uint64_t ld_acq64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_rel64(uint64_t *p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Exclusive scan of counts[0, len) into start[0, len] (start[len] = total),
+// single pass with decoupled look-back; 1024 elements per block.
+__global__ void __launch_bounds__(256) scan_counts_kernel(const uint32_t *__restrict__ counts, int64_t len,
+                                                          uint32_t *__restrict__ start, EstScratch S,
+                                                          int32_t *status) {
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_w[8];
+    __shared__ uint64_t s_prefix;
+    if (threadIdx.x == 0) s_tile = atomicAdd(S.ticket, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t base = tile * kScanT + threadIdx.x * 4;
+    uint32_t v[4], loc = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = base + k < len ? counts[base + k] : 0u;
+        loc += v[k];
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[w] = x;
+    __syncthreads();
+    uint32_t wpre = 0, tot = 0;
+    for (int q = 0; q < 8; ++q) {
+        if (q < w) wpre += s_w[q];
+        tot += s_w[q];
+    }
+    if (threadIdx.x == 0) {
+        uint64_t prefix = 0;
+        if (tile == 0) {
+            st_rel64(&S.scan_state[0], (2ull << 62) | tot);
+        } else {
+            st_rel64(&S.scan_state[tile], (1ull << 62) | tot);
+            int64_t p = tile - 1;
+            uint32_t spins = 0;
+            while (p >= 0) {
+                const uint64_t wd = ld_acq64(&S.scan_state[p]);
+                if ((wd >> 62) == 0) {
+                    if (++spins > kSpinLimit) { atomicExch(status, (int32_t)P2E_ERR_TIMEOUT); break; }
+                    backoff(spins);
+                    continue;
+                }
+                prefix += wd & ((1ull << 62) - 1);
+                if ((wd >> 62) == 2) break;
+                --p;
+            }
+            st_rel64(&S.scan_state[tile], (2ull << 62) | (prefix + tot));
+        }
+        s_prefix = prefix;
+    }
+    __syncthreads();
+    uint32_t run = (uint32_t)s_prefix + wpre + x - loc;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (base + k <= len) start[base + k] = run;
+        run += v[k];
+    }
+}
+
+__global__ void __launch_bounds__(256) scatter_kernel(int64_t n, EstScratch S) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = S.cell[i];
+        S.order[S.start[c] + atomicAdd(&S.fill[c], 1u)] = (uint32_t)i;
+    }
+}
+
+// sorted insertion of (d, j) into best[] (static indices only, so the list
+// stays in registers)
+__device__ __forceinline__ void knn_insert(float (&bd)[kK], uint32_t (&bi)[kK], float d, uint32_t j) {
+#pragma unroll
+    for (int k = 0; k < kK; ++k) {
+        const bool lt = d < bd[k] || (d == bd[k] && j < bi[k]);
+        const float td = lt ? bd[k] : d;
+        const uint32_t tj = lt ? bi[k] : j;
+        bd[k] = lt ? d : bd[k];
+        bi[k] = lt ? j : bi[k];
+        d = td;
+        j = tj;
+    }
+}
+
+// cyclic Jacobi on a symmetric 3x3 (fp32); V columns are eigenvectors
+__device__ void jacobi3f(float A[3][3], float V[3][3]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) V[i][j] = i == j ? 1.f : 0.f;
+    const float tr = fabsf(A[0][0]) + fabsf(A[1][1]) + fabsf(A[2][2]);
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        const float off = fabsf(A[0][1]) + fabsf(A[0][2]) + fabsf(A[1][2]);
+        if (!(off > 1e-7f * tr)) break;
+#pragma unroll
+        for (int pq = 0; pq < 3; ++pq) {
+            const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+            if (A[p][q] == 0.f) continue;
+            const float theta = (A[q][q] - A[p][p]) / (2.f * A[p][q]);
+            const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+            const float c = rsqrtf(t * t + 1.f), s = t * c;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float akp = A[k][p], akq = A[k][q];
+                A[k][p] = c * akp - s * akq;
+                A[k][q] = s * akp + c * akq;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float apk = A[p][k], aqk = A[q][k];
+                A[p][k] = c * apk - s * aqk;
+                A[q][k] = s * apk + c * aqk;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float vkp = V[k][p], vkq = V[k][q];
+                V[k][p] = c * vkp - s * vkq;
+                V[k][q] = s * vkp + c * vkq;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ float4 shepperd_f(const float R[3][3]) {
+    const float tr = R[0][0] + R[1][1] + R[2][2];
+    float w, x, y, z;
+    if (tr >= R[0][0] && tr >= R[1][1] && tr >= R[2][2]) {
+        const float s = 2.f * sqrtf(1.f + tr);
+        w = 0.25f * s; x = (R[2][1] - R[1][2]) / s; y = (R[0][2] - R[2][0]) / s; z = (R[1][0] - R[0][1]) / s;
+    } else if (R[0][0] >= R[1][1] && R[0][0] >= R[2][2]) {
+        const float s = 2.f * sqrtf(fmaxf(1.f + R[0][0] - R[1][1] - R[2][2], 1e-30f));
+        w = (R[2][1] - R[1][2]) / s; x = 0.25f * s; y = (R[0][1] + R[1][0]) / s; z = (R[0][2] + R[2][0]) / s;
+    } else if (R[1][1] >= R[2][2]) {
+        const float s = 2.f * sqrtf(fmaxf(1.f + R[1][1] - R[0][0] - R[2][2], 1e-30f));
+        w = (R[0][2] - R[2][0]) / s; x = (R[0][1] + R[1][0]) / s; y = 0.25f * s; z = (R[1][2] + R[2][1]) / s;
+    } else {
+        const float s = 2.f * sqrtf(fmaxf(1.f + R[2][2] - R[0][0] - R[1][1], 1e-30f));
+        w = (R[1][0] - R[0][1]) / s; x = (R[0][2] + R[2][0]) / s; y = (R[1][2] + R[2][1]) / s; z = 0.25f * s;
+    }
+    return make_float4(w, x, y, z);
+}
+
+__global__ void __launch_bounds__(128) knn_pca_kernel(const float4 *__restrict__ xyz,
+                                                      const float4 *__restrict__ rgb, int64_t n,
+                                                      float opacity, EstScratch S, uint32_t *__restrict__ knn_out,
+                                                      float4 *__restrict__ mean_op, float4 *__restrict__ scale,
+                                                      float4 *__restrict__ quat, float4 *__restrict__ rgb_out,
+                                                      float4 *__restrict__ normal) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const GridParams g = *S.gp;
+    const uint32_t i = S.order[t];
+    const float4 p = __ldg(xyz + i);
+    int c0[3];
+    cell_of(g, p.x, p.y, p.z, c0);
+    float bd[kK];
+    uint32_t bi[kK];
+#pragma unroll
+    for (int k = 0; k < kK; ++k) { bd[k] = INFINITY; bi[k] = 0xffffffffu; }
+    const int rmax = max(g.dim[0], max(g.dim[1], g.dim[2]));
+    for (int r = 0; r <= rmax; ++r) {
+        for (int dz = -r; dz <= r; ++dz) {
+            const int cz = c0[2] + dz;
+            if (cz < 0 || cz >= g.dim[2]) continue;
+            for (int dy = -r; dy <= r; ++dy) {
+                const int cy = c0[1] + dy;
+                if (cy < 0 || cy >= g.dim[1]) continue;
+                const bool shell = (dz == -r || dz == r || dy == -r || dy == r);
+                for (int dx = -r; dx <= r; dx += (shell ? 1 : 2 * r)) {
+                    const int cx = c0[0] + dx;
+                    if (cx >= 0 && cx < g.dim[0]) {
+                        const uint32_t c = (uint32_t)(((int64_t)cz * g.dim[1] + cy) * g.dim[0] + cx);
+                        const uint32_t s = S.start[c], e = S.start[c + 1];
+                        for (uint32_t q = s; q < e; ++q) {
+                            const uint32_t j = S.order[q];
+                            if (j == i) continue;
+                            const float4 pj = __ldg(xyz + j);
+                            const float ex = pj.x - p.x, ey = pj.y - p.y, ez = pj.z - p.z;
+                            const float d = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                            if (d < bd[kK - 1] || (d == bd[kK - 1] && j < bi[kK - 1])) knn_insert(bd, bi, d, j);
+                        }
+                    }
+                    if (r == 0) break;
+                }
+            }
+        }
+        // any point outside rings 0..r is at least r*h away (with margin for
+        // the rounding of the cell assignment)
+        const float bound = fmaxf(0.f, (float)r * g.h * (1.f - 1e-4f) - 1e-6f);
+        if (bi[kK - 1] != 0xffffffffu && bd[kK - 1] < bound * bound) break;
+    }
+    if (knn_out)
+#pragma unroll
+        for (int k = 0; k < kK; ++k) knn_out[(int64_t)i * kK + k] = bi[k];
+    // covariance of the neighbours about their centroid
+    float m[3] = {0, 0, 0};
+    float4 q[kK];
+#pragma unroll
+    for (int k = 0; k < kK; ++k) {
+        q[k] = __ldg(xyz + bi[k]);
+        m[0] += q[k].x; m[1] += q[k].y; m[2] += q[k].z;
+    }
+    for (int k = 0; k < 3; ++k) m[k] *= (1.f / kK);
+    float C[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+    for (int k = 0; k < kK; ++k) {
+        const float d[3] = {q[k].x - m[0], q[k].y - m[1], q[k].z - m[2]};
+        for (int a = 0; a < 3; ++a)
+            for (int b = a; b < 3; ++b) C[a][b] = fmaf(d[a], d[b], C[a][b]);
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b) {
+            C[a][b] *= (1.f / kK);
+            C[b][a] = C[a][b];
+        }
+    float V[3][3];
+    jacobi3f(C, V);
+    float lam[3] = {C[0][0], C[1][1], C[2][2]};
+    int o[3] = {0, 1, 2};
+    if (lam[o[1]] > lam[o[0]]) { int tt = o[0]; o[0] = o[1]; o[1] = tt; }
+    if (lam[o[2]] > lam[o[1]]) { int tt = o[1]; o[1] = o[2]; o[2] = tt; }
+    if (lam[o[1]] > lam[o[0]]) { int tt = o[0]; o[0] = o[1]; o[1] = tt; }
+    float R[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) R[k][a] = V[k][o[a]];
+    const float sg = (p.x - g.cen[0]) * R[0][2] + (p.y - g.cen[1]) * R[1][2] + (p.z - g.cen[2]) * R[2][2];
+    if (sg < 0.f)
+        for (int k = 0; k < 3; ++k) R[k][2] = -R[k][2];
+    const float det = R[0][0] * (R[1][1] * R[2][2] - R[1][2] * R[2][1]) -
+                      R[0][1] * (R[1][0] * R[2][2] - R[1][2] * R[2][0]) +
+                      R[0][2] * (R[1][0] * R[2][1] - R[1][1] * R[2][0]);
+    if (det < 0.f)
+        for (int k = 0; k < 3; ++k) R[k][1] = -R[k][1];
+    float s[3];
+    for (int a = 0; a < 3; ++a) s[a] = sqrtf(fmaxf(lam[o[a]], 0.f));
+    s[2] = fmaxf(s[2], 0.1f * s[1]);
+    mean_op[i] = make_float4(p.x, p.y, p.z, opacity);
+    scale[i] = make_float4(s[0], s[1], s[2], 0.f);
+    quat[i] = shepperd_f(R);
+    rgb_out[i] = __ldg(rgb + i);
+    normal[i] = make_float4(R[0][2], R[1][2], R[2][2], 0.f);
+}
+
+__global__ void est_init_kernel(EstScratch S) {
+    if (threadIdx.x < 3) {
+        S.bbox[threadIdx.x] = ord_of(INFINITY);
+        S.bbox[3 + threadIdx.x] = ord_of(-INFINITY);
+        S.sum[threadIdx.x] = 0.0;
+    }
+}
+
+cudaError_t launch_mlp_estimate(const float *xyz, const float *rgb, int64_t n, const void *mlp,
+                                const uint32_t *knn, p2e_gaussians *out, void *scratch, int num_sms,
+                                cudaStream_t st);
+
+cudaError_t launch_estimate(const float *xyz, const float *rgb, int64_t n, int32_t mode,
+                            const void *mlp, float pca_opacity, p2e_gaussians *out,
+                            uint32_t *knn_idx, void *scratch, int num_sms, cudaStream_t st) {
+    EstScratch S;
+    est_layout(n, scratch, &S);
+    cudaError_t e;
+    // bbox starts at (+inf, -inf); sums, counts, fill, tickets, look-back at 0
+    est_init_kernel<<<1, 32, 0, st>>>(S);
+    if ((e = cudaMemsetAsync(S.counts, 0, (size_t)S.ncell_max * 4, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(S.fill, 0, (size_t)S.ncell_max * 4, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(S.scan_state, 0, (size_t)(S.scan_tiles + 1) * 8, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(S.ticket, 0, 64, st)) != cudaSuccess) return e;
+    int32_t *status = (int32_t *)(S.ticket + 8);
+    const int g1 = num_sms * 4;
+    bbox_kernel<<<num_sms * 2, 256, 0, st>>>((const float4 *)xyz, n, S);
+    grid_setup_kernel<<<1, 1, 0, st>>>(n, S);
+    cell_count_kernel<<<g1, 256, 0, st>>>((const float4 *)xyz, n, S);
+    scan_counts_kernel<<<(unsigned)S.scan_tiles, 256, 0, st>>>(S.counts, S.ncell_max, S.start, S, status);
+    scatter_kernel<<<g1, 256, 0, st>>>(n, S);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    uint32_t *knn = knn_idx ? knn_idx : S.knn;
+    knn_pca_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
+        (const float4 *)xyz, (const float4 *)rgb, n, pca_opacity, S, knn, (float4 *)out->mean_op,
+        (float4 *)out->scale, (float4 *)out->quat, (float4 *)out->rgb, (float4 *)out->normal);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (mode == 1) return launch_mlp_estimate(xyz, rgb, n, mlp, knn, out, S.mlp_scratch, num_sms, st);
+    return cudaSuccess;
+}
+
 }  // namespace p2e

@@ -1,0 +1,81 @@
+"""GPU kNN-PCA estimation (p2e_estimate, mode 0) against the FP64 oracle.
+
+kNN: the neighbour sets must be equal, except where fp32 and fp64 order
+two candidates differently; the accepted mismatch is one whose neighbours'
+FP64 distances agree with the oracle's sorted distances to 1e-6 relative.
+PCA: Sigma = R diag(s^2) R^T within 1e-4 of max|Sigma| per point (Sigma, not
+(s, q): eigenvectors are ill-conditioned near equal eigenvalues), unit
+normals parallel, with the orientation checked where (p - c) . n is clear.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(xyz, rgb, opacity=0.9):
+    from paper_2409_16504_gb300.estimate import Estimator, cloud_tensors
+    a, b = cloud_tensors(xyz, rgb)
+    n = len(xyz)
+    knn = torch.zeros((n, 16), dtype=torch.int32, device="cuda")
+    gs = Estimator(n)(a, b, opacity=opacity, knn=knn)
+    torch.cuda.synchronize()
+    return {k: getattr(gs, k).cpu().numpy() for k in ("mean_op", "scale", "quat", "rgb", "normal")}, \
+        knn.cpu().numpy().astype(np.int64)
+
+
+def _check(xyz, rgb):
+    xyz = np.asarray(xyz, np.float32)
+    got, gidx = _run(xyz, rgb)
+    idx, d2 = oracle.knn(xyz)
+    P = xyz.astype(np.float64)
+    same = (np.sort(gidx, 1) == np.sort(idx, 1)).all(1)
+    bad = np.nonzero(~same)[0]
+    for i in bad:
+        dg = np.sort(((P[gidx[i]] - P[i]) ** 2).sum(1))
+        np.testing.assert_allclose(dg, d2[i], rtol=1e-6, atol=1e-20)
+    assert len(bad) <= max(5, len(xyz) // 2000)
+    e = oracle.pca(xyz, idx)
+    ok = same
+    S_ref = oracle.sigma_of(e["scale"][ok], e["quat"][ok])
+    S_got = oracle.sigma_of(got["scale"][ok, :3], got["quat"][ok])
+    err = np.abs(S_got - S_ref).max((1, 2)) / np.abs(S_ref).max((1, 2))
+    assert np.percentile(err, 99.9) < 1e-4 and err.max() < 1e-3, err.max()
+    cos = np.abs((got["normal"][ok, :3] * e["normal"][ok]).sum(1))
+    # the normal is ill-defined only when the two smallest eigenvalues tie
+    gap = (e["lam"][ok, 1] - e["lam"][ok, 2]) / e["lam"][ok, 0]
+    assert (cos[gap > 1e-3] > 1 - 1e-3).all()
+    cen = P.mean(0)
+    side = ((P[ok] - cen) * e["normal"][ok]).sum(1)
+    clear = (np.abs(side) > 1e-4) & (gap > 1e-3)
+    assert ((got["normal"][ok, :3] * e["normal"][ok]).sum(1)[clear] > 0).all()
+    np.testing.assert_array_equal(got["mean_op"][:, :3], xyz)
+    assert (got["mean_op"][:, 3] == np.float32(0.9)).all()
+    np.testing.assert_array_equal(got["rgb"][:, :3], np.asarray(rgb, np.float32))
+    return len(bad)
+
+
+def test_estimate_pca_humanoid_200k():
+    xyz, rgb, _, _ = scenes.humanoid_cloud(200_000, seed=3)
+    nbad = _check(xyz, rgb)
+    print("kNN ambiguous points", nbad)
+
+
+def test_estimate_pca_sphere_and_minimum_size():
+    g = scenes.sphere_cloud(4096, seed=1)
+    _check(g["mean"], g["rgb"])
+    rng = np.random.default_rng(0)
+    p = rng.standard_normal((17, 3)).astype(np.float32)
+    _check(p, rng.random((17, 3)))
+
+
+def test_estimate_rejects_too_few_points():
+    from paper_2409_16504_gb300 import P2EError
+    from paper_2409_16504_gb300.estimate import Estimator, cloud_tensors
+    a, b = cloud_tensors(np.zeros((10, 3)), np.zeros((10, 3)))
+    with pytest.raises(P2EError):
+        Estimator(10)(a, b)
