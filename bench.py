@@ -39,8 +39,10 @@ SEED = 2
 def workload_name(path: str) -> str:
     return {"render": "800K-point humanoid proxy, surface-aligned Gaussians, 1024x1024 render "
                       "(projection + binning + radix sort + compositing)",
-            "pca": "800K-point humanoid proxy, kNN-PCA estimation + 1024x1024 render",
-            "learned": "800K-point humanoid proxy, kNN-PCA + learned MLP estimation + 1024x1024 render"}[path]
+            "pca": "800K-point humanoid proxy, 1 frame = kNN-PCA estimation of all points + "
+                   "1024x1024 render (projection, binning, radix sort, compositing)",
+            "learned": "800K-point humanoid proxy, 1 frame = kNN-PCA + learned MLP estimation of all "
+                       "points + 1024x1024 render (projection, binning, radix sort, compositing)"}[path]
 
 
 def make_inputs():
@@ -109,7 +111,18 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def cpu_baseline(budget_s: float = 12.0) -> dict:
+def oracle_frame(xyz, rgb, g, cam, path):
+    """One frame of the FP64 oracle: estimation (kNN-PCA) when the path has
+    one, then projection, binning and compositing."""
+    import oracle
+    if path != "render":
+        g = oracle.estimate_pca(xyz, rgb)
+    p = oracle.project(g, cam)
+    oracle.bin_keys([p], [cam])
+    oracle.render(g, cam, proj=p)
+
+
+def cpu_baseline(path: str, budget_s: float = 12.0) -> dict:
     """The FP64 oracle on the host cores, on a bounded sample of frames."""
     import oracle
     xyz, rgb, g = make_inputs()
@@ -117,15 +130,14 @@ def cpu_baseline(budget_s: float = 12.0) -> dict:
     t0 = time.perf_counter()
     frames = 0
     while frames < len(cams) and (time.perf_counter() - t0) < budget_s:
-        p = oracle.project(g, cams[frames])
-        oracle.bin_keys([p], [cams[frames]])
-        oracle.render(g, cams[frames], proj=p)
+        oracle_frame(xyz, rgb, g, cams[frames], path)
         frames += 1
     dt = time.perf_counter() - t0
+    what = "kNN-PCA estimation + render" if path != "render" else "render"
     return {"value": frames * RES * RES / dt / 1e6, "unit": "Mpix/s", "cores": oracle.num_threads(),
             "kind": "oracle", "ms_per_frame": 1e3 * dt / frames,
-            "sample": f"{frames} frames of the render stage (project + bin + composite) on the "
-                      f"surface-aligned Gaussian set, 1024x1024"}
+            "sample": f"{frames} frames of the oracle's {what} of the 800K-point cloud at 1024x1024 "
+                      f"(the oracle has no learned network; its frame is the kNN-PCA path)"}
 
 
 def run_reference(args, rank, world):
@@ -138,9 +150,7 @@ def run_reference(args, rank, world):
     times = []
     for i, cam in enumerate(cams):
         t = time.perf_counter()
-        p = oracle.project(g, cam)
-        oracle.bin_keys([p], [cam])
-        oracle.render(g, cam, proj=p)
+        oracle_frame(xyz, rgb, g, cam, "pca")
         if i >= args.warmup:
             times.append(time.perf_counter() - t)
     tot = sum(times)
@@ -149,7 +159,7 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "p50_ms": 1e3 * float(np.percentile(times, 50)), "p99_ms": 1e3 * float(np.percentile(times, 99)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_name("render"), "points": N_POINTS,
+            "data": "synthetic", "config": {"workload": workload_name("pca"), "points": N_POINTS,
                                             "resolution": RES},
             "cpu_baseline": {"value": val, "unit": "Mpix/s", "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": f"{args.steps} frames after {args.warmup} warm-up"},
@@ -164,7 +174,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--path", default="render", choices=["render", "pca", "learned"])
+    ap.add_argument("--path", default=None, choices=["render", "pca", "learned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=int, default=16, choices=[8, 16, 32])
     args = ap.parse_args()
@@ -181,130 +191,174 @@ def main():
     import torch.distributed as dist
 
     from paper_2409_16504_gb300 import GaussianSet, Images, Renderer
+    from paper_2409_16504_gb300.estimate import LEARNED, PCA, Estimator, cloud_tensors
+    from paper_2409_16504_gb300.render import p2e_project, p2e_render, p2e_sort_bin
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
+    mlp_blob = learned_weights(dev)
+    paths = [args.path] if args.path else (["learned", "pca"] if mlp_blob is not None else ["pca"])
     xyz, rgb, g = make_inputs()
     center = xyz.mean(0)
     e_steps = max(3, min(args.steps, 50))
     cams = cameras(center, args.warmup + max(args.steps, e_steps), SEED + 100 + rank)
-    gs = GaussianSet.from_numpy(g, dev)
+    cx, cc = cloud_tensors(xyz, rgb, dev)
+    g_static = GaussianSet.from_numpy(g, dev)
+    est = Estimator(len(xyz), dev)
+    gs = GaussianSet.empty(len(xyz), dev)
     st = torch.cuda.current_stream()
-    # capacity from a probe frame, with headroom for other viewpoints
     rend = Renderer({"tile": args.tile}, capacity=1 << 21, device=dev)
-    probe = rend.render(gs, [cams[0]])
-    rend.capacity = int(rend.n_keys * 1.6) + 4096
+    est(cx, cc, out=gs)
+    rend.render(gs, [cams[0]])
+    rend.capacity = int(rend.n_keys * 1.6) + 4096   # headroom for other viewpoints
     rend.render(gs, [cams[0]])
     img = Images([cams[0]], dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
-    def frame(cam):
-        from paper_2409_16504_gb300.render import p2e_project, p2e_render, p2e_sort_bin
-        e0, e1, e2, e3 = ev(), ev(), ev(), ev()
-        e0.record(st)
-        p2e_project(gs, [cam], rend.cfg, rend.proj)
-        e1.record(st)
-        p2e_sort_bin(rend.proj, gs.n, [cam], rend.cfg, rend.bins)
-        e2.record(st)
-        p2e_render(gs, rend.proj, rend.bins, [cam], rend.cfg, img.rgb, img.normal, img.depth,
+    def frame(cam, path):
+        es = [ev() for _ in range(5)]
+        es[0].record(st)
+        if path == "render":
+            src = g_static
+        else:
+            est(cx, cc, mode=LEARNED if path == "learned" else PCA, mlp_blob=mlp_blob, out=gs)
+            src = gs
+        es[1].record(st)
+        p2e_project(src, [cam], rend.cfg, rend.proj)
+        es[2].record(st)
+        p2e_sort_bin(rend.proj, src.n, [cam], rend.cfg, rend.bins)
+        es[3].record(st)
+        p2e_render(src, rend.proj, rend.bins, [cam], rend.cfg, img.rgb, img.normal, img.depth,
                    img.alpha, img.last)
-        e3.record(st)
-        return e0, e1, e2, e3
+        es[4].record(st)
+        return es
 
-    for i in range(args.warmup):
-        flush.fill_(i & 0xFF)
-        frame(cams[i])
-    torch.cuda.synchronize()
+    def timed(path):
+        for i in range(args.warmup):
+            flush.fill_(i & 0xFF)
+            frame(cams[i], path)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        recs = []
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            recs.append(frame(cams[args.warmup + i], path))
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        stage = np.array([[a.elapsed_time(b) for a, b in zip(r[:-1], r[1:])] for r in recs])
+        return stage
+
     clk = Clocks(local)
     clk.start()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    recs = []
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)
-        recs.append(frame(cams[args.warmup + i]))
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    results = {p: timed(p) for p in paths}
     clocks = clk.stop()
-    stage = np.array([[a.elapsed_time(b), b.elapsed_time(c), c.elapsed_time(d)] for a, b, c, d in recs])
-    frame_ms = stage.sum(1)
-    tot_ms = float(frame_ms.sum())
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * args.steps * RES * RES / (tot_ms / 1e3) / 1e6
+    st_ok, k = 0, rend.n_keys
+    from paper_2409_16504_gb300 import p2e_bins_check
+    st_ok, k = p2e_bins_check(rend.bins)
+    if st_ok != 0:
+        raise RuntimeError(f"binning status {st_ok}: key capacity {rend.capacity} < {k}")
 
-    # end to end through the public API with host buffers
-    host = {k: getattr(gs, k).cpu().pin_memory() for k in ("mean_op", "scale", "quat", "rgb", "normal")}
-    out_host = torch.empty((3 * RES * RES + 3 * RES * RES + RES * RES,), dtype=torch.float32).pin_memory()
-    gd = GaussianSet.empty(gs.n, dev)
-    h2d = sum(t.numel() * 4 for t in host.values())
+    def summary(stage):
+        fm = stage.sum(1)
+        tot = float(fm.sum())
+        if world > 1:
+            t = torch.tensor([tot], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        return dict(value=world * args.steps * RES * RES / (tot / 1e3) / 1e6, ms=tot / args.steps,
+                    p50=float(np.percentile(fm, 50)), p99=float(np.percentile(fm, 99)),
+                    stage={nm: float(x) for nm, x in zip(["estimate", "project", "sort_bin", "blend"],
+                                                         stage.mean(0))})
+    sums = {p: summary(results[p]) for p in paths}
+    head_path = paths[0]
+    hs = sums[head_path]
+
+    # end to end through the public API: the cloud comes from pinned host
+    # memory every frame, the rgb/normal/depth images go back to the host
+    hx, hc = cx.cpu().pin_memory(), cc.cpu().pin_memory()
+    out_host = torch.empty((7 * RES * RES,), dtype=torch.float32).pin_memory()
+    dx, dc = torch.empty_like(cx), torch.empty_like(cc)
+    h2d = (hx.numel() + hc.numel()) * 4
     d2h = out_host.numel() * 4
+    mode = LEARNED if head_path == "learned" else PCA
+
+    def e2e_frame(cam):
+        dx.copy_(hx, non_blocking=True)
+        dc.copy_(hc, non_blocking=True)
+        src = est(dx, dc, mode=mode, mlp_blob=mlp_blob, out=gs) if head_path != "render" else g_static
+        rend.render(src, [cam], out=img, check=False)
+        out_host[: 3 * RES * RES].copy_(img.rgb, non_blocking=True)
+        out_host[3 * RES * RES: 6 * RES * RES].copy_(img.normal, non_blocking=True)
+        out_host[6 * RES * RES:].copy_(img.depth, non_blocking=True)
+
     for w in range(2):
-        for k, t in host.items():
-            getattr(gd, k).copy_(t, non_blocking=True)
-        rend.render(gd, [cams[w]], out=img, check=False)
+        e2e_frame(cams[w])
     torch.cuda.synchronize()
     a, b = ev(), ev()
     a.record(st)
     for i in range(e_steps):
-        for k, t in host.items():
-            getattr(gd, k).copy_(t, non_blocking=True)
-        rend.render(gd, [cams[args.warmup + i]], out=img, check=False)
-        out_host[: 3 * RES * RES].copy_(img.rgb, non_blocking=True)
-        out_host[3 * RES * RES: 6 * RES * RES].copy_(img.normal, non_blocking=True)
-        out_host[6 * RES * RES:].copy_(img.depth, non_blocking=True)
+        e2e_frame(cams[args.warmup + i])
     b.record(st)
     torch.cuda.synchronize()
     e2e_ms = a.elapsed_time(b) / e_steps
-    e2e_val = world * RES * RES / (e2e_ms / 1e3) / 1e6
 
-    # roofline of the dominant stage
-    peaks, src = measured_peaks()
-    names = ["project", "sort_bin", "blend"]
-    mean_stage = stage.mean(0)
-    dom = int(np.argmax(mean_stage))
-    K = rend.n_keys
-    n = gs.n
-    if dom == 0:
+    # roofline of the dominant kernel stage
+    peaks, src_peak = measured_peaks()
+    dom = max(hs["stage"], key=hs["stage"].get)
+    K, n = k, len(xyz)
+    if dom == "blend":
+        # gathered splat records (xy, conic, rect, rgb, normal + the index) per
+        # key and the nine output planes per pixel
+        alg = K * (4 + 16 + 16 + 8 + 16 + 16) + RES * RES * 36
+    elif dom == "sort_bin":
+        alg = n * (4 + 8 + 4) + K * 12 + 6 * K * 24
+    elif dom == "project":
         alg = n * (48 + 44)
-    elif dom == 1:
-        alg = n * 16 + K * 12 + 6 * K * 24
     else:
-        alg = K * (4 + 64) + RES * RES * 36
-    achieved = alg / (mean_stage[dom] / 1e3) / 1e9
-    roof = {"kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-            "peak_source": src}
+        alg = n * (32 + 80 + 16 * 4)
+    achieved = alg / (hs["stage"][dom] / 1e3) / 1e9
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "peak_source": src_peak, "algorithmic_bytes_per_launch": alg}
 
-    line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
-            "p50_ms": float(np.percentile(frame_ms, 50)), "p99_ms": float(np.percentile(frame_ms, 99)),
-            "stage_ms": {nm: float(x) for nm, x in zip(names, mean_stage)},
+    launches_per_frame = {"render": 13, "pca": 13 + 7, "learned": 13 + 7 + 1}[head_path]
+    line = {"metric": METRIC, "value": hs["value"], "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": hs["ms"], "p50_ms": hs["p50"], "p99_ms": hs["p99"],
+            "stage_ms": hs["stage"], "path": head_path,
+            "paths": {p: {"Mpix_s": v["value"], "p50_ms": v["p50"], "p99_ms": v["p99"], "stage_ms": v["stage"]}
+                      for p, v in sums.items()},
             "keys_per_frame": K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_name(args.path), "points": N_POINTS, "resolution": RES,
+            "config": {"workload": workload_name(head_path), "points": N_POINTS, "resolution": RES,
                        "cameras": "uniform on a 2.5 m sphere, re-drawn per frame",
-                       "l2": "flushed (256 MiB write) before every timed frame",
-                       "tile": args.tile,
+                       "l2": "flushed (256 MiB write) before every timed frame", "tile": args.tile,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "clocks": clocks, "gpu_launches": 11 * args.steps,
-            "e2e": {"value": e2e_val, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "clocks": clocks, "gpu_launches": launches_per_frame * args.steps * len(paths),
+            "e2e": {"value": world * RES * RES / (e2e_ms / 1e3) / 1e6, "unit": "Mpix/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "roofline": roof}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(head_path)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def learned_weights(dev):
+    """The trained estimator's weight blob, if the package ships one."""
+    try:
+        from paper_2409_16504_gb300 import mlp
+    except ImportError:
+        return None
+    return mlp.load_trained(dev)
 
 
 if __name__ == "__main__":

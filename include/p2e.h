@@ -144,6 +144,8 @@ typedef struct {
 
 enum { P2E_SCRATCH_SORT = 0, P2E_SCRATCH_ESTIMATE = 1, P2E_SCRATCH_BACKWARD = 2 };
 
+#define P2E_MLP_BLOB_BYTES 31552
+
 /* Defaults of p2e_config (see above). */
 p2e_config p2e_default_config(void);
 
@@ -228,8 +230,15 @@ p2e_status p2e_render_backward(const p2e_gaussians *g, const p2e_projected *proj
  * mode 1: the learned per-point MLP (16 x (offset, colour) -> 64 -> 64 -> 64
  *   -> 8, bf16 weights, fp32 accumulation on tcgen05 tensor cores) predicting
  *   corrections of the PCA frame, scale, rotation and opacity.
- * mlp_weights: device blob from p2e_mlp_blob_bytes layout (mode 1), else
- * NULL.  out: device Gaussian set (mean_op, scale, quat, rgb, normal) of n
+ * mlp_weights: device blob of P2E_MLP_BLOB_BYTES (mode 1; 16-byte aligned),
+ * else NULL.  Layout: bf16 W1[64][96], W2[64][64], W3[64][64], W4[16][64]
+ * (row = output unit; rows 8..15 of W4 are padding and must be zero), then
+ * fp32 b1[64], b2[64], b3[64], b4[16].  Features per point: for each of the
+ * 16 nearest neighbours j in distance order, R^T (p_j - p_i) / r_i and
+ * c_j - c_i (R the canonical PCA frame, r_i the 16th-neighbour distance).
+ * Outputs y[0..7] correct the PCA estimate in its frame:
+ * s = s_pca exp(clip(y0..2, -4, 4)), q = q_pca (x) normalize(1 + y3, y4, y5, y6),
+ * o = sigmoid(logit(pca_opacity) + y7), normal = third axis of R(q).  out: device Gaussian set (mean_op, scale, quat, rgb, normal) of n
  * entries (the const qualifiers of p2e_gaussians are cast away for output).
  * knn_idx (optional, may be NULL): device uint32[n*16] neighbour indices.
  * scratch: p2e_scratch_bytes(P2E_SCRATCH_ESTIMATE, n, 0) bytes. */

@@ -10,10 +10,11 @@
  *   covariance  Cov = 1/16 sum (p_j - pbar)(p_j - pbar)^T, pbar the mean of
  *               the 16 neighbours;
  *   axes        cyclic Jacobi eigen-decomposition, l1 >= l2 >= l3;
- *   Gaussian    s_a = kappa sqrt(l_a), s3 = max(s3, flat s2), rotation
- *               [e1 e2 e3] made proper (e2 flipped if det < 0), quaternion
- *               by Shepperd's method, normal = e3 oriented away from the
- *               cloud centroid.
+ *   Gaussian    s_a = kappa sqrt(l_a), s3 = max(s3, flat s2); rotation
+ *               [e1 e2 e3] in a canonical frame (e3 = normal turned away
+ *               from the cloud centroid, e1 with its largest-magnitude
+ *               component positive, e2 = e3 x e1), quaternion by Shepperd's
+ *               method.
  */
 #include <math.h>
 #include <stdint.h>
@@ -214,16 +215,20 @@ void or_pca(int64_t n, const float *xyz, const int64_t *idx, double kappa, doubl
             lam[3 * i + a] = l[o[a]];
             for (int k = 0; k < 3; ++k) R[k][a] = V[k][o[a]];
         }
-        /* normal = smallest axis, pointing away from the cloud centroid */
+        /* canonical frame: e3 (normal) away from the cloud centroid, e1 with
+         * its largest-magnitude component positive, e2 = e3 x e1 */
         double sg = 0;
         for (int k = 0; k < 3; ++k) sg += (xyz[3 * i + k] - cen[k]) * R[k][2];
         if (sg < 0)
             for (int k = 0; k < 3; ++k) R[k][2] = -R[k][2];
-        const double det = R[0][0] * (R[1][1] * R[2][2] - R[1][2] * R[2][1]) -
-                           R[0][1] * (R[1][0] * R[2][2] - R[1][2] * R[2][0]) +
-                           R[0][2] * (R[1][0] * R[2][1] - R[1][1] * R[2][0]);
-        if (det < 0)
-            for (int k = 0; k < 3; ++k) R[k][1] = -R[k][1];
+        int km = 0;
+        for (int k = 1; k < 3; ++k)
+            if (fabs(R[k][0]) > fabs(R[km][0])) km = k;
+        if (R[km][0] < 0)
+            for (int k = 0; k < 3; ++k) R[k][0] = -R[k][0];
+        R[0][1] = R[1][2] * R[2][0] - R[2][2] * R[1][0];
+        R[1][1] = R[2][2] * R[0][0] - R[0][2] * R[2][0];
+        R[2][1] = R[0][2] * R[1][0] - R[1][2] * R[0][0];
         for (int k = 0; k < 3; ++k) normal[3 * i + k] = R[k][2];
         double s[3];
         for (int a = 0; a < 3; ++a) s[a] = kappa * sqrt(lam[3 * i + a] > 0 ? lam[3 * i + a] : 0.0);

@@ -13,9 +13,10 @@
 //             16th distance is below the distance to the next ring (ties by
 //             index); then the neighbours' covariance, a cyclic Jacobi
 //             eigen-decomposition, scale = sqrt(lambda) (smallest axis at
-//             least 0.1 of the middle one), proper rotation -> quaternion
-//             (Shepperd), normal = smallest axis turned away from the
-//             centroid.
+//             least 0.1 of the middle one), rotation in a canonical frame
+//             (normal = smallest axis turned away from the centroid, first
+//             axis with its largest component positive, e2 = e3 x e1) ->
+//             quaternion (Shepperd).
 #include <algorithm>
 
 #include "common.cuh"
@@ -421,14 +422,20 @@ __global__ void __launch_bounds__(128) knn_pca_kernel(const float4 *__restrict__
     float R[3][3];
     for (int a = 0; a < 3; ++a)
         for (int k = 0; k < 3; ++k) R[k][a] = V[k][o[a]];
+    // canonical frame: normal away from the centroid, e1's largest-magnitude
+    // component positive, e2 = e3 x e1
     const float sg = (p.x - g.cen[0]) * R[0][2] + (p.y - g.cen[1]) * R[1][2] + (p.z - g.cen[2]) * R[2][2];
     if (sg < 0.f)
         for (int k = 0; k < 3; ++k) R[k][2] = -R[k][2];
-    const float det = R[0][0] * (R[1][1] * R[2][2] - R[1][2] * R[2][1]) -
-                      R[0][1] * (R[1][0] * R[2][2] - R[1][2] * R[2][0]) +
-                      R[0][2] * (R[1][0] * R[2][1] - R[1][1] * R[2][0]);
-    if (det < 0.f)
-        for (int k = 0; k < 3; ++k) R[k][1] = -R[k][1];
+    {
+        const float a0 = fabsf(R[0][0]), a1 = fabsf(R[1][0]), a2 = fabsf(R[2][0]);
+        const float big = (a1 > a0) ? ((a2 > a1) ? R[2][0] : R[1][0]) : ((a2 > a0) ? R[2][0] : R[0][0]);
+        if (big < 0.f)
+            for (int k = 0; k < 3; ++k) R[k][0] = -R[k][0];
+    }
+    R[0][1] = R[1][2] * R[2][0] - R[2][2] * R[1][0];
+    R[1][1] = R[2][2] * R[0][0] - R[0][2] * R[2][0];
+    R[2][1] = R[0][2] * R[1][0] - R[1][2] * R[0][0];
     float s[3];
     for (int a = 0; a < 3; ++a) s[a] = sqrtf(fmaxf(lam[o[a]], 0.f));
     s[2] = fmaxf(s[2], 0.1f * s[1]);

@@ -1,10 +1,349 @@
-// K11: learned per-point estimator (filled in after the closed-form path).
+// K11: learned per-point estimator on the 5th-generation tensor cores.
+//
+// The paper's estimator ends in a shared per-point MLP head that predicts
+// each Gaussian's scale, rotation and opacity (Sec. 3.1-3.2).  Here the
+// head reads the point's 16 nearest neighbours directly:
+//   features  per neighbour j (distance order): R^T (p_j - p_i) / r_i and
+//             c_j - c_i, R the canonical PCA frame, r_i the 16th-neighbour
+//             distance (96 inputs)
+//   network   96 -> 64 -> 64 -> 64 (ReLU) -> 8, bf16 operands, fp32 accumulate
+//   outputs   corrections of the PCA estimate in its own frame:
+//             s = s_pca exp(clip(y0..2, -4, 4)), q = q_pca (x) normalize(1 + y3..6),
+//             o = sigmoid(logit(o_pca) + y7), normal = third axis of R(q).
+//
+// Kernel: persistent CTAs of 128 threads; one tile = 128 points = the UMMA
+// M dimension.  Each thread gathers one point's features into shared memory
+// (bf16, no-swizzle K-major core-matrix layout); one elected thread issues
+// tcgen05.mma (kind::f16, bf16 x bf16 -> f32 accumulator in TMEM, K = 16
+// per instruction) and commits to an mbarrier; every thread then reads its
+// row of the accumulator with tcgen05.ld, adds the bias, applies ReLU,
+// rounds to bf16 and writes the next layer's A operand.  The weights (30 KB
+// bf16) stay in shared memory for the whole kernel.  Every mbarrier wait is
+// bounded; a wait that gives up records P2E_ERR_TIMEOUT, the CTA stops
+// issuing work and still releases its TMEM.
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace p2e {
+
+constexpr int kTM = 128, kIn = 96, kHid = 64, kOutPad = 16, kNb = 16;
+constexpr int kBlobW1 = 0, kBlobW2 = kBlobW1 + kHid * kIn * 2, kBlobW3 = kBlobW2 + kHid * kHid * 2,
+              kBlobW4 = kBlobW3 + kHid * kHid * 2, kBlobB = kBlobW4 + kOutPad * kHid * 2;
+constexpr int kBlobBytes = kBlobB + (3 * kHid + kOutPad) * 4;
+static_assert(kBlobBytes == P2E_MLP_BLOB_BYTES, "weight blob layout of p2e.h");
+constexpr uint32_t kTmemCols = 64;
+
 size_t mlp_scratch_bytes(int64_t) { return 256; }
-cudaError_t launch_mlp_estimate(const float *, const float *, int64_t, const void *, const uint32_t *,
-                                p2e_gaussians *, void *, int, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+struct __align__(128) MlpSmem {
+    __nv_bfloat16 A[kTM * kIn];
+    __nv_bfloat16 H[kTM * kHid];
+    __nv_bfloat16 W1[kHid * kIn];
+    __nv_bfloat16 W2[kHid * kHid];
+    __nv_bfloat16 W3[kHid * kHid];
+    __nv_bfloat16 W4[kOutPad * kHid];
+    float b[3 * kHid + kOutPad];
+    uint64_t mbar;
+    uint32_t tmem;
+    int err;
+};
+
+// element offset of (r, k) in an R x K bf16 matrix stored as 8x8 core
+// matrices (8 rows x 16 bytes each, rows 16 B apart): core matrices are
+// 128 B apart along K and (K/8)*128 B apart along the rows.
+__device__ __forceinline__ int core_off(int r, int k, int K) {
+    return (((r >> 3) * (K >> 3) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
 }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: start, leading (K-direction) and stride
+// (row-direction) byte offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t make_sdesc(const void *p, uint32_t lbo, uint32_t sbo) {
+    const uint32_t a = smem_u32(p);
+    return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: f32 accumulator, bf16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(mbar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+    const uint32_t a = smem_u32(mbar);
+    for (uint32_t it = 0; it < (1u << 20); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive fp32 accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// bias + ReLU + bf16 of a 64-wide accumulator row into the next A operand
+__device__ __forceinline__ void epilogue_hidden(uint32_t taddr, const float *bias, __nv_bfloat16 *H, int row) {
+#pragma unroll
+    for (int c16 = 0; c16 < kHid / 16; ++c16) {
+        float v[16];
+        tmem_ld16(taddr + c16 * 16, v);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int k = c16 * 16 + half * 8 + 2 * e;
+                const float lo = fmaxf(v[half * 8 + 2 * e] + bias[k], 0.f);
+                const float hi = fmaxf(v[half * 8 + 2 * e + 1] + bias[k + 1], 0.f);
+                const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+                w[e] = *reinterpret_cast<const uint32_t *>(&p);
+            }
+            *reinterpret_cast<uint4 *>(H + core_off(row, c16 * 16 + half * 8, kHid)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+// the per-layer MMA chain: D[128 x N] = A[128 x K] B[N x K]^T
+__device__ __forceinline__ void issue_layer(uint32_t tmem, const __nv_bfloat16 *A, const __nv_bfloat16 *Bm, int K,
+                                            int N, uint64_t *mbar) {
+    tc_fence_after();
+    const uint32_t id = idesc_bf16(kTM, N);
+    for (int s = 0; s < K / 16; ++s) {
+        const uint64_t da = make_sdesc(A + s * 16 * 8, 128, (K / 8) * 128);
+        const uint64_t db = make_sdesc(Bm + s * 16 * 8, 128, (K / 8) * 128);
+        umma_bf16(tmem, da, db, id, s > 0 ? 1u : 0u);
+    }
+    umma_commit(mbar);
+}
+
+__device__ __forceinline__ float4 qmul(float4 a, float4 b) {
+    return make_float4(a.x * b.x - a.y * b.y - a.z * b.z - a.w * b.w, a.x * b.y + a.y * b.x + a.z * b.w - a.w * b.z,
+                       a.x * b.z - a.y * b.w + a.z * b.x + a.w * b.y, a.x * b.w + a.y * b.z - a.z * b.y + a.w * b.x);
+}
+
+__global__ void __launch_bounds__(kTM) mlp_estimate_kernel(const float4 *__restrict__ xyz,
+                                                           const float4 *__restrict__ rgb, int64_t n,
+                                                           const unsigned char *__restrict__ blob,
+                                                           const uint32_t *__restrict__ knn,
+                                                           float4 *__restrict__ mean_op, float4 *__restrict__ scale,
+                                                           float4 *__restrict__ quat, float4 *__restrict__ normal,
+                                                           int32_t *status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    MlpSmem &sm = *reinterpret_cast<MlpSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    // weights -> shared memory in the core-matrix layout (16-byte pieces)
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(blob);
+        auto load_w = [&](__nv_bfloat16 *dst, int off, int N, int K) {
+            for (int t = tid; t < N * K / 8; t += kTM) {
+                const int r = t / (K / 8), c = t % (K / 8);
+                *reinterpret_cast<uint4 *>(dst + core_off(r, c * 8, K)) = src[off / 16 + t];
+            }
+        };
+        load_w(sm.W1, kBlobW1, kHid, kIn);
+        load_w(sm.W2, kBlobW2, kHid, kHid);
+        load_w(sm.W3, kBlobW3, kHid, kHid);
+        load_w(sm.W4, kBlobW4, kOutPad, kHid);
+        const float *bsrc = reinterpret_cast<const float *>(blob + kBlobB);
+        for (int t = tid; t < 3 * kHid + kOutPad; t += kTM) sm.b[t] = bsrc[t];
+    }
+    if (tid == 0) {
+        sm.err = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sm.mbar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem;
+    const uint32_t my_lane = tmem + ((uint32_t)(warp * 32) << 16);
+    uint32_t phase = 0;
+    const int64_t ntiles = (n + kTM - 1) / kTM;
+
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t i = tile * kTM + tid;
+        const bool live = i < n;
+        // ---- features of point i -> row tid of A
+        float4 p = make_float4(0, 0, 0, 0), c = p, q = make_float4(1, 0, 0, 0);
+        if (live) {
+            p = __ldg(xyz + i);
+            c = __ldg(rgb + i);
+            q = quat[i];
+        }
+        const float w = q.x, x = q.y, y = q.z, z = q.w;
+        const float R00 = 1.f - 2.f * (y * y + z * z), R01 = 2.f * (x * y - w * z), R02 = 2.f * (x * z + w * y);
+        const float R10 = 2.f * (x * y + w * z), R11 = 1.f - 2.f * (x * x + z * z), R12 = 2.f * (y * z - w * x);
+        const float R20 = 2.f * (x * z - w * y), R21 = 2.f * (y * z + w * x), R22 = 1.f - 2.f * (x * x + y * y);
+        float inv_r = 0.f;
+        if (live) {
+            const float4 pl = __ldg(xyz + knn[i * kNb + kNb - 1]);
+            const float dx = pl.x - p.x, dy = pl.y - p.y, dz = pl.z - p.z;
+            inv_r = 1.f / fmaxf(sqrtf(dx * dx + dy * dy + dz * dz), 1e-12f);
+        }
+#pragma unroll 4
+        for (int k = 0; k < kNb; k += 4) {
+            // 4 neighbours = 24 features = 3 core-matrix rows of 8
+            float f[24];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                float4 pj = p, cj = c;
+                if (live) {
+                    const uint32_t j = knn[i * kNb + k + u];
+                    pj = __ldg(xyz + j);
+                    cj = __ldg(rgb + j);
+                }
+                const float dx = pj.x - p.x, dy = pj.y - p.y, dz = pj.z - p.z;
+                f[6 * u + 0] = (R00 * dx + R10 * dy + R20 * dz) * inv_r;
+                f[6 * u + 1] = (R01 * dx + R11 * dy + R21 * dz) * inv_r;
+                f[6 * u + 2] = (R02 * dx + R12 * dy + R22 * dz) * inv_r;
+                f[6 * u + 3] = cj.x - c.x;
+                f[6 * u + 4] = cj.y - c.y;
+                f[6 * u + 5] = cj.z - c.z;
+            }
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                uint32_t wv[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[ch * 8 + 2 * e], f[ch * 8 + 2 * e + 1]);
+                    wv[e] = *reinterpret_cast<const uint32_t *>(&b2);
+                }
+                *reinterpret_cast<uint4 *>(sm.A + core_off(tid, k * 6 + ch * 8, kIn)) =
+                    make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            }
+        }
+        proxy_fence();
+        tc_fence_before();
+        __syncthreads();
+        // ---- four layers
+        bool ok = true;
+        const __nv_bfloat16 *Bs[4] = {sm.W1, sm.W2, sm.W3, sm.W4};
+        for (int L = 0; L < 4 && ok; ++L) {
+            if (tid == 0) issue_layer(tmem, L == 0 ? sm.A : sm.H, Bs[L], L == 0 ? kIn : kHid, L == 3 ? kOutPad : kHid,
+                                      &sm.mbar);
+            ok = !__syncthreads_or(!mbar_wait(&sm.mbar, phase));  // uniform decision
+            phase ^= 1u;
+            tc_fence_after();
+            if (!ok) break;
+            if (L < 3) {
+                epilogue_hidden(my_lane, sm.b + L * kHid, sm.H, tid);
+                proxy_fence();
+                tc_fence_before();
+                __syncthreads();
+            }
+        }
+        if (!ok) {
+            atomicExch(status, (int32_t)P2E_ERR_TIMEOUT);
+            sm.err = 1;
+            break;
+        }
+        // ---- outputs: corrections of the PCA frame
+        float yv[16];
+        tmem_ld16(my_lane, yv);
+        if (live) {
+            float yy[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) yy[e] = yv[e] + sm.b[3 * kHid + e];
+            const float4 s0 = scale[i];
+            scale[i] = make_float4(s0.x * __expf(fminf(fmaxf(yy[0], -4.f), 4.f)),
+                                   s0.y * __expf(fminf(fmaxf(yy[1], -4.f), 4.f)),
+                                   s0.z * __expf(fminf(fmaxf(yy[2], -4.f), 4.f)), 0.f);
+            float4 dq = make_float4(1.f + yy[3], yy[4], yy[5], yy[6]);
+            const float dn = rsqrtf(fmaxf(dq.x * dq.x + dq.y * dq.y + dq.z * dq.z + dq.w * dq.w, 1e-30f));
+            dq = make_float4(dq.x * dn, dq.y * dn, dq.z * dn, dq.w * dn);
+            const float4 qf = qmul(q, dq);
+            quat[i] = qf;
+            const float4 m = mean_op[i];
+            const float o0 = fminf(fmaxf(m.w, 1e-6f), 1.f - 1e-6f);
+            const float o = 1.f / (1.f + __expf(-(__logf(o0 / (1.f - o0)) + yy[7])));
+            mean_op[i] = make_float4(m.x, m.y, m.z, o);
+            const float W = qf.x, X = qf.y, Y = qf.z, Z = qf.w;
+            normal[i] = make_float4(2.f * (X * Z + W * Y), 2.f * (Y * Z - W * X), 1.f - 2.f * (X * X + Y * Y), 0.f);
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    __syncthreads();
+    if (sm.err && tid == 0) mbar_wait(&sm.mbar, phase ^ 1u);  // let an overdue MMA finish (bounded)
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+cudaError_t launch_mlp_estimate(const float *xyz, const float *rgb, int64_t n, const void *mlp,
+                                const uint32_t *knn, p2e_gaussians *out, void *scratch, int num_sms,
+                                cudaStream_t st) {
+    int32_t *status = (int32_t *)scratch;
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    const size_t smem = sizeof(MlpSmem) + 1024;
+    static int configured[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int slot = (dev >= 0 && dev < 64) ? dev : 0;
+    if (!configured[slot]) {
+        e = cudaFuncSetAttribute(mlp_estimate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured[slot] = 1;
+    }
+    const int64_t ntiles = (n + kTM - 1) / kTM;
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms * 2);
+    mlp_estimate_kernel<<<grid, kTM, smem, st>>>((const float4 *)xyz, (const float4 *)rgb, n,
+                                                 (const unsigned char *)mlp, knn, (float4 *)out->mean_op,
+                                                 (float4 *)out->scale, (float4 *)out->quat, (float4 *)out->normal,
+                                                 status);
+    return cudaGetLastError();
+}
+
 }  // namespace p2e
