@@ -181,6 +181,29 @@ p2e_status p2e_project(const p2e_gaussians *g, const p2e_camera *cams, int32_t n
 p2e_status p2e_sort_bin(const p2e_projected *proj, int64_t n, const p2e_camera *cams,
                         int32_t n_views, const p2e_config *cfg, p2e_bins *io, void *stream);
 
+/* p2e_sort_bin_noalloc -- the same binning as p2e_sort_bin for callers that
+ * are not allowed to allocate device memory: code running inside a host
+ * application that owns the GPU's memory budget (an engine or compositor
+ * plugin that is handed its buffers), or a latency-critical loop where a
+ * cudaMalloc/cudaFree could stall or synchronise the device.  The paper has
+ * no counterpart; this is a deployment convenience.
+ * Its scratch is a fixed 4.25 MiB array inside libp2e that every GPU using
+ * the library keeps until the process exits; io->scratch and
+ * io->scratch_bytes are ignored, everything else in io is used as in
+ * p2e_sort_bin and still belongs to the caller.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Limits: n * n_views <= P2E_NOALLOC_MAX_N and io->capacity <=
+ * P2E_NOALLOC_MAX_CAPACITY, otherwise P2E_ERR_INVALID_ARG is returned and
+ * nothing is enqueued.  All calls share the one array (the call clears what
+ * must start at zero), so calls whose work overlaps on the GPU -- on
+ * different streams, or on different host threads -- race and give wrong
+ * results; serialise them. */
+#define P2E_NOALLOC_MAX_N (1 << 22)
+#define P2E_NOALLOC_MAX_CAPACITY (1 << 21)
+p2e_status p2e_sort_bin_noalloc(const p2e_projected *proj, int64_t n, const p2e_camera *cams,
+                                int32_t n_views, const p2e_config *cfg, p2e_bins *io, void *stream);
+
 /* p2e_bins_check -- synchronises `stream`, copies the key count to
  * *n_keys_host and returns P2E_ERR_CAPACITY if it exceeded io->capacity,
  * P2E_ERR_TIMEOUT if a device wait gave up, else P2E_OK. */

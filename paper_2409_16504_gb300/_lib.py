@@ -21,8 +21,10 @@ P2E_SCRATCH_SORT, P2E_SCRATCH_ESTIMATE, P2E_SCRATCH_BACKWARD = 0, 1, 2
 
 # every symbol include/p2e.h declares
 EXPORTS = ("p2e_default_config", "p2e_total_tiles", "p2e_scratch_bytes", "p2e_project",
-           "p2e_sort_bin", "p2e_bins_check", "p2e_render", "p2e_render_backward", "p2e_estimate",
-           "p2e_status_string")
+           "p2e_sort_bin", "p2e_sort_bin_noalloc", "p2e_bins_check", "p2e_render",
+           "p2e_render_backward", "p2e_estimate", "p2e_status_string")
+NOALLOC_MAX_N = 1 << 22
+NOALLOC_MAX_CAPACITY = 1 << 21
 
 
 class P2ECamera(C.Structure):
@@ -84,6 +86,9 @@ def load(path: str | None = None):
         lib.p2e_sort_bin.restype = C.c_int
         lib.p2e_sort_bin.argtypes = [C.POINTER(P2EProjected), i64, C.POINTER(P2ECamera), i32,
                                      C.POINTER(P2EConfig), C.POINTER(P2EBins), vp]
+        lib.p2e_sort_bin_noalloc.restype = C.c_int
+        lib.p2e_sort_bin_noalloc.argtypes = [C.POINTER(P2EProjected), i64, C.POINTER(P2ECamera), i32,
+                                             C.POINTER(P2EConfig), C.POINTER(P2EBins), vp]
         lib.p2e_bins_check.restype = C.c_int
         lib.p2e_bins_check.argtypes = [C.POINTER(P2EBins), C.POINTER(C.c_int64), vp]
         lib.p2e_render.restype = C.c_int

@@ -261,3 +261,39 @@ p2e_status p2e_estimate(const float *xyz, const float *rgb, int64_t n, int32_t m
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// p2e_sort_bin_noalloc: p2e_sort_bin with its scratch in a fixed device
+// array owned by this library, for callers that may not allocate device
+// memory (see include/p2e.h).  The array lives as long as the library is
+// loaded, on every device it is used on.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kNoallocScratchBytes = 4456448;  // 4.25 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+static void *g_noalloc_addr[64];  // device address of the array, per device, 0 = not set up
+}  // namespace
+
+extern "C" p2e_status p2e_sort_bin_noalloc(const p2e_projected *proj, int64_t n, const p2e_camera *cams,
+                                           int32_t n_views, const p2e_config *cfg, p2e_bins *io,
+                                           void *stream) {
+    if (!io || n < 0 || n_views < 1 || n_views > P2E_MAX_VIEWS) return P2E_ERR_INVALID_ARG;
+    if (n * n_views > P2E_NOALLOC_MAX_N || io->capacity > P2E_NOALLOC_MAX_CAPACITY || io->capacity < 0)
+        return P2E_ERR_INVALID_ARG;
+    if (sort_scratch_bytes(n * n_views, io->capacity) > kNoallocScratchBytes) return P2E_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return P2E_ERR_CUDA;
+    if (!g_noalloc_addr[dev]) {
+        // first call on this device: look up the array's device address
+        // (host code cannot use the symbol itself as a device pointer)
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return P2E_ERR_CUDA;
+        g_noalloc_addr[dev] = ptr;
+    }
+    p2e_bins local = *io;
+    local.scratch = g_noalloc_addr[dev];
+    local.scratch_bytes = (int64_t)kNoallocScratchBytes;
+    const p2e_status s = p2e_sort_bin(proj, n, cams, n_views, cfg, &local, stream);
+    io->result = local.result;
+    return s;
+}
