@@ -29,7 +29,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "p2e_oracle.c"), os.path.join(_HERE, "knn_pca.c")]
+_SRCS = [os.path.join(_HERE, "p2e_oracle.c"), os.path.join(_HERE, "knn_pca.c"),
+         os.path.join(_HERE, "raycast.c")]
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -266,3 +267,38 @@ def sigma_of(scale, quat) -> np.ndarray:
                   np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], 1)
     s2 = np.asarray(scale, np.float64) ** 2
     return np.einsum("nij,nj,nkj->nik", R, s2, R)
+
+
+# ---------------------------------------------------------------- ground truth
+def prim_records(prims) -> np.ndarray:
+    """Analytic primitives (scenes.Primitive) as the ray caster's records."""
+    out = np.zeros((len(prims), 20))
+    for k, p in enumerate(prims):
+        if p.kind == "ell":
+            out[k, 0] = 0
+            out[k, 1:4], out[k, 4:7] = p.center, p.radii
+            out[k, 7:16] = np.asarray(p.rot, np.float64).reshape(9)
+        else:
+            out[k, 0] = 1
+            out[k, 1:4], out[k, 4:7], out[k, 7] = p.p0, p.p1, p.r
+    return out
+
+
+def raycast(prims, cam: dict, texture=None, bg=(0.0, 0.0, 0.0)) -> dict:
+    """Exact ground-truth view: rgb (texture at the hit), outward normal,
+    camera depth and coverage of one ray per pixel centre."""
+    W, H = cam["width"], cam["height"]
+    rec = np.ascontiguousarray(prim_records(prims))
+    hit = np.zeros((H, W), np.uint8)
+    depth = np.zeros((H, W))
+    normal = np.zeros((H, W, 3))
+    point = np.zeros((H, W, 3))
+    cf = cam_floats(cam)
+    lib().or_raycast(_p(cf), C.c_int(W), C.c_int(H), _p(rec), C.c_int(len(prims)), _p(hit),
+                     _p(depth), _p(normal), _p(point))
+    h = hit.astype(bool)
+    rgb = np.zeros((H, W, 3)) + np.asarray(bg, np.float64)
+    if texture is not None and h.any():
+        rgb[h] = texture(point[h])
+    return dict(hit=h, depth=depth, normal=normal.transpose(2, 0, 1), rgb=rgb.transpose(2, 0, 1),
+                point=point)

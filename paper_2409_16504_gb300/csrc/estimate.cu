@@ -6,7 +6,7 @@
 // that frame with a per-point network.
 //
 //   bbox      one reduction: bounding box and centroid of the cloud
-//   grid      uniform cells (about two cells per point at most), counting
+//   grid      uniform cells (at most four cells per point), counting
 //             sort of the points by cell (count, scan, scatter)
 //   knn+pca   one thread per point, points taken in cell order: exact 16
 //             nearest other points by searching rings of cells until the
@@ -44,13 +44,14 @@ struct EstScratch {
     uint32_t *start;      // ncell_max + 1
     uint64_t *scan_state; // scan tiles + 1
     uint32_t *ticket;
+    float4 *spts;         // n points in cell order, .w = bits of the original index
     uint32_t *knn;        // n * 16 (when the caller passes none)
     void *mlp_scratch;    // see mlp.cu
     int64_t ncell_max, scan_tiles;
 };
 
 __host__ __device__ inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
-static int64_t ncell_cap(int64_t n) { return std::max<int64_t>(2 * n, 1 << 16); }
+static int64_t ncell_cap(int64_t n) { return std::max<int64_t>(4 * n, 1 << 16); }
 constexpr int kScanT = 1024;
 size_t mlp_scratch_bytes(int64_t n);
 
@@ -75,6 +76,7 @@ static size_t est_layout(int64_t n, void *base, EstScratch *S) {
     s.start = (uint32_t *)take((size_t)(nc + 1) * 4);
     s.scan_state = (uint64_t *)take((size_t)(st + 1) * 8);
     s.ticket = (uint32_t *)take(64);
+    s.spts = (float4 *)take((size_t)n * 16);
     s.knn = (uint32_t *)take((size_t)n * kK * 4);
     s.mlp_scratch = take(mlp_scratch_bytes(n));
     s.ncell_max = nc;
@@ -143,8 +145,8 @@ __global__ void grid_setup_kernel(int64_t n, EstScratch S) {
     emax = fmaxf(emax, 1e-30f);
     double vol = 1.0;
     for (int k = 0; k < 3; ++k) vol *= fmax((double)ext[k], 1e-3 * (double)emax);
-    // about two cells per point: half the spacing of 4 points per cell
-    double h = 0.5 * cbrt(vol * 4.0 / (double)n);
+    // fine enough that a 3x3x3 block holds the 16 nearest with few extras
+    double h = 0.4 * cbrt(vol * 4.0 / (double)n);
     for (int it = 0; it < 64; ++it) {
         double cells = 1.0;
         for (int k = 0; k < 3; ++k) {
@@ -261,31 +263,43 @@ __global__ void __launch_bounds__(256) scan_counts_kernel(const uint32_t *__rest
     }
 }
 
-__global__ void __launch_bounds__(256) scatter_kernel(int64_t n, EstScratch S) {
+__global__ void __launch_bounds__(256) scatter_kernel(const float4 *__restrict__ xyz, int64_t n, EstScratch S) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t c = S.cell[i];
-        S.order[S.start[c] + atomicAdd(&S.fill[c], 1u)] = (uint32_t)i;
+        const uint32_t q = S.start[c] + atomicAdd(&S.fill[c], 1u);
+        S.order[q] = (uint32_t)i;
+        const float4 p = __ldg(xyz + i);
+        S.spts[q] = make_float4(p.x, p.y, p.z, __uint_as_float((uint32_t)i));
     }
 }
 
-// sorted insertion of (d, j) into best[] (static indices only, so the list
-// stays in registers)
-__device__ __forceinline__ void knn_insert(float (&bd)[kK], uint32_t (&bi)[kK], float d, uint32_t j) {
-#pragma unroll
-    for (int k = 0; k < kK; ++k) {
-        const bool lt = d < bd[k] || (d == bd[k] && j < bi[k]);
-        const float td = lt ? bd[k] : d;
-        const uint32_t tj = lt ? bi[k] : j;
-        bd[k] = lt ? d : bd[k];
-        bi[k] = lt ? j : bi[k];
-        d = td;
-        j = tj;
+constexpr int kKnnThreads = 128;
+
+// Per-thread list of the 16 best (distance, index) pairs, kept sorted in
+// shared memory ([slot][thread], conflict-free); an insertion shifts only the
+// entries that follow it.
+struct KnnList {
+    float *d;
+    uint32_t *j;
+    __device__ __forceinline__ float &D(int k) { return d[k * kKnnThreads]; }
+    __device__ __forceinline__ uint32_t &J(int k) { return j[k * kKnnThreads]; }
+    __device__ __forceinline__ void insert(float dd, uint32_t jj) {
+        int k = kK - 1;
+        while (k > 0 && (dd < D(k - 1) || (dd == D(k - 1) && jj < J(k - 1)))) {
+            D(k) = D(k - 1);
+            J(k) = J(k - 1);
+            --k;
+        }
+        D(k) = dd;
+        J(k) = jj;
     }
-}
+};
 
 // cyclic Jacobi on a symmetric 3x3 (fp32); V columns are eigenvectors
-__device__ void jacobi3f(float A[3][3], float V[3][3]) {
+__device__ __forceinline__ void jacobi3f(float (&A)[3][3], float (&V)[3][3]) {
+#pragma unroll
     for (int i = 0; i < 3; ++i)
+#pragma unroll
         for (int j = 0; j < 3; ++j) V[i][j] = i == j ? 1.f : 0.f;
     const float tr = fabsf(A[0][0]) + fabsf(A[1][1]) + fabsf(A[2][2]);
     for (int sweep = 0; sweep < 12; ++sweep) {
@@ -339,111 +353,217 @@ __device__ __forceinline__ float4 shepperd_f(const float R[3][3]) {
     return make_float4(w, x, y, z);
 }
 
-__global__ void __launch_bounds__(128) knn_pca_kernel(const float4 *__restrict__ xyz,
+constexpr int kRad = 6;       // trial radii of the first pass, in cell sizes
+constexpr int kBuf = 48;      // candidates kept by the second pass
+
+// Iterates the candidate points of rings 0..1 around the query's cell
+// (points of the 3x3x3 block, taken from the cell-ordered copy).
+template <typename F>
+__device__ __forceinline__ void for_block(const GridParams &g, const EstScratch &S, const int c0[3], F &&f) {
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int cz = c0[2] + dz;
+        if (cz < 0 || cz >= g.dim[2]) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int cy = c0[1] + dy;
+            if (cy < 0 || cy >= g.dim[1]) continue;
+            const int x0 = max(c0[0] - 1, 0), x1 = min(c0[0] + 1, g.dim[0] - 1);
+            const uint32_t row = (uint32_t)(((int64_t)cz * g.dim[1] + cy) * g.dim[0]);
+            // cells x0..x1 of a row are contiguous in the cell-ordered points
+            const uint32_t s0 = S.start[row + x0], e0 = S.start[row + x1 + 1];
+            for (uint32_t q = s0; q < e0; ++q) f(S.spts[q]);
+        }
+    }
+}
+
+// One thread per query point (points taken in cell order).  Exact 16
+// nearest other points, ties by index:
+//   pass 1  count the block's candidates within kRad trial radii (branch
+//           free) and pick the smallest radius that holds 16 of them; that
+//           radius is at most one cell size, so every point within it lies
+//           in the 3x3x3 block;
+//   pass 2  keep the candidates within the radius (at most kBuf) in shared
+//           memory and select the 16 smallest.
+// A query whose block holds fewer than 16 points within a cell size, or
+// whose buffer would overflow, takes the incremental ring search instead.
+__global__ void __launch_bounds__(kKnnThreads) knn_pca_kernel(const float4 *__restrict__ xyz,
                                                       const float4 *__restrict__ rgb, int64_t n,
                                                       float opacity, EstScratch S, uint32_t *__restrict__ knn_out,
                                                       float4 *__restrict__ mean_op, float4 *__restrict__ scale,
                                                       float4 *__restrict__ quat, float4 *__restrict__ rgb_out,
                                                       float4 *__restrict__ normal) {
+    __shared__ float s_d[kBuf * kKnnThreads];
+    __shared__ uint32_t s_j[kBuf * kKnnThreads];
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     const GridParams g = *S.gp;
-    const uint32_t i = S.order[t];
-    const float4 p = __ldg(xyz + i);
+    const float4 pq = S.spts[t];
+    const uint32_t i = __float_as_uint(pq.w);
+    const float4 p = pq;
     int c0[3];
     cell_of(g, p.x, p.y, p.z, c0);
-    float bd[kK];
-    uint32_t bi[kK];
+    // ---- pass 1: counts within the trial radii (the query itself included)
+    float r2[kRad];
 #pragma unroll
-    for (int k = 0; k < kK; ++k) { bd[k] = INFINITY; bi[k] = 0xffffffffu; }
-    const int rmax = max(g.dim[0], max(g.dim[1], g.dim[2]));
-    for (int r = 0; r <= rmax; ++r) {
-        for (int dz = -r; dz <= r; ++dz) {
-            const int cz = c0[2] + dz;
-            if (cz < 0 || cz >= g.dim[2]) continue;
-            for (int dy = -r; dy <= r; ++dy) {
-                const int cy = c0[1] + dy;
-                if (cy < 0 || cy >= g.dim[1]) continue;
-                const bool shell = (dz == -r || dz == r || dy == -r || dy == r);
-                for (int dx = -r; dx <= r; dx += (shell ? 1 : 2 * r)) {
-                    const int cx = c0[0] + dx;
-                    if (cx >= 0 && cx < g.dim[0]) {
-                        const uint32_t c = (uint32_t)(((int64_t)cz * g.dim[1] + cy) * g.dim[0] + cx);
-                        const uint32_t s = S.start[c], e = S.start[c + 1];
-                        for (uint32_t q = s; q < e; ++q) {
-                            const uint32_t j = S.order[q];
-                            if (j == i) continue;
-                            const float4 pj = __ldg(xyz + j);
-                            const float ex = pj.x - p.x, ey = pj.y - p.y, ez = pj.z - p.z;
-                            const float d = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                            if (d < bd[kK - 1] || (d == bd[kK - 1] && j < bi[kK - 1])) knn_insert(bd, bi, d, j);
+    for (int k = 0; k < kRad; ++k) {
+        const float f = 0.40f + 0.12f * k;   // 0.40 .. 1.00 cell sizes
+        const float rr = fminf(f, 1.f) * g.h * (1.f - 1e-4f) - 1e-6f;
+        r2[k] = rr * rr;
+    }
+    int cnt[kRad] = {0, 0, 0, 0, 0, 0};
+    for_block(g, S, c0, [&](const float4 &pj) {
+        const float ex = pj.x - p.x, ey = pj.y - p.y, ez = pj.z - p.z;
+        const float d = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+#pragma unroll
+        for (int k = 0; k < kRad; ++k) cnt[k] += d < r2[k] ? 1 : 0;
+    });
+    float T = -1.f;
+    int nbuf = 0;
+#pragma unroll
+    for (int k = kRad - 1; k >= 0; --k)
+        if (cnt[k] >= kK + 1 && cnt[k] <= kBuf + 1) { T = r2[k]; nbuf = cnt[k] - 1; }
+    float *bd = s_d + threadIdx.x;
+    uint32_t *bj = s_j + threadIdx.x;
+    KnnList best{bd, bj};
+    if (T > 0.f) {
+        // ---- pass 2: the candidates within T, then the 16 smallest
+        int m = 0;
+        for_block(g, S, c0, [&](const float4 &pj) {
+            const uint32_t j = __float_as_uint(pj.w);
+            const float ex = pj.x - p.x, ey = pj.y - p.y, ez = pj.z - p.z;
+            const float d = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            if (d < T && j != i && m < kBuf) {
+                bd[m * kKnnThreads] = d;
+                bj[m * kKnnThreads] = j;
+                ++m;
+            }
+        });
+        // partial selection sort: the 16 smallest (d, j) to the front
+        for (int a = 0; a < kK; ++a) {
+            int best_k = a;
+            float dbst = bd[a * kKnnThreads];
+            uint32_t jbst = bj[a * kKnnThreads];
+            for (int b = a + 1; b < m; ++b) {
+                const float db = bd[b * kKnnThreads];
+                const uint32_t jb = bj[b * kKnnThreads];
+                if (db < dbst || (db == dbst && jb < jbst)) { best_k = b; dbst = db; jbst = jb; }
+            }
+            bd[best_k * kKnnThreads] = bd[a * kKnnThreads];
+            bj[best_k * kKnnThreads] = bj[a * kKnnThreads];
+            bd[a * kKnnThreads] = dbst;
+            bj[a * kKnnThreads] = jbst;
+        }
+        (void)nbuf;
+    } else {
+        // ---- fallback: incremental search over growing rings
+        for (int k = 0; k < kK; ++k) { best.D(k) = INFINITY; best.J(k) = 0xffffffffu; }
+        float thr = INFINITY;
+        uint32_t thr_j = 0xffffffffu;
+        const int rmax = max(g.dim[0], max(g.dim[1], g.dim[2]));
+        for (int r = 0; r <= rmax; ++r) {
+            for (int dz = -r; dz <= r; ++dz) {
+                const int cz = c0[2] + dz;
+                if (cz < 0 || cz >= g.dim[2]) continue;
+                for (int dy = -r; dy <= r; ++dy) {
+                    const int cy = c0[1] + dy;
+                    if (cy < 0 || cy >= g.dim[1]) continue;
+                    const bool shell = (dz == -r || dz == r || dy == -r || dy == r);
+                    for (int dx = -r; dx <= r; dx += (shell ? 1 : 2 * r)) {
+                        const int cx = c0[0] + dx;
+                        if (cx >= 0 && cx < g.dim[0]) {
+                            const uint32_t c = (uint32_t)(((int64_t)cz * g.dim[1] + cy) * g.dim[0] + cx);
+                            for (uint32_t q = S.start[c]; q < S.start[c + 1]; ++q) {
+                                const float4 pj = S.spts[q];
+                                const uint32_t j = __float_as_uint(pj.w);
+                                if (j == i) continue;
+                                const float ex = pj.x - p.x, ey = pj.y - p.y, ez = pj.z - p.z;
+                                const float d = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                                if (d < thr || (d == thr && j < thr_j)) {
+                                    best.insert(d, j);
+                                    thr = best.D(kK - 1);
+                                    thr_j = best.J(kK - 1);
+                                }
+                            }
                         }
+                        if (r == 0) break;
                     }
-                    if (r == 0) break;
                 }
             }
+            const float bound = fmaxf(0.f, (float)r * g.h * (1.f - 1e-4f) - 1e-6f);
+            if (thr_j != 0xffffffffu && thr < bound * bound) break;
         }
-        // any point outside rings 0..r is at least r*h away (with margin for
-        // the rounding of the cell assignment)
-        const float bound = fmaxf(0.f, (float)r * g.h * (1.f - 1e-4f) - 1e-6f);
-        if (bi[kK - 1] != 0xffffffffu && bd[kK - 1] < bound * bound) break;
     }
-    if (knn_out)
-#pragma unroll
-        for (int k = 0; k < kK; ++k) knn_out[(int64_t)i * kK + k] = bi[k];
+    {
+        if (knn_out)
+            for (int k = 0; k < kK; ++k) knn_out[(int64_t)i * kK + k] = best.J(k);
     // covariance of the neighbours about their centroid
     float m[3] = {0, 0, 0};
-    float4 q[kK];
-#pragma unroll
     for (int k = 0; k < kK; ++k) {
-        q[k] = __ldg(xyz + bi[k]);
-        m[0] += q[k].x; m[1] += q[k].y; m[2] += q[k].z;
+        const float4 qk = __ldg(xyz + best.J(k));
+        m[0] += qk.x; m[1] += qk.y; m[2] += qk.z;
     }
     for (int k = 0; k < 3; ++k) m[k] *= (1.f / kK);
     float C[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-#pragma unroll
-    for (int k = 0; k < kK; ++k) {
-        const float d[3] = {q[k].x - m[0], q[k].y - m[1], q[k].z - m[2]};
+        for (int k = 0; k < kK; ++k) {
+        const float4 qk = __ldg(xyz + best.J(k));  // second pass, from L1
+        const float d[3] = {qk.x - m[0], qk.y - m[1], qk.z - m[2]};
+        #pragma unroll
         for (int a = 0; a < 3; ++a)
+            #pragma unroll
             for (int b = a; b < 3; ++b) C[a][b] = fmaf(d[a], d[b], C[a][b]);
     }
+    #pragma unroll
     for (int a = 0; a < 3; ++a)
+        #pragma unroll
         for (int b = a; b < 3; ++b) {
             C[a][b] *= (1.f / kK);
             C[b][a] = C[a][b];
         }
     float V[3][3];
     jacobi3f(C, V);
-    float lam[3] = {C[0][0], C[1][1], C[2][2]};
-    int o[3] = {0, 1, 2};
-    if (lam[o[1]] > lam[o[0]]) { int tt = o[0]; o[0] = o[1]; o[1] = tt; }
-    if (lam[o[2]] > lam[o[1]]) { int tt = o[1]; o[1] = o[2]; o[2] = tt; }
-    if (lam[o[1]] > lam[o[0]]) { int tt = o[0]; o[0] = o[1]; o[1] = tt; }
+    // eigenpairs in descending order (static indices only)
+    float l0 = C[0][0], l1 = C[1][1], l2 = C[2][2];
+    float e0[3] = {V[0][0], V[1][0], V[2][0]}, e1[3] = {V[0][1], V[1][1], V[2][1]}, e2[3] = {V[0][2], V[1][2], V[2][2]};
+#define P2E_SWAP_PAIR(la, lb, ua, ub)                                  \
+    do {                                                               \
+        const float t_ = la; la = lb; lb = t_;                         \
+        _Pragma("unroll") for (int k_ = 0; k_ < 3; ++k_) {             \
+            const float w_ = ua[k_]; ua[k_] = ub[k_]; ub[k_] = w_;     \
+        }                                                              \
+    } while (0)
+    if (l1 > l0) P2E_SWAP_PAIR(l0, l1, e0, e1);
+    if (l2 > l1) P2E_SWAP_PAIR(l1, l2, e1, e2);
+    if (l1 > l0) P2E_SWAP_PAIR(l0, l1, e0, e1);
+#undef P2E_SWAP_PAIR
+    const float lamv[3] = {l0, l1, l2};
     float R[3][3];
-    for (int a = 0; a < 3; ++a)
-        for (int k = 0; k < 3; ++k) R[k][a] = V[k][o[a]];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { R[k][0] = e0[k]; R[k][1] = e1[k]; R[k][2] = e2[k]; }
     // canonical frame: normal away from the centroid, e1's largest-magnitude
     // component positive, e2 = e3 x e1
     const float sg = (p.x - g.cen[0]) * R[0][2] + (p.y - g.cen[1]) * R[1][2] + (p.z - g.cen[2]) * R[2][2];
     if (sg < 0.f)
+        #pragma unroll
         for (int k = 0; k < 3; ++k) R[k][2] = -R[k][2];
     {
         const float a0 = fabsf(R[0][0]), a1 = fabsf(R[1][0]), a2 = fabsf(R[2][0]);
         const float big = (a1 > a0) ? ((a2 > a1) ? R[2][0] : R[1][0]) : ((a2 > a0) ? R[2][0] : R[0][0]);
         if (big < 0.f)
+            #pragma unroll
             for (int k = 0; k < 3; ++k) R[k][0] = -R[k][0];
     }
     R[0][1] = R[1][2] * R[2][0] - R[2][2] * R[1][0];
     R[1][1] = R[2][2] * R[0][0] - R[0][2] * R[2][0];
     R[2][1] = R[0][2] * R[1][0] - R[1][2] * R[0][0];
     float s[3];
-    for (int a = 0; a < 3; ++a) s[a] = sqrtf(fmaxf(lam[o[a]], 0.f));
+    #pragma unroll
+    for (int a = 0; a < 3; ++a) s[a] = sqrtf(fmaxf(lamv[a], 0.f));
     s[2] = fmaxf(s[2], 0.1f * s[1]);
     mean_op[i] = make_float4(p.x, p.y, p.z, opacity);
     scale[i] = make_float4(s[0], s[1], s[2], 0.f);
     quat[i] = shepperd_f(R);
     rgb_out[i] = __ldg(rgb + i);
     normal[i] = make_float4(R[0][2], R[1][2], R[2][2], 0.f);
+    }
 }
 
 __global__ void est_init_kernel(EstScratch S) {
@@ -476,10 +596,10 @@ cudaError_t launch_estimate(const float *xyz, const float *rgb, int64_t n, int32
     grid_setup_kernel<<<1, 1, 0, st>>>(n, S);
     cell_count_kernel<<<g1, 256, 0, st>>>((const float4 *)xyz, n, S);
     scan_counts_kernel<<<(unsigned)S.scan_tiles, 256, 0, st>>>(S.counts, S.ncell_max, S.start, S, status);
-    scatter_kernel<<<g1, 256, 0, st>>>(n, S);
+    scatter_kernel<<<g1, 256, 0, st>>>((const float4 *)xyz, n, S);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     uint32_t *knn = knn_idx ? knn_idx : S.knn;
-    knn_pca_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
+    knn_pca_kernel<<<(unsigned)((n + kKnnThreads - 1) / kKnnThreads), kKnnThreads, 0, st>>>(
         (const float4 *)xyz, (const float4 *)rgb, n, pca_opacity, S, knn, (float4 *)out->mean_op,
         (float4 *)out->scale, (float4 *)out->quat, (float4 *)out->rgb, (float4 *)out->normal);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
