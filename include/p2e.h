@@ -269,6 +269,45 @@ p2e_status p2e_estimate(const float *xyz, const float *rgb, int64_t n, int32_t m
                         const void *mlp_weights, float pca_opacity, p2e_gaussians *out,
                         uint32_t *knn_idx, void *scratch, int64_t scratch_bytes, void *stream);
 
+/* ---- training of the learned estimator (Sec. 3.3) ------------------- */
+
+/* p2e_loss_eq5 -- the training loss of Eq. 5 and its gradient:
+ *   L = w1 mean|I - I^| + w2 mean(|n x n^| + w3 min(|n - n^|, |n + n^|))
+ * (the L1 mean is over pixels and the 3 channels, the normal term's over
+ * pixels; the paper uses w1 = 1, w2 = 10, w3 = 0.1).  rgb/normal: the
+ * rendered planar images of p2e_render, gt_rgb/gt_normal the targets in the
+ * same layout; view_pixels (host) holds H*W of each of n_views views.
+ * Writes *loss_dev (device float, overwritten), d_rgb and d_normal
+ * (dL/dI^, dL/dn^, same layout).  The gradient of |.| at 0 is taken as 0. */
+p2e_status p2e_loss_eq5(const float *rgb, const float *normal, const float *gt_rgb,
+                        const float *gt_normal, const int64_t *view_pixels, int32_t n_views,
+                        float w1, float w2, float w3, float *loss_dev, float *d_rgb,
+                        float *d_normal, void *stream);
+
+/* p2e_mlp_backward -- gradient of a loss with respect to the estimator's
+ * parameters, given its gradient with respect to the estimated Gaussians
+ * (d_scale[3n], d_quat[4n] w.r.t. the output quaternion, d_opacity[n],
+ * d_normal[3n] w.r.t. the output normal; as p2e_render_backward writes
+ * them).  xyz, rgb: the cloud (device float4[n]); knn_idx: the 16
+ * neighbours of p2e_estimate (device uint32[n*16]); pca: the mode-0
+ * estimate of the same cloud (its scale, quat and mean_op.w are read);
+ * mlp_weights: the blob the forward used.  The network is re-evaluated
+ * with the forward's bf16 roundings.  grad: device float[P2E_MLP_PARAMS]
+ * in blob order (W1, W2, W3, W4 16x64, b1, b2, b3, b4 16), ACCUMULATED
+ * into.  Synchronises the stream once (reads the PCA opacity). */
+#define P2E_MLP_PARAMS 15568
+p2e_status p2e_mlp_backward(const float *xyz, const float *rgb, int64_t n, const uint32_t *knn_idx,
+                            const p2e_gaussians *pca, const void *mlp_weights, const float *d_scale,
+                            const float *d_quat, const float *d_opacity, const float *d_normal,
+                            float *grad, void *stream);
+
+/* p2e_adam -- one Adam step (bias-corrected) on the fp32 parameter vector
+ * (count must be P2E_MLP_PARAMS; W4/b4 rows 8..15 are kept at zero), zeroes
+ * grad, and, if blob is not NULL, rewrites the P2E_MLP_BLOB_BYTES weight
+ * blob (bf16 weights rounded to nearest even, fp32 biases).  step >= 1. */
+p2e_status p2e_adam(float *params, float *grad, float *m, float *v, int64_t count, float lr,
+                    float beta1, float beta2, float eps, int32_t step, void *blob, void *stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *p2e_status_string(p2e_status s);
 

@@ -147,3 +147,86 @@ def estimate(xyz, rgb, p: dict, opacity: float = 0.9) -> dict:
     out = apply_corrections(e["scale"], e["quat"], np.full(len(xyz), opacity), y)
     out.update(idx=idx, pca=e, y=y)
     return out
+
+
+def _ident(x):
+    return np.asarray(x, np.float64)
+
+
+def loss_grad_params(p: dict, x, scale_pca, quat_pca, opacity_pca, up: dict, rounding: bool = True) -> dict:
+    """Exact gradient of L = sum(up_scale * s) + sum(up_quat * q) +
+    sum(up_opacity * o) + sum(up_normal * normal) with respect to the
+    network's parameters, the outputs s, q, o, normal being those of
+    :func:`apply_corrections` on the network's raw outputs.
+
+    ``rounding=True`` rounds operands and hidden activations to bf16 as the
+    tensor-core forward does (the rounding is held fixed, i.e. treated as
+    the identity in the derivative); ``rounding=False`` is the plain FP64
+    network, whose gradient the finite-difference pin checks.
+    Returns gradients keyed like the parameters (W4, b4 with 16 rows).
+    """
+    r = bf16_round if rounding else _ident
+    W = {k: r(p[k]) for k in ("W1", "W2", "W3", "W4")}
+    b = {k: np.asarray(p[k], np.float32 if rounding else np.float64).astype(np.float64)
+         for k in ("b1", "b2", "b3", "b4")}
+    h0 = r(x)
+    a1 = h0 @ W["W1"].T + b["b1"]
+    h1 = r(np.maximum(a1, 0))
+    a2 = h1 @ W["W2"].T + b["b2"]
+    h2 = r(np.maximum(a2, 0))
+    a3 = h2 @ W["W3"].T + b["b3"]
+    h3 = r(np.maximum(a3, 0))
+    y = (h3 @ W["W4"].T + b["b4"])[:, :OUT]
+    n = len(y)
+    # ---- output mapping backward
+    s0 = np.asarray(scale_pca, np.float64)
+    q0 = np.asarray(quat_pca, np.float64)
+    q0 = q0 / np.linalg.norm(q0, axis=1, keepdims=True)
+    dy = np.zeros((n, OUT))
+    inside = (y[:, 0:3] > -4.0) & (y[:, 0:3] < 4.0)
+    dy[:, 0:3] = np.where(inside, up["scale"] * s0 * np.exp(np.clip(y[:, 0:3], -4, 4)), 0.0)
+    dq = np.stack([1.0 + y[:, 3], y[:, 4], y[:, 5], y[:, 6]], 1)
+    dn = np.linalg.norm(dq, axis=1, keepdims=True)
+    dh = dq / dn
+    a0, a1_, a2_, a3_ = q0.T
+    # q = L(q0) dh with L the left Hamilton product matrix
+    L = np.stack([np.stack([a0, -a1_, -a2_, -a3_], 1), np.stack([a1_, a0, -a3_, a2_], 1),
+                  np.stack([a2_, a3_, a0, -a1_], 1), np.stack([a3_, -a2_, a1_, a0], 1)], 1)
+    qf = np.einsum("nij,nj->ni", L, dh)
+    Wq, Xq, Yq, Zq = qf.T
+    gn = np.asarray(up["normal"], np.float64)
+    gq = np.asarray(up["quat"], np.float64).copy()
+    gq[:, 0] += 2 * Yq * gn[:, 0] - 2 * Xq * gn[:, 1]
+    gq[:, 1] += 2 * Zq * gn[:, 0] - 2 * Wq * gn[:, 1] - 4 * Xq * gn[:, 2]
+    gq[:, 2] += 2 * Wq * gn[:, 0] + 2 * Zq * gn[:, 1] - 4 * Yq * gn[:, 2]
+    gq[:, 3] += 2 * Xq * gn[:, 0] + 2 * Yq * gn[:, 1]
+    gh = np.einsum("nji,nj->ni", L, gq)
+    dy[:, 3:7] = (gh - dh * (dh * gh).sum(1, keepdims=True)) / dn
+    o0 = np.asarray(opacity_pca, np.float64)
+    o = 1.0 / (1.0 + np.exp(-(np.log(o0 / (1 - o0)) + y[:, 7])))
+    dy[:, 7] = up["opacity"] * o * (1 - o)
+    # ---- layers
+    g = {}
+    dyp = np.zeros((n, OUT_PAD))
+    dyp[:, :OUT] = dy
+    g["W4"] = dyp.T @ h3
+    g["b4"] = dyp.sum(0)
+    d3 = (dyp @ W["W4"]) * (a3 > 0)
+    g["W3"], g["b3"] = d3.T @ h2, d3.sum(0)
+    d2 = (d3 @ W["W3"]) * (a2 > 0)
+    g["W2"], g["b2"] = d2.T @ h1, d2.sum(0)
+    d1 = (d2 @ W["W2"]) * (a1 > 0)
+    g["W1"], g["b1"] = d1.T @ h0, d1.sum(0)
+    return g
+
+
+def linear_outputs(p: dict, x, scale_pca, quat_pca, opacity_pca, up: dict) -> float:
+    """The scalar whose gradient :func:`loss_grad_params` returns, with the
+    plain FP64 network (for finite differences)."""
+    h = np.asarray(x, np.float64)
+    for w, b in (("W1", "b1"), ("W2", "b2"), ("W3", "b3")):
+        h = np.maximum(h @ np.asarray(p[w], np.float64).T + np.asarray(p[b], np.float64), 0)
+    y = (h @ np.asarray(p["W4"], np.float64).T + np.asarray(p["b4"], np.float64))[:, :OUT]
+    out = apply_corrections(scale_pca, quat_pca, opacity_pca, y)
+    return float((up["scale"] * out["scale"]).sum() + (up["quat"] * out["quat"]).sum() +
+                 (up["opacity"] * out["opacity"]).sum() + (up["normal"] * out["normal"]).sum())

@@ -6,7 +6,7 @@
 // that frame with a per-point network.
 //
 //   bbox      one reduction: bounding box and centroid of the cloud
-//   grid      uniform cells (at most four cells per point), counting
+//   grid      uniform cells (about two cells per point at most), counting
 //             sort of the points by cell (count, scan, scatter)
 //   knn+pca   one thread per point, points taken in cell order: exact 16
 //             nearest other points by searching rings of cells until the
@@ -51,7 +51,7 @@ struct EstScratch {
 };
 
 __host__ __device__ inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
-static int64_t ncell_cap(int64_t n) { return std::max<int64_t>(4 * n, 1 << 16); }
+static int64_t ncell_cap(int64_t n) { return std::max<int64_t>(2 * n, 1 << 16); }
 constexpr int kScanT = 1024;
 size_t mlp_scratch_bytes(int64_t n);
 
@@ -145,8 +145,9 @@ __global__ void grid_setup_kernel(int64_t n, EstScratch S) {
     emax = fmaxf(emax, 1e-30f);
     double vol = 1.0;
     for (int k = 0; k < 3; ++k) vol *= fmax((double)ext[k], 1e-3 * (double)emax);
-    // fine enough that a 3x3x3 block holds the 16 nearest with few extras
-    double h = 0.4 * cbrt(vol * 4.0 / (double)n);
+    // about two cells per point: half the spacing of 4 points per cell, so
+    // that a 3x3x3 block of cells almost always holds the 16 nearest
+    double h = 0.5 * cbrt(vol * 4.0 / (double)n);
     for (int it = 0; it < 64; ++it) {
         double cells = 1.0;
         for (int k = 0; k < 3; ++k) {

@@ -30,6 +30,7 @@ constexpr int kNT = 256;
 constexpr int oW1 = 0, oW2 = oW1 + kHid * kIn, oW3 = oW2 + kHid * kHid, oW4 = oW3 + kHid * kHid,
               oB1 = oW4 + kOutPad * kHid, oB2 = oB1 + kHid, oB3 = oB2 + kHid, oB4 = oB3 + kHid,
               kNParams = oB4 + kOutPad;
+static_assert(kNParams == P2E_MLP_PARAMS, "parameter layout of p2e.h");
 
 // ------------------------------------------------------------------ loss
 struct LossViews {

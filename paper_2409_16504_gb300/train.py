@@ -1,0 +1,167 @@
+"""End-to-end training of the learned per-point estimator (Sec. 3.3) through
+the differentiable splatting, on the GPU, by libp2e's own kernels:
+
+    estimate (kNN-PCA, then the tcgen05 network)  -> Gaussians
+    render the views                               -> RGB, normal images
+    loss of Eq. 5 against the ground-truth views   -> dL/dimages
+    render backward                                -> dL/d(scale, quat, opacity, normal)
+    network backward                               -> dL/dparameters
+    Adam                                           -> parameters + bf16 weight blob
+
+This module only drives those C-ABI calls and owns the buffers.  Training
+scenes are seeded humanoid proxies with jittered sizes and poses; their
+ground-truth views come from ``scenes.gt_views`` (exact ray casting of the
+analytic surfaces, the stand-in for images rasterised from meshes).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import math
+import os
+import sys
+import time
+
+import numpy as np
+import torch
+
+from . import _lib, mlp
+from ._lib import P2EGaussians, check
+from .estimate import LEARNED, PCA, Estimator, cloud_tensors
+from .render import DEFAULT_CONFIG, GaussianSet, Renderer, _ptr, _stream, p2e_render_backward
+
+LOSS_W = (1.0, 10.0, 0.1)   # w1, w2, w3 of Eq. 5
+ORDER = ("W1", "W2", "W3", "W4", "b1", "b2", "b3", "b4")
+
+
+def flatten(params: dict) -> torch.Tensor:
+    return torch.cat([params[k].reshape(-1).to(torch.float32) for k in ORDER]).contiguous()
+
+
+def unflatten(theta: torch.Tensor) -> dict:
+    out, off = {}, 0
+    for k in ORDER:
+        n = int(np.prod(mlp.SHAPES[k]))
+        out[k] = theta[off: off + n].reshape(mlp.SHAPES[k]).clone()
+        off += n
+    return out
+
+
+class Scene:
+    """A training / evaluation scene: cloud on the device, cameras, and the
+    ground-truth RGB and normal images in the renderer's planar layout."""
+
+    def __init__(self, seed: int, n_points: int, n_views: int, res: int, jitter: float = 0.15,
+                 device="cuda"):
+        import scenes
+        prims = scenes.humanoid_primitives(seed, jitter=jitter)
+        xyz, rgb, _, _ = scenes.humanoid_cloud(n_points, seed=seed, prims=prims)
+        rng = np.random.default_rng(seed + 7)
+        center = xyz.mean(0)
+        self.cams = [scenes.sphere_camera(center, 2.5, rng, res, res) for _ in range(n_views)]
+        gt = scenes.gt_views(prims, self.cams)
+        self.xyz, self.rgb = cloud_tensors(xyz, rgb, device)
+        self.n = n_points
+        self.gt_rgb = torch.from_numpy(np.concatenate([g["rgb"].reshape(-1) for g in gt]).astype(np.float32)).to(device)
+        self.gt_normal = torch.from_numpy(
+            np.concatenate([g["normal"].reshape(-1) for g in gt]).astype(np.float32)).to(device)
+        self.view_pixels = (C.c_int64 * n_views)(*[res * res] * n_views)
+
+
+class Trainer:
+    def __init__(self, n_max: int, seed: int = 0, lr: float = 1e-3, cfg: dict | None = None, device="cuda"):
+        self.device = device
+        self.cfg = {**DEFAULT_CONFIG, **(cfg or {})}
+        self.theta = flatten(mlp.init_params(seed, device))
+        assert self.theta.numel() == _lib.MLP_PARAMS
+        self.m = torch.zeros_like(self.theta)
+        self.v = torch.zeros_like(self.theta)
+        self.grad = torch.zeros_like(self.theta)
+        self.blob = mlp.pack(unflatten(self.theta))
+        self.lr = lr
+        self.t = 0
+        self.est = Estimator(n_max, device)
+        self.loss_dev = torch.zeros(1, dtype=torch.float32, device=device)
+
+    def params(self) -> dict:
+        return unflatten(self.theta)
+
+    def _forward(self, sc: Scene, learned: bool = True):
+        knn = torch.empty((sc.n, 16), dtype=torch.int32, device=self.device)
+        g_pca = self.est(sc.xyz, sc.rgb, mode=PCA, knn=knn)
+        g = self.est(sc.xyz, sc.rgb, mode=LEARNED, mlp_blob=self.blob) if learned else g_pca
+        r = Renderer(self.cfg, capacity=max(1 << 18, 6 * sc.n * len(sc.cams)), device=self.device)
+        img = r.render(g, sc.cams)
+        return knn, g_pca, g, r, img
+
+    def _loss(self, sc: Scene, img):
+        d_rgb = torch.empty_like(img.rgb)
+        d_nrm = torch.empty_like(img.normal)
+        check("p2e_loss_eq5", _lib.load().p2e_loss_eq5(
+            _ptr(img.rgb), _ptr(img.normal), _ptr(sc.gt_rgb), _ptr(sc.gt_normal), sc.view_pixels,
+            len(sc.cams), *LOSS_W, _ptr(self.loss_dev), _ptr(d_rgb), _ptr(d_nrm), _stream()))
+        return d_rgb, d_nrm
+
+    def step(self, sc: Scene) -> float:
+        knn, g_pca, g, r, img = self._forward(sc)
+        d_rgb, d_nrm = self._loss(sc, img)
+        d = p2e_render_backward(g, r.proj, r.bins, sc.cams, r.cfg, img.alpha, img.last, d_rgb=d_rgb,
+                                d_normal=d_nrm)
+        ps = g_pca.c_struct()
+        lib = _lib.load()
+        check("p2e_mlp_backward", lib.p2e_mlp_backward(
+            _ptr(sc.xyz), _ptr(sc.rgb), sc.n, _ptr(knn), C.byref(ps), _ptr(self.blob), _ptr(d["scale"]),
+            _ptr(d["quat"]), _ptr(d["opacity"]), _ptr(d["normal"]), _ptr(self.grad), _stream()))
+        self.t += 1
+        check("p2e_adam", lib.p2e_adam(_ptr(self.theta), _ptr(self.grad), _ptr(self.m), _ptr(self.v),
+                                       self.theta.numel(), self.lr, 0.9, 0.999, 1e-8, self.t,
+                                       _ptr(self.blob), _stream()))
+        return float(self.loss_dev.item())
+
+    @torch.no_grad()
+    def evaluate(self, sc: Scene, learned: bool = True) -> dict:
+        """Eq. 5 loss and RGB PSNR (all pixels, images in [0, 1]) of one scene."""
+        _, _, _, _, img = self._forward(sc, learned)
+        self._loss(sc, img)
+        mse = float(((img.rgb - sc.gt_rgb) ** 2).mean().item())
+        return dict(loss=float(self.loss_dev.item()), psnr=10.0 * math.log10(1.0 / max(mse, 1e-12)))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description="train the learned per-point estimator")
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--scenes", type=int, default=24)
+    ap.add_argument("--points", type=int, default=150_000)
+    ap.add_argument("--views", type=int, default=4)
+    ap.add_argument("--res", type=int, default=256)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--eval-scenes", type=int, default=4)
+    ap.add_argument("--out", default=mlp.TRAINED)
+    a = ap.parse_args(argv)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    t0 = time.time()
+    pool = [Scene(1000 + s, a.points, a.views, a.res) for s in range(a.scenes)]
+    held = [Scene(2000 + s, a.points, 12, a.res) for s in range(a.eval_scenes)]
+    print(f"scenes ready in {time.time() - t0:.1f} s", flush=True)
+    tr = Trainer(a.points, lr=a.lr)
+    before = [tr.evaluate(h, learned=False) for h in held]
+    t1 = time.time()
+    for it in range(a.steps):
+        loss = tr.step(pool[it % len(pool)])
+        if it % 50 == 0 or it == a.steps - 1:
+            print(f"step {it:5d} loss {loss:.5f}", flush=True)
+    torch.cuda.synchronize()
+    dt = time.time() - t1
+    after = [tr.evaluate(h, learned=True) for h in held]
+    mlp.save(tr.params(), a.out)
+    pca_psnr = float(np.mean([b["psnr"] for b in before]))
+    net_psnr = float(np.mean([x["psnr"] for x in after]))
+    print(f"trained {a.steps} steps in {dt:.1f} s ({1e3 * dt / a.steps:.1f} ms/step); held-out PSNR "
+          f"kNN-PCA {pca_psnr:.2f} dB, learned {net_psnr:.2f} dB; loss {np.mean([b['loss'] for b in before]):.4f}"
+          f" -> {np.mean([x['loss'] for x in after]):.4f}; saved {a.out}", flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -380,3 +380,84 @@ def mean_spacing(n: int, prims, rng=None) -> float:
     rng = rng or np.random.default_rng(0)
     area = sum(p.area(rng) for p in prims)
     return math.sqrt(area / n)
+
+
+# ----------------------------------------------------------------------------
+# ground-truth views of the analytic scenes (training targets)
+# ----------------------------------------------------------------------------
+def gt_views(prims: list, cams: list, bg=(0.0, 0.0, 0.0)) -> list:
+    """Ray-cast views of the union of the primitives: per camera a dict with
+    planar ``rgb (3,H,W)`` (the scene texture at the hit), outward ``normal
+    (3,H,W)``, camera ``depth (H,W)`` and coverage ``hit (H,W)``.  One ray per
+    pixel centre, nearest positive hit over every primitive surface (the
+    first surface a ray meets is on the union's boundary).  These are
+    synthetic inputs, the stand-in for images rasterised from meshes."""
+    out = []
+    for cam in cams:
+        V = np.asarray(cam["viewmat"], np.float64)
+        T, t = V[:, :3], V[:, 3]
+        W, H = cam["width"], cam["height"]
+        f32 = lambda k: float(np.float32(cam[k]))  # noqa: E731
+        ii, jj = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+        dc = np.stack([(ii - f32("cx")) / f32("fx"), (jj - f32("cy")) / f32("fy"), np.ones_like(ii)], -1)
+        d = dc.reshape(-1, 3) @ T               # T^T dc, camera z of the ray = 1
+        o = -T.T @ t
+        tb = np.full(len(d), np.inf)
+        nb = np.zeros((len(d), 3))
+        for p in prims:
+            if p.kind == "ell":
+                R = np.asarray(p.rot, np.float64)
+                ol = (R.T @ (o - p.center)) / p.radii
+                dl = (d @ R) / p.radii
+                a = (dl * dl).sum(1)
+                b = 2 * dl @ ol
+                c = ol @ ol - 1
+                disc = b * b - 4 * a * c
+                ok = disc >= 0
+                sq = np.sqrt(np.where(ok, disc, 0))
+                t1 = (-b - sq) / (2 * a)
+                t2 = (-b + sq) / (2 * a)
+                tt = np.where(t1 > 0, t1, t2)
+                use = ok & (tt > 0) & (tt < tb)
+                g = (ol[None, :] + tt[:, None] * dl) / p.radii
+                n = g @ R.T
+                n /= np.linalg.norm(n, axis=1, keepdims=True) + 1e-300
+                tb = np.where(use, tt, tb)
+                nb[use] = n[use]
+            else:
+                ax = p.p1 - p.p0
+                h = np.linalg.norm(ax)
+                ax = ax / h
+                w = o - p.p0
+                wa, da = w @ ax, d @ ax
+                wp = w - wa * ax
+                dp = d - da[:, None] * ax
+                A = (dp * dp).sum(1)
+                B = 2 * dp @ wp
+                Cc = wp @ wp - p.r ** 2
+                disc = B * B - 4 * A * Cc
+                ok = (disc >= 0) & (A > 0)
+                sq = np.sqrt(np.where(ok, disc, 0))
+                Aq = np.where(A > 0, A, 1.0)
+                for tt in ((-B - sq) / (2 * Aq), (-B + sq) / (2 * Aq)):
+                    s = wa + tt * da
+                    use = ok & (tt > 0) & (tt < tb) & (s >= 0) & (s <= h)
+                    n = (wp[None, :] + tt[:, None] * dp) / p.r
+                    tb = np.where(use, tt, tb)
+                    nb[use] = n[use]
+                    ok = ok & ~use
+                with np.errstate(divide="ignore", invalid="ignore"):
+                    for s_end, sgn in ((0.0, -1.0), (h, 1.0)):
+                        tt = (s_end - wa) / da
+                        q = wp[None, :] + tt[:, None] * dp
+                        use = (da != 0) & (tt > 0) & (tt < tb) & ((q * q).sum(1) <= p.r ** 2)
+                        tb = np.where(use, tt, tb)
+                        nb[use] = sgn * ax
+        hit = np.isfinite(tb)
+        pts = o + np.where(hit, tb, 0)[:, None] * d
+        rgb = np.tile(np.asarray(bg, np.float64), (len(d), 1))
+        if hit.any():
+            rgb[hit] = texture(pts[hit])
+        out.append(dict(rgb=rgb.T.reshape(3, H, W), normal=nb.T.reshape(3, H, W),
+                        depth=np.where(hit, tb, 0).reshape(H, W), hit=hit.reshape(H, W)))
+    return out

@@ -41,3 +41,16 @@ def test_capped_cylinder_end_on_is_a_disk():
     assert (g["hit"][clear] == (rr < rad_px)[clear]).all()
     np.testing.assert_allclose(g["depth"][g["hit"]], D - 0.5, rtol=1e-12)
     np.testing.assert_allclose(g["normal"][2][g["hit"]], -1.0)
+
+
+def test_scene_gt_views_match_oracle_raycast():
+    """The training targets (scenes.gt_views, numpy) equal the oracle's
+    exact C ray caster on the humanoid proxy."""
+    prims = scenes.humanoid_primitives()
+    cam = scenes.sphere_camera(np.array([0, 0.5, 0]), 2.5, np.random.default_rng(3), 192, 160)
+    g = scenes.gt_views(prims, [cam])[0]
+    o = oracle.raycast(prims, cam, texture=scenes.texture)
+    assert (g["hit"] == o["hit"]).all() and o["hit"].sum() > 200
+    np.testing.assert_allclose(g["depth"], o["depth"], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(g["normal"], o["normal"], atol=1e-9)
+    np.testing.assert_allclose(g["rgb"], o["rgb"], atol=1e-9)
