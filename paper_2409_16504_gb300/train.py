@@ -69,10 +69,11 @@ class Scene:
 
 
 class Trainer:
-    def __init__(self, n_max: int, seed: int = 0, lr: float = 1e-3, cfg: dict | None = None, device="cuda"):
+    def __init__(self, n_max: int, seed: int = 0, lr: float = 1e-3, cfg: dict | None = None, device="cuda",
+                 params: dict | None = None):
         self.device = device
         self.cfg = {**DEFAULT_CONFIG, **(cfg or {})}
-        self.theta = flatten(mlp.init_params(seed, device))
+        self.theta = flatten(params if params is not None else mlp.init_params(seed, device)).to(device)
         assert self.theta.numel() == _lib.MLP_PARAMS
         self.m = torch.zeros_like(self.theta)
         self.v = torch.zeros_like(self.theta)
