@@ -217,9 +217,13 @@ p2e_status p2e_bins_check(const p2e_bins *io, int64_t *n_keys_host, void *stream
  * compositing stops before a splat with T (1 - alpha) < t_min.
  * Outputs (device, planar fp32, views concatenated):
  *   rgb[3][H][W] = C + T bg, normal[3][H][W], depth[H][W], alpha[H][W] =
- *   1 - T, last[H][W] uint32 = one past the position, in the pixel's tile
- *   list, of the last contributing splat (0 = none).  Any output pointer
- *   may be NULL except `last` when a backward pass will follow. */
+ *   1 - T, last[H][W] uint32 = one past the position of the pixel's last
+ *   contributing splat in this call's sorted value array
+ *   bins->vals[bins->result] (0 = none); vals[last - 1] is that splat's
+ *   Gaussian index.  Positions count every view of the call, so `last`
+ *   (unlike the other planes) depends on the batch a view is rendered in.
+ *   Any output pointer may be NULL except `last` when a backward pass
+ *   will follow. */
 p2e_status p2e_render(const p2e_gaussians *g, const p2e_projected *proj, const p2e_bins *bins,
                       const p2e_camera *cams, int32_t n_views, const p2e_config *cfg,
                       float *rgb, float *normal, float *depth, float *alpha, uint32_t *last,

@@ -244,31 +244,82 @@ def humanoid_primitives(seed: int | None = None, jitter: float = 0.0) -> list:
     return prims + limbs
 
 
-def deform_primitives(prims: list, t: float, amp: float = 0.35,
-                      period: float = 4.0) -> list:
-    """Limbs swing sinusoidally about their proximal joints at time ``t`` (s).
-
-    Used by the dynamic-cloud serving workload.  Joint chains follow the
-    primitive order of :func:`humanoid_primitives`.
-    """
-    out = [Primitive(p.kind, p.center.copy(), p.radii.copy(), p.rot.copy(),
-                     p.p0.copy(), p.p1.copy(), p.r) for p in prims]
+def limb_motion(prims: list, t: float, amp: float = 0.35, period: float = 4.0) -> list:
+    """Per primitive the rigid motion ``x -> b + R (x - a)``, as ``(R, a, b)``,
+    that swings the limbs sinusoidally about their proximal joints at time
+    ``t`` (s); identity for head, neck, torso and pelvis.  Joint chains
+    follow the primitive order of :func:`humanoid_primitives` (upper arm,
+    forearm, thigh, shin per side)."""
+    eye = np.eye(3)
+    out = [(eye, np.zeros(3), np.zeros(3)) for _ in prims]
     w = 2.0 * math.pi * t / period
     for side in range(2):
         base = 4 + 4 * side
-        ua, fa, th, sh = out[base], out[base + 1], out[base + 2], out[base + 3]
+        ua, fa, th, sh = prims[base], prims[base + 1], prims[base + 2], prims[base + 3]
         ph = math.pi * side
         r1 = _rot_axis([1, 0, 0], amp * math.sin(w + ph))
         r2 = _rot_axis([1, 0, 0], 0.5 * amp * math.sin(w + ph + 0.7))
-        el = ua.p0 + r1 @ (ua.p1 - ua.p0)
-        wr = el + r1 @ r2 @ (fa.p1 - fa.p0)
-        ua.p1, fa.p0, fa.p1 = el, el, wr
         r3 = _rot_axis([1, 0, 0], -amp * math.sin(w + ph))
         r4 = _rot_axis([1, 0, 0], 0.5 * amp * (1 + math.sin(w + ph + 0.5)))
-        kn = th.p0 + r3 @ (th.p1 - th.p0)
-        an = kn + r3 @ r4 @ (sh.p1 - sh.p0)
-        th.p1, sh.p0, sh.p1 = kn, kn, an
+        el = ua.p0 + r1 @ (ua.p1 - ua.p0)          # moved elbow
+        kn = th.p0 + r3 @ (th.p1 - th.p0)          # moved knee
+        out[base] = (r1, ua.p0, ua.p0)
+        out[base + 1] = (r1 @ r2, fa.p0, el)
+        out[base + 2] = (r3, th.p0, th.p0)
+        out[base + 3] = (r3 @ r4, sh.p0, kn)
     return out
+
+
+def deform_primitives(prims: list, t: float, amp: float = 0.35,
+                      period: float = 4.0) -> list:
+    """The primitives moved by :func:`limb_motion` at time ``t`` (s)."""
+    out = []
+    for p, (R, a, b) in zip(prims, limb_motion(prims, t, amp, period)):
+        q = Primitive(p.kind, p.center.copy(), p.radii.copy(), p.rot.copy(), p.p0.copy(), p.p1.copy(), p.r)
+        if p.kind == "cyl":
+            q.p0, q.p1 = b + R @ (p.p0 - a), b + R @ (p.p1 - a)
+        out.append(q)
+    return out
+
+
+class DynamicCloud:
+    """A moving, resampled humanoid point-cloud video.
+
+    One ``n_max``-point coloured sample of the rest pose is drawn once; frame
+    ``k`` of ``frames`` (spread over one ``period``) keeps the first
+    ``n(t) = mid + amp sin(2 pi t / period)`` points of a fixed random
+    permutation (a uniform subsample, so the point count swings between the
+    ends of ``n_range``) and moves each point with its primitive's limb
+    motion at ``t = k period / frames``.  Colours travel with the surface.
+    """
+
+    def __init__(self, n_range=(300_000, 1_200_000), seed: int = 0, frames: int = 16, period: float = 4.0):
+        self.prims = humanoid_primitives()
+        lo, hi = int(n_range[0]), int(n_range[1])
+        pts, _, pid = sample_surface(self.prims, hi, seed)
+        rng = np.random.default_rng(seed + 1)
+        perm = rng.permutation(hi)
+        self.pts, self.pid = pts[perm], pid[perm]
+        self.rgb = texture(self.pts).astype(np.float32)
+        self.frames, self.period = int(frames), float(period)
+        self.mid, self.amp = (lo + hi) / 2.0, (hi - lo) / 2.0
+
+    def time_of(self, k: int) -> float:
+        return (k % self.frames) * self.period / self.frames
+
+    def count(self, k: int) -> int:
+        return int(round(self.mid + self.amp * math.sin(2.0 * math.pi * self.time_of(k) / self.period)))
+
+    def frame(self, k: int):
+        """``(xyz float32 (n,3), rgb float32 (n,3))`` of frame ``k``."""
+        n = self.count(k)
+        x, pid = self.pts[:n], self.pid[:n]
+        out = x.copy()
+        for i, (R, a, b) in enumerate(limb_motion(self.prims, self.time_of(k))):
+            m = pid == i
+            if m.any():
+                out[m] = b + (x[m] - a) @ R.T
+        return out.astype(np.float32), self.rgb[:n]
 
 
 def sample_surface(prims: list, n: int, seed: int, noise: float = 1e-3):
