@@ -8,10 +8,13 @@
 //   bbox      one reduction: bounding box and centroid of the cloud
 //   grid      uniform cells (about two cells per point at most), counting
 //             sort of the points by cell (count, scan, scatter)
-//   knn+pca   one thread per point, points taken in cell order: exact 16
-//             nearest other points by searching rings of cells until the
-//             16th distance is below the distance to the next ring (ties by
-//             index); then the neighbours' covariance, a cyclic Jacobi
+//   knn+pca   one thread per point, points taken in cell order (a
+//             cell-ordered copy of the points): exact 16 nearest other
+//             points (ties by index) by a two-pass threshold search of the
+//             3x3x3 cell block (count within trial radii, then buffer and
+//             select), or, where the block cannot certify the answer, by
+//             rings of cells searched until the 16th distance is below the
+//             distance to the next ring; then the neighbours' covariance, a cyclic Jacobi
 //             eigen-decomposition, scale = sqrt(lambda) (smallest axis at
 //             least 0.1 of the middle one), rotation in a canonical frame
 //             (normal = smallest axis turned away from the centroid, first

@@ -130,8 +130,8 @@ class Trainer:
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description="train the learned per-point estimator")
-    ap.add_argument("--steps", type=int, default=600)
-    ap.add_argument("--scenes", type=int, default=24)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--scenes", type=int, default=32)
     ap.add_argument("--points", type=int, default=150_000)
     ap.add_argument("--views", type=int, default=4)
     ap.add_argument("--res", type=int, default=256)
