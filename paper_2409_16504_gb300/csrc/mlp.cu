@@ -36,9 +36,11 @@ constexpr uint32_t kTmemCols = 64;
 
 size_t mlp_scratch_bytes(int64_t) { return 256; }
 
+// H (the hidden activations) aliases the front of A: layer 1 has finished
+// reading A when its epilogue writes H, and each later layer has finished
+// reading H when its epilogue overwrites it.  55 KB per CTA: four CTAs per SM.
 struct __align__(128) MlpSmem {
     __nv_bfloat16 A[kTM * kIn];
-    __nv_bfloat16 H[kTM * kHid];
     __nv_bfloat16 W1[kHid * kIn];
     __nv_bfloat16 W2[kHid * kHid];
     __nv_bfloat16 W3[kHid * kHid];
@@ -205,6 +207,7 @@ __global__ void __launch_bounds__(kTM) mlp_estimate_kernel(const float4 *__restr
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = sm.tmem;
+    __nv_bfloat16 *const H = sm.A;
     const uint32_t my_lane = tmem + ((uint32_t)(warp * 32) << 16);
     uint32_t phase = 0;
     const int64_t ntiles = (n + kTM - 1) / kTM;
@@ -268,14 +271,14 @@ __global__ void __launch_bounds__(kTM) mlp_estimate_kernel(const float4 *__restr
         bool ok = true;
         const __nv_bfloat16 *Bs[4] = {sm.W1, sm.W2, sm.W3, sm.W4};
         for (int L = 0; L < 4 && ok; ++L) {
-            if (tid == 0) issue_layer(tmem, L == 0 ? sm.A : sm.H, Bs[L], L == 0 ? kIn : kHid, L == 3 ? kOutPad : kHid,
+            if (tid == 0) issue_layer(tmem, L == 0 ? sm.A : H, Bs[L], L == 0 ? kIn : kHid, L == 3 ? kOutPad : kHid,
                                       &sm.mbar);
             ok = !__syncthreads_or(!mbar_wait(&sm.mbar, phase));  // uniform decision
             phase ^= 1u;
             tc_fence_after();
             if (!ok) break;
             if (L < 3) {
-                epilogue_hidden(my_lane, sm.b + L * kHid, sm.H, tid);
+                epilogue_hidden(my_lane, sm.b + L * kHid, H, tid);
                 proxy_fence();
                 tc_fence_before();
                 __syncthreads();
@@ -337,8 +340,15 @@ cudaError_t launch_mlp_estimate(const float *xyz, const float *rgb, int64_t n, c
         if (e != cudaSuccess) return e;
         configured[slot] = 1;
     }
+    static int per_sm[64] = {0};
+    if (!per_sm[slot]) {
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mlp_estimate_kernel, kTM, smem);
+        // TMEM: 64 columns per CTA of the SM's 512
+        per_sm[slot] = std::max(1, std::min(nb, 512 / (int)kTmemCols));
+    }
     const int64_t ntiles = (n + kTM - 1) / kTM;
-    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms * 2);
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms * per_sm[slot]);
     mlp_estimate_kernel<<<grid, kTM, smem, st>>>((const float4 *)xyz, (const float4 *)rgb, n,
                                                  (const unsigned char *)mlp, knn, (float4 *)out->mean_op,
                                                  (float4 *)out->scale, (float4 *)out->quat, (float4 *)out->normal,
