@@ -223,7 +223,12 @@ p2e_status p2e_bins_check(const p2e_bins *io, int64_t *n_keys_host, void *stream
  *   Gaussian index.  Positions count every view of the call, so `last`
  *   (unlike the other planes) depends on the batch a view is rendered in.
  *   Any output pointer may be NULL except `last` when a backward pass
- *   will follow. */
+ *   will follow.
+ * Scratch: the free half of the key double buffer, keys[1 - result] and
+ * vals[1 - result], is overwritten (per-segment compositing states and
+ * the work-item table); the sorted keys/vals[result] are left intact.
+ * Device waits are bounded; one that gives up sets *bins->status_dev to
+ * P2E_ERR_TIMEOUT (reported by p2e_bins_check). */
 p2e_status p2e_render(const p2e_gaussians *g, const p2e_projected *proj, const p2e_bins *bins,
                       const p2e_camera *cams, int32_t n_views, const p2e_config *cfg,
                       float *rgb, float *normal, float *depth, float *alpha, uint32_t *last,

@@ -1,37 +1,46 @@
 // K6: front-to-back alpha compositing (Sec. 3.1, Eq. 1-2), with the normal
 // and depth images obtained by substituting n_k and z_k for c_k.
 //
-// Scheduling.  A persistent grid pulls work items from the list of
-// non-empty tiles that p2e_sort_bin leaves (longest list first); pixels of
-// empty tiles get the background from a separate fill kernel.  A work item
-// is one B x B pixel block of a binning tile: binning tiles of 16 are split
-// into four 8 x 8 blocks, so that the few tiles a compact subject covers
-// keep more SMs busy; each block screens its tile's whole list (next step)
-// and composites only the splats that reach it.
+// Work decomposition.  A compact subject covers few tiles (a 1 m figure at
+// 2.5 m fills ~150 of 4096 16-px tiles at 1024^2) with long depth lists
+// (up to ~40K splats), so neither a CTA per tile nor a thread per pixel
+// keeps the GPU busy.  Here one WARP owns an 8 x 4 pixel block (lane =
+// pixel) of one binning tile and one SEGMENT of the tile's list (256 splats
+// per block of the tile, e.g. 2048 for 16-px tiles); warps are fully
+// independent (no block-wide barrier) and pull (tile, segment, block) items
+// from a global counter, tiles in work-list order (longest first).
 //
-// Per pixel block, the depth-sorted list is consumed in waves of up to G
-// chunks of 256 splats:
-//   fill     the next splats of the list are screened by their pixel
-//            rectangle alone (8 bytes): only those whose rectangle meets a
-//            pixel that is still compositing enter the wave, compacted in
-//            list order (block-wide prefix sum).  Once the inside of a
-//            surface has saturated, the rest of a long list costs one
-//            rectangle load per splat instead of a full gather.
-//   gather   the wave's splat records go to shared memory (16-byte loads)
-//   cover    splat-parallel: every splat tests the live pixels of its pixel
-//            rectangle (set bits of the live rows) against its sigma_mult
-//            ellipse and sets its bit in those pixels' 256-bit chunk masks
-//   blend    pixel-parallel: group k composites chunk k from T = 1, walking
-//            only the set bits of its mask, in list (= depth) order
-//   merge    group 0 combines the chunks in order with the associative
-//            "over" rule C += T C_k, T *= T_k.  T is non-increasing, so the
-//            cutoff can only fall inside chunk k when T T_k < t_min; only
-//            that chunk is then re-walked from the true T with the stop
-//            rule, which reproduces the sequential result.
-// A splat is skipped only where it cannot contribute (outside its
-// rectangle, or on a pixel that has stopped), so the result is the
-// sequential one.  The tile is finished when every pixel has reached the
-// cutoff or the list ends.
+// Per item the warp streams its segment in chunks of 32 splats: every lane
+// loads one splat's index and pixel rectangle, the warp keeps (ballot) the
+// splats whose rectangle meets a live pixel of the block, stages their
+// records in shared memory in list order, and then every lane composites
+// the staged splats for its pixel in order (broadcast shared-memory reads,
+// one splat per step for all 32 pixels).
+//
+// Segments of one (tile, block) are chained like a decoupled look-back
+// scan under the associative "over" operator:
+//   segment 0    composite from T = 1 with the stop rule: exactly the
+//                sequential recurrence;
+//   later ones   composite the segment from T = 1 without stopping (a pure
+//                product), then fold with the predecessor's inclusive state:
+//                C = C_in + T_in C_s, T = T_in T_s.  T is non-increasing, so
+//                the stop can only fall inside the segment when
+//                T_in T_s < t_min; those pixels re-walk the segment from the
+//                true state with the stop rule, which reproduces the
+//                sequential result.  The predecessor is polled every 128
+//                splats: pixels it shows done, or whose stop it shows to lie
+//                in the part already walked, drop out of the speculation
+//                (their result no longer depends on it), so saturated
+//                surfaces cost little.  Which rule gives a pixel's result
+//                depends only on the data, never on timing: results are
+//                deterministic.
+// A segment that is not the last publishes its inclusive per-pixel state
+// (T, C, N, D, last | done) and a ready flag; the last one writes the image.
+// The predecessor holds an earlier item, taken by a running warp, so every
+// wait ends; waits are still bounded and a wait that gives up records
+// P2E_ERR_TIMEOUT.  The per-segment states live in the free half of the key
+// double buffer (keys[1 - result]), the item table in vals[1 - result].
+// Without room there (tiny capacities) every (tile, block) is one exact item.
 //
 // Sub-pixel accuracy: the pixel offset is formed as
 //   (x - (floor(u) - x0)) + (0.5 - frac(u)),
@@ -43,306 +52,393 @@
 
 namespace p2e {
 
-template <int B>
-struct BlendShape {
-    static constexpr int NPIX = B * B;
-    static constexpr int G = (B == 32) ? 1 : 4;    // chunk groups per CTA
-    static constexpr int NT = NPIX * G;            // 256, 1024, 1024 threads
-    static constexpr int NW = NT / 32;
-    static constexpr int CHUNK = 256;
-    static constexpr int WAVE = G * CHUNK;
-    static constexpr int MW = CHUNK / 32;          // mask words per pixel and chunk
+constexpr int kBW = 8, kBH = 4;    // pixel block of one warp
+constexpr int kWarps = 8;          // warps per CTA
+constexpr int kStateWords = 9;     // T, C0..2, N0..2, D, last | done << 31
+constexpr uint32_t kDoneBit = 1u << 31;
+
+__host__ __device__ constexpr int blocks_of(int tile) { return (tile / kBW) * (tile / kBH); }
+__host__ __device__ constexpr uint32_t seg_of(int tile) { return 256u * (uint32_t)blocks_of(tile); }
+
+struct StageRec {          // the staged splats of one warp
+    float4 off[32];        // (0.5 - frac u, 0.5 - frac v, floor u - x0, floor v - y0)
+    float4 co[32];         // (A, B, C, o)
+    float4 cz[32];         // (r, g, b, depth)
+    float4 nr[32];         // (nx, ny, nz, -)
+    uint32_t pos[32];      // list position
 };
 
-template <int B>
-struct BlendSmem {
-    using S = BlendShape<B>;
-    float4 off[S::WAVE];     // (0.5 - frac u, 0.5 - frac v, floor u - x0, floor v - y0)
-    float4 co[S::WAVE];      // (A, B, C, o)
-    float4 cz[S::WAVE];      // (r, g, b, depth)
-    float4 nr[S::WAVE];      // (nx, ny, nz, -)
-    uint32_t rect[S::WAVE];  // tile-relative pixel box clamped to the tile, 4 x u8
-    uint32_t gidx[S::WAVE];  // Gaussian of the wave slot
-    uint32_t lpos[S::WAVE];  // list position of the wave slot
-    uint32_t mask[S::G][S::MW][S::NPIX];  // word-major: conflict-free per-pixel reads
-    float part[S::G][8][S::NPIX];   // per chunk: C0..2, N0..2, D, T
-    uint32_t plast[S::G][S::NPIX];  // per chunk: last contributor (+1), 0 = none
-    uint32_t alive[B];              // row bitmasks of the pixels still compositing
-    uint32_t wscan[S::NW];          // fill: exclusive prefix of the warps' kept counts
-    uint32_t wtotal, cut;
-    uint8_t done[S::NPIX];
-    uint32_t item;
+struct PixState {
+    float T, c0, c1, c2, n0, n1, n2, D;
+    uint32_t last;
+    bool done;
 };
 
-__device__ __forceinline__ uint32_t row_bits(int x0, int x1) {  // bits x0..x1 (x1 <= 31)
-    return (x1 >= 31 ? 0xffffffffu : ((1u << (x1 + 1)) - 1u)) & ~((1u << x0) - 1u);
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Row bitmasks of the live pixels from group 0's threads (pixel = thread):
-// one warp holds 32 / B rows of the tile.
-template <int B>
-__device__ __forceinline__ void publish_alive(uint32_t *alive, int tid, bool live) {
-    const uint32_t m = __ballot_sync(0xffffffffu, live);
-    if ((tid & 31) == 0)
-        for (int rr = 0; rr < 32 / B; ++rr)
-            alive[(tid >> 5) * (32 / B) + rr] = (B == 32) ? m : ((m >> (rr * B)) & ((1u << B) - 1u));
+__device__ __forceinline__ bool chain_enabled(int allow_chain, const int64_t *n_keys_dev, int64_t capacity,
+                                              uint32_t n_work) {
+    return allow_chain && *n_keys_dev <= capacity && (int64_t)n_work + 1 <= capacity;
 }
 
-template <int B>
-__global__ void __launch_bounds__(BlendShape<B>::NT) blend_kernel(
-    const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
-    const uint32_t *__restrict__ work, uint32_t *__restrict__ work_counter,
-    const float4 *__restrict__ xy_depth, const float4 *__restrict__ conic_op,
-    const ushort4 *__restrict__ rect, const float4 *__restrict__ rgb,
-    const float4 *__restrict__ normal, float *__restrict__ out_rgb, float *__restrict__ out_nrm,
-    float *__restrict__ out_depth, float *__restrict__ out_alpha, uint32_t *__restrict__ out_last,
-    __grid_constant__ const Views P) {
-    using S = BlendShape<B>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    BlendSmem<B> &sm = *reinterpret_cast<BlendSmem<B> *>(smem_raw);
+// Item table: item_base[w] = first item of work entry w (exclusive scan of
+// blocks x segments over the work list), item_base[n_work] = total.
+// Chaining (segments of seg_of(tile) splats) is used only when the key
+// count fits the capacity and the table fits vals[1 - result]; otherwise
+// every (tile, block) is one item and no table is needed.
+__global__ void __launch_bounds__(1024) render_items_kernel(const uint2 *__restrict__ ranges,
+                                                            const uint32_t *__restrict__ work,
+                                                            const int64_t *__restrict__ n_keys_dev,
+                                                            int64_t capacity, int allow_chain, int tile,
+                                                            uint32_t *__restrict__ item_base) {
+    __shared__ uint32_t s_sum[32], s_off[32];
+    __shared__ uint32_t s_carry, s_tot;
+    const uint32_t n_work = work[0];
+    const uint32_t nb = (uint32_t)blocks_of(tile), S = seg_of(tile);
+    if (!chain_enabled(allow_chain, n_keys_dev, capacity, n_work)) return;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (int)(blockDim.x >> 5);
+    for (uint32_t b0 = 0; b0 < n_work; b0 += blockDim.x) {
+        const uint32_t w = b0 + threadIdx.x;
+        uint32_t v = 0;
+        if (w < n_work) {
+            const uint2 r = ranges[work[2 + w]];
+            v = nb * ((r.y - r.x + S - 1) / S);
+        }
+        uint32_t x = v;  // inclusive scan within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_sum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            const uint32_t s = lane < nw ? s_sum[lane] : 0u;
+            uint32_t t = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            s_off[lane] = t - s;
+            if (lane == 31) s_tot = t;
+        }
+        __syncthreads();
+        const uint32_t carry = s_carry;
+        if (w < n_work) item_base[w] = carry + s_off[wid] + x - v;
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry = carry + s_tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) item_base[n_work] = s_carry;
+}
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int grp = tid / S::NPIX;
-    const int pi = tid - grp * S::NPIX;     // pixel of this thread inside the tile
-    const int lx = pi % B, ly = pi / B;
-    const float lxf = (float)lx, lyf = (float)ly;
+__device__ __forceinline__ void fresh_state(PixState &s, bool inside) {
+    s.T = 1.f;
+    s.c0 = s.c1 = s.c2 = s.n0 = s.n1 = s.n2 = s.D = 0.f;
+    s.last = 0u;
+    s.done = !inside;
+}
+
+// per-lane state words, word-major ([word][lane]: coalesced)
+__device__ __forceinline__ void load_state(const float *src, int lane, PixState &s) {
+    s.T = src[0 * 32 + lane];
+    s.c0 = src[1 * 32 + lane];
+    s.c1 = src[2 * 32 + lane];
+    s.c2 = src[3 * 32 + lane];
+    s.n0 = src[4 * 32 + lane];
+    s.n1 = src[5 * 32 + lane];
+    s.n2 = src[6 * 32 + lane];
+    s.D = src[7 * 32 + lane];
+    const uint32_t w = __float_as_uint(src[8 * 32 + lane]);
+    s.last = w & ~kDoneBit;
+    s.done = (w & kDoneBit) != 0u;
+}
+__device__ __forceinline__ void store_state(float *dst, int lane, const PixState &s) {
+    dst[0 * 32 + lane] = s.T;
+    dst[1 * 32 + lane] = s.c0;
+    dst[2 * 32 + lane] = s.c1;
+    dst[3 * 32 + lane] = s.c2;
+    dst[4 * 32 + lane] = s.n0;
+    dst[5 * 32 + lane] = s.n1;
+    dst[6 * 32 + lane] = s.n2;
+    dst[7 * 32 + lane] = s.D;
+    dst[8 * 32 + lane] = __uint_as_float(s.last | (s.done ? kDoneBit : 0u));
+}
+
+// Bits of the 8 x 4 block (bit 8y + x) covered by the block-relative
+// rectangle [rx0, rx1] x [ry0, ry1] (non-empty, inside the block).
+__device__ __forceinline__ uint32_t rect_bits(int rx0, int rx1, int ry0, int ry1) {
+    const uint32_t row = (0xffu >> (kBW - 1 - (rx1 - rx0))) << rx0;
+    const uint32_t rows = (0xfu >> (kBH - 1 - (ry1 - ry0))) << ry0;
+    const uint32_t spread = (rows & 1u) | ((rows & 2u) << 7) | ((rows & 4u) << 14) | ((rows & 8u) << 21);
+    return row * spread;
+}
+
+// Streams list positions [s0, s1) for the warp's block: every lane screens
+// four splats per step of 128 (independent loads), the hits of each chunk
+// of 32 are staged in list order and then composited by every lane for its
+// pixel.  kStop: the stop rule of the
+// sequential recurrence; otherwise a pure product from the given state.
+// With a poll flag, returns early (the position reached, a multiple of 128
+// splats past s0) as soon as the flag is set; otherwise returns s1.
+template <bool kStop>
+__device__ __forceinline__ uint32_t composite_segment(uint32_t s0, uint32_t s1, int64_t gbase, int x0, int y0,
+                                                      float lxf, float lyf, const uint32_t *__restrict__ vals,
+                                                      const float4 *__restrict__ xy_depth,
+                                                      const float4 *__restrict__ conic_op,
+                                                      const ushort4 *__restrict__ rect,
+                                                      const float4 *__restrict__ rgb,
+                                                      const float4 *__restrict__ normal, const Views &P,
+                                                      StageRec &sg, int lane, PixState &st,
+                                                      const uint32_t *poll = nullptr) {
     const float pw_min = -0.5f * P.sigma_mult * P.sigma_mult;
     const float amax = P.alpha_max, afloor = P.alpha_floor, tmin = P.t_min;
-    // work items: every non-empty binning tile (side P.tile) split into
-    // sub x sub pixel blocks of side B, all blocks of a tile adjacent
-    const int sub = P.tile / B;
-    const uint32_t n_items = work[0] * (uint32_t)(sub * sub);
+    const uint32_t lt = (1u << lane) - 1u;
+    constexpr int kAhead = 4;  // chunks of 32 screened per step (independent loads)
+    for (uint32_t base = s0; base < s1; base += 32 * kAhead) {
+        if (poll) {
+            uint32_t ready = 0;
+            if (lane == 0) ready = ld_acquire_u32(poll);
+            if (__shfl_sync(0xffffffffu, ready, 0)) return base;
+        }
+        const uint32_t live = __ballot_sync(0xffffffffu, !st.done);
+        if (!live) break;
+        uint32_t gk[kAhead];
+#pragma unroll
+        for (int k = 0; k < kAhead; ++k) {
+            const uint32_t idx = base + 32u * k + (uint32_t)lane;
+            gk[k] = idx < s1 ? __ldg(vals + idx) : 0xffffffffu;
+        }
+        bool hk[kAhead];
+#pragma unroll
+        for (int k = 0; k < kAhead; ++k) {
+            hk[k] = false;
+            if (gk[k] != 0xffffffffu) {
+                if (gk[k] >= (uint32_t)P.n) gk[k] = 0;  // only reachable with corrupted bins
+                const ushort4 rc = __ldg(rect + gbase + gk[k]);
+                const int rx0 = max(0, (int)rc.x - x0), rx1 = min(kBW - 1, (int)rc.z - x0);
+                const int ry0 = max(0, (int)rc.y - y0), ry1 = min(kBH - 1, (int)rc.w - y0);
+                if (rx0 <= rx1 && ry0 <= ry1) hk[k] = (rect_bits(rx0, rx1, ry0, ry1) & live) != 0u;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kAhead; ++k) {
+            const uint32_t hits = __ballot_sync(0xffffffffu, hk[k]);
+            if (!hits) continue;
+            const uint32_t g = gk[k];
+            if (hk[k]) {
+                const int q = __popc(hits & lt);
+                const float4 xy = __ldg(xy_depth + gbase + g);
+                const float4 cc = __ldg(rgb + g);
+                sg.off[q] = splat_offset(xy, x0, y0);
+                sg.co[q] = __ldg(conic_op + gbase + g);
+                sg.cz[q] = make_float4(cc.x, cc.y, cc.z, xy.z);
+                sg.nr[q] = __ldg(normal + g);
+                sg.pos[q] = base + 32u * k + (uint32_t)lane;
+            }
+            __syncwarp();
+            const int nh = __popc(hits);
+            if (!st.done) {
+                for (int j = 0; j < nh; ++j) {
+                    const float4 o = sg.off[j], co = sg.co[j];
+                    const float power = splat_power(o, co, lxf, lyf);
+                    if (power < pw_min) continue;
+                    float e;
+                    bool fr;
+                    const float alpha = splat_alpha(co.w, power, amax, e, fr);
+                    if (alpha < afloor) continue;
+                    const float Tn = st.T * (1.f - alpha);
+                    if (kStop && Tn < tmin) {
+                        st.done = true;
+                        break;
+                    }
+                    const float wgt = alpha * st.T;
+                    const float4 cz = sg.cz[j], nr = sg.nr[j];
+                    st.c0 = fmaf(wgt, cz.x, st.c0);
+                    st.c1 = fmaf(wgt, cz.y, st.c1);
+                    st.c2 = fmaf(wgt, cz.z, st.c2);
+                    st.n0 = fmaf(wgt, nr.x, st.n0);
+                    st.n1 = fmaf(wgt, nr.y, st.n1);
+                    st.n2 = fmaf(wgt, nr.z, st.n2);
+                    st.D = fmaf(wgt, cz.w, st.D);
+                    st.T = Tn;
+                    st.last = sg.pos[j] + 1u;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    return s1;
+}
+
+template <int BT>
+__global__ void __launch_bounds__(kWarps * 32) blend_kernel(
+    const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ work,
+    uint32_t *__restrict__ work_counter, const uint32_t *__restrict__ item_base,
+    const int64_t *__restrict__ n_keys_dev, int64_t capacity, int allow_chain, float *__restrict__ states,
+    uint32_t *__restrict__ flags, const float4 *__restrict__ xy_depth, const float4 *__restrict__ conic_op,
+    const ushort4 *__restrict__ rect, const float4 *__restrict__ rgb, const float4 *__restrict__ normal,
+    float *__restrict__ out_rgb, float *__restrict__ out_nrm, float *__restrict__ out_depth,
+    float *__restrict__ out_alpha, uint32_t *__restrict__ out_last, int32_t *__restrict__ status,
+    __grid_constant__ const Views P) {
+    constexpr int NBX = BT / kBW, NB = blocks_of(BT);
+    constexpr uint32_t S = seg_of(BT);
+    constexpr int SW = kStateWords * 32;  // state floats of one (segment, block)
+    __shared__ StageRec stage[kWarps];
+    const int lane = threadIdx.x & 31;
+    StageRec &sg = stage[threadIdx.x >> 5];
+    const int lx = lane % kBW, ly = lane / kBW;
+    const float lxf = (float)lx, lyf = (float)ly;
+    const float tmin = P.t_min;
+    const uint32_t n_work = work[0];
+    const bool chained = chain_enabled(allow_chain, n_keys_dev, capacity, n_work);
+    const uint32_t total = chained ? item_base[n_work] : n_work * (uint32_t)NB;
 
     for (;;) {
-        if (tid == 0) sm.item = atomicAdd(work_counter, 1u);
-        __syncthreads();
-        const uint32_t item = sm.item;
-        if (item >= n_items) break;
-        const int64_t tile = work[2 + item / (uint32_t)(sub * sub)];
-        const int blk = (int)(item % (uint32_t)(sub * sub));
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(work_counter, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= total) break;
+        uint32_t w, local;
+        if (chained) {  // last work entry whose first item is <= item
+            uint32_t lo = 0, hi = n_work;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (__ldg(item_base + mid) <= item) lo = mid;
+                else hi = mid;
+            }
+            w = lo;
+            local = item - __ldg(item_base + w);
+        } else {
+            w = item / (uint32_t)NB;
+            local = item % (uint32_t)NB;
+        }
+        const uint32_t seg = local / (uint32_t)NB;
+        const int blk = (int)(local % (uint32_t)NB);
+        const int64_t tile = work[2 + w];
         const int vi = view_of_tile(P, tile);
         const View &V = P.v[vi];
-        const int64_t lt = tile - V.tile_base;
-        const int ty = (int)(lt / V.tiles_x), tx = (int)(lt - (int64_t)ty * V.tiles_x);
-        const int x0 = tx * P.tile + (blk % sub) * B, y0 = ty * P.tile + (blk / sub) * B;
+        const int64_t ltile = tile - V.tile_base;
+        const int ty = (int)(ltile / V.tiles_x), tx = (int)(ltile - (int64_t)ty * V.tiles_x);
+        const int x0 = tx * BT + (blk % NBX) * kBW, y0 = ty * BT + (blk / NBX) * kBH;
         const int px = x0 + lx, py = y0 + ly;
         const bool inside = px < V.W && py < V.H;
         const uint2 r = ranges[tile];
         const int64_t gbase = (int64_t)vi * P.n;
+        const uint32_t nseg = chained ? (r.y - r.x + S - 1) / S : 1u;
+        const uint32_t s0 = chained ? r.x + seg * S : r.x;
+        const uint32_t s1 = chained ? min(r.y, s0 + S) : r.y;
 
-        float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f, D = 0.f;
-        uint32_t last = 0;
-        bool done = !inside;
-        if (grp == 0) {
-            sm.done[pi] = done ? 1 : 0;
-            publish_alive<B>(sm.alive, tid, !done);
+        PixState st;
+        fresh_state(st, inside);
+        if (seg == 0) {
+            composite_segment<true>(s0, s1, gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect, rgb, normal,
+                                    P, sg, lane, st);
+        } else {
+            // predecessor: the segment starting S earlier; a non-last segment
+            // starting at list position p keeps its state in slot p / S
+            const size_t pslot = (size_t)((s0 - S) / S) * NB + blk;
+            const uint32_t *pflag = flags + pslot;
+            const float *pstate = states + pslot * SW;
+            PixState pr;
+            bool known = __all_sync(0xffffffffu, ld_acquire_u32(pflag) != 0u);
+            if (known) load_state(pstate, lane, pr);
+            // speculate from T = 1 (pure product) for the pixels whose result
+            // may need it; a pixel drops out once the predecessor shows it
+            // done or shows that the stop falls in the part already walked
+            bool rewalk = false;
+            if (known) st.done = st.done || pr.done;
+            uint32_t reached = composite_segment<false>(s0, s1, gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op,
+                                                        rect, rgb, normal, P, sg, lane, st,
+                                                        known ? nullptr : pflag);
+            if (!known) {
+                // wait (bounded) for the predecessor's inclusive state
+                uint32_t ready = 0;
+                if (lane == 0) {
+                    for (uint32_t it = 0;; ++it) {
+                        ready = ld_acquire_u32(pflag);
+                        // give up at the limit, or at once after another wait gave up
+                        if (ready || it >= kSpinLimit ||
+                            *(volatile int32_t *)status == (int32_t)P2E_ERR_TIMEOUT)
+                            break;
+                        backoff(it);
+                    }
+                    if (!ready) atomicExch(status, (int32_t)P2E_ERR_TIMEOUT);
+                }
+                ready = __shfl_sync(0xffffffffu, ready, 0);
+                if (ready && ld_acquire_u32(pflag)) load_state(pstate, lane, pr);
+                else fresh_state(pr, inside);
+                if (reached < s1) {
+                    rewalk = !pr.done && !st.done && pr.T * st.T < tmin;
+                    st.done = st.done || pr.done || rewalk;
+                    composite_segment<false>(reached, s1, gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect,
+                                             rgb, normal, P, sg, lane, st);
+                }
+            }
+            // result: the predecessor's state if done; else fold
+            // C = C_in + T_in C_s, T = T_in T_s over the whole segment, unless
+            // the stop falls inside it (T_in T_s < t_min, T non-increasing):
+            // then re-walk the segment from the true state with the stop rule
+            if (pr.done) {
+                st = pr;
+            } else if (!rewalk && pr.T * st.T >= tmin) {
+                st.c0 = fmaf(pr.T, st.c0, pr.c0);
+                st.c1 = fmaf(pr.T, st.c1, pr.c1);
+                st.c2 = fmaf(pr.T, st.c2, pr.c2);
+                st.n0 = fmaf(pr.T, st.n0, pr.n0);
+                st.n1 = fmaf(pr.T, st.n1, pr.n1);
+                st.n2 = fmaf(pr.T, st.n2, pr.n2);
+                st.D = fmaf(pr.T, st.D, pr.D);
+                st.T = pr.T * st.T;
+                if (!st.last) st.last = pr.last;
+                st.done = false;
+            } else {
+                rewalk = true;
+            }
+            if (__any_sync(0xffffffffu, rewalk)) {
+                PixState rw = pr;
+                rw.done = !rewalk;  // only the re-walking pixels take part
+                composite_segment<true>(s0, s1, gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect, rgb,
+                                        normal, P, sg, lane, rw);
+                if (rewalk) st = rw;
+            }
         }
-
-        uint32_t pos = r.x;  // next list position to screen (uniform)
-        for (;;) {
-            if (__syncthreads_count(grp == 0 ? done : true) == S::NT) break;
-            if (pos >= r.y) break;
-            // ---- fill: the next splats whose rectangle meets a live pixel
-            uint32_t nfill = 0;  // uniform
-            while (nfill < (uint32_t)S::WAVE && pos < r.y) {
-                const uint32_t idx = pos + (uint32_t)tid;
-                bool keep = false;
-                uint32_t g = 0, rw = 0;
-                if (idx < r.y) {
-                    g = __ldg(vals + idx);
-                    if (g >= (uint32_t)P.n) g = 0;  // only reachable with corrupted bins
-                    const ushort4 rc = __ldg(rect + gbase + g);
-                    const int rx0 = max(0, (int)rc.x - x0), rx1 = min(B - 1, (int)rc.z - x0);
-                    const int ry0 = max(0, (int)rc.y - y0), ry1 = min(B - 1, (int)rc.w - y0);
-                    if (rx0 <= rx1 && ry0 <= ry1) {
-                        const uint32_t bits = row_bits(rx0, rx1);
-                        for (int y = ry0; y <= ry1 && !keep; ++y) keep = (sm.alive[y] & bits) != 0u;
-                        rw = (uint32_t)rx0 | ((uint32_t)rx1 << 8) | ((uint32_t)ry0 << 16) | ((uint32_t)ry1 << 24);
-                    }
-                }
-                const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-                if (lane == 0) sm.wscan[warp] = (uint32_t)__popc(bal);
-                __syncthreads();
-                if (warp == 0) {
-                    const uint32_t v = lane < S::NW ? sm.wscan[lane] : 0u;
-                    uint32_t inc = v;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
-                        if (lane >= o) inc += u;
-                    }
-                    if (lane < S::NW) sm.wscan[lane] = inc - v;
-                    if (lane == 31) sm.wtotal = inc;
-                }
-                __syncthreads();
-                const uint32_t rank = nfill + sm.wscan[warp] + (uint32_t)__popc(bal & ((1u << lane) - 1u));
-                if (keep && rank < (uint32_t)S::WAVE) {
-                    sm.gidx[rank] = g;
-                    sm.lpos[rank] = idx;
-                    sm.rect[rank] = rw;
-                }
-                if (keep && rank == (uint32_t)S::WAVE) sm.cut = idx;  // first splat that did not fit
-                __syncthreads();
-                const uint32_t total = sm.wtotal;
-                if (nfill + total > (uint32_t)S::WAVE) {
-                    pos = sm.cut;
-                    nfill = S::WAVE;
-                } else {
-                    pos = min(pos + (uint32_t)S::NT, r.y);
-                    nfill += total;
-                }
-            }
-            if (nfill == 0) break;  // nothing left in the list reaches a live pixel
-            const int wn = (int)nfill;
-            // ---- gather + clear masks
-            {
-                uint32_t *mw = &sm.mask[0][0][0];
-                for (int t = tid; t < S::G * S::NPIX * S::MW; t += S::NT) mw[t] = 0u;
-            }
-            for (int t = tid; t < wn; t += S::NT) {
-                const uint32_t g = sm.gidx[t];
-                const float4 xy = __ldg(xy_depth + gbase + g);
-                const float4 cc = __ldg(rgb + g);
-                sm.off[t] = splat_offset(xy, x0, y0);
-                sm.co[t] = __ldg(conic_op + gbase + g);
-                sm.cz[t] = make_float4(cc.x, cc.y, cc.z, xy.z);
-                sm.nr[t] = __ldg(normal + g);
-            }
-            __syncthreads();
-            // ---- cover: splat-parallel, over the live pixels of each rectangle
-            for (int t = tid; t < wn; t += S::NT) {
-                const uint32_t rw = sm.rect[t];
-                const int rx0 = rw & 0xff, rx1 = (rw >> 8) & 0xff, ry0 = (rw >> 16) & 0xff, ry1 = rw >> 24;
-                const float4 o = sm.off[t], co = sm.co[t];
-                const int k = t / S::CHUNK, b = t % S::CHUNK;
-                const uint32_t bit = 1u << (b & 31);
-                uint32_t *mk = &sm.mask[k][b >> 5][0];
-                const uint32_t rb = row_bits(rx0, rx1);
-                for (int y = ry0; y <= ry1; ++y) {
-                    uint32_t m = sm.alive[y] & rb;
-                    while (m) {
-                        const int x = __ffs(m) - 1;
-                        m &= m - 1u;
-                        if (splat_power(o, co, (float)x, (float)y) < pw_min) continue;
-                        atomicOr(mk + y * B + x, bit);
-                    }
-                }
-            }
-            __syncthreads();
-            // ---- blend: chunk `grp`, composited from T = 1 over its set bits
-            float t_ = 1.f, a0 = 0.f, a1 = 0.f, a2 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f, dd = 0.f;
-            uint32_t lastl = 0;
-            if (!sm.done[pi] && grp * S::CHUNK < wn) {
-#pragma unroll 1
-                for (int w = 0; w < S::MW; ++w) {
-                    uint32_t m = sm.mask[grp][w][pi];
-                    while (m) {
-                        const int j = grp * S::CHUNK + w * 32 + (__ffs(m) - 1);
-                        m &= m - 1u;
-                        const float4 o = sm.off[j], co = sm.co[j];
-                        const float power = splat_power(o, co, lxf, lyf);
-                        if (power < pw_min) continue;
-                        float e;
-                        bool fr;
-                        const float alpha = splat_alpha(co.w, power, amax, e, fr);
-                        if (alpha < afloor) continue;
-                        const float wgt = alpha * t_;
-                        const float4 cz = sm.cz[j], nr = sm.nr[j];
-                        a0 = fmaf(wgt, cz.x, a0);
-                        a1 = fmaf(wgt, cz.y, a1);
-                        a2 = fmaf(wgt, cz.z, a2);
-                        b0 = fmaf(wgt, nr.x, b0);
-                        b1 = fmaf(wgt, nr.y, b1);
-                        b2 = fmaf(wgt, nr.z, b2);
-                        dd = fmaf(wgt, cz.w, dd);
-                        t_ = t_ * (1.f - alpha);
-                        lastl = sm.lpos[j] + 1u;
-                    }
-                }
-            }
-            sm.part[grp][0][pi] = a0;
-            sm.part[grp][1][pi] = a1;
-            sm.part[grp][2][pi] = a2;
-            sm.part[grp][3][pi] = b0;
-            sm.part[grp][4][pi] = b1;
-            sm.part[grp][5][pi] = b2;
-            sm.part[grp][6][pi] = dd;
-            sm.part[grp][7][pi] = t_;
-            sm.plast[grp][pi] = lastl;
-            __syncthreads();
-            // ---- merge the chunks in list order (group 0)
-            if (grp == 0 && !done) {
-                for (int k = 0; k < S::G && k * S::CHUNK < wn; ++k) {
-                    const float Tk = sm.part[k][7][pi];
-                    if (T * Tk >= tmin) {
-                        c0 = fmaf(T, sm.part[k][0][pi], c0);
-                        c1 = fmaf(T, sm.part[k][1][pi], c1);
-                        c2 = fmaf(T, sm.part[k][2][pi], c2);
-                        n0 = fmaf(T, sm.part[k][3][pi], n0);
-                        n1 = fmaf(T, sm.part[k][4][pi], n1);
-                        n2 = fmaf(T, sm.part[k][5][pi], n2);
-                        D = fmaf(T, sm.part[k][6][pi], D);
-                        T = T * Tk;
-                        if (sm.plast[k][pi]) last = sm.plast[k][pi];
-                        continue;
-                    }
-                    // the cutoff falls inside chunk k: walk it from the true T
-                    for (int w = 0; w < S::MW && !done; ++w) {
-                        uint32_t m = sm.mask[k][w][pi];
-                        while (m) {
-                            const int j = k * S::CHUNK + w * 32 + (__ffs(m) - 1);
-                            m &= m - 1u;
-                            const float4 o = sm.off[j], co = sm.co[j];
-                            const float power = splat_power(o, co, lxf, lyf);
-                            if (power < pw_min) continue;
-                            float e;
-                            bool fr;
-                            const float alpha = splat_alpha(co.w, power, amax, e, fr);
-                            if (alpha < afloor) continue;
-                            const float Tn = T * (1.f - alpha);
-                            if (Tn < tmin) {
-                                done = true;
-                                break;
-                            }
-                            const float wgt = alpha * T;
-                            const float4 cz = sm.cz[j], nr = sm.nr[j];
-                            c0 = fmaf(wgt, cz.x, c0);
-                            c1 = fmaf(wgt, cz.y, c1);
-                            c2 = fmaf(wgt, cz.z, c2);
-                            n0 = fmaf(wgt, nr.x, n0);
-                            n1 = fmaf(wgt, nr.y, n1);
-                            n2 = fmaf(wgt, nr.z, n2);
-                            D = fmaf(wgt, cz.w, D);
-                            T = Tn;
-                            last = sm.lpos[j] + 1u;
-                        }
-                    }
-                    if (done) break;
-                }
-                sm.done[pi] = done ? 1 : 0;
-            }
-            if (grp == 0) publish_alive<B>(sm.alive, tid, !done);
-        }
-        if (grp == 0 && inside) {
+        if (seg + 1 < nseg) {
+            const size_t slot = (size_t)(s0 / S) * NB + blk;
+            store_state(states + slot * SW, lane, st);
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) st_release_u32(flags + slot, 1u);
+        } else if (inside) {
             const int64_t HW = (int64_t)V.H * V.W;
             const int64_t p = (int64_t)py * V.W + px;
             if (out_rgb) {
                 float *o = out_rgb + 3 * V.pix_base + p;
-                o[0] = fmaf(T, P.bg[0], c0);
-                o[HW] = fmaf(T, P.bg[1], c1);
-                o[2 * HW] = fmaf(T, P.bg[2], c2);
+                o[0] = fmaf(st.T, P.bg[0], st.c0);
+                o[HW] = fmaf(st.T, P.bg[1], st.c1);
+                o[2 * HW] = fmaf(st.T, P.bg[2], st.c2);
             }
             if (out_nrm) {
                 float *o = out_nrm + 3 * V.pix_base + p;
-                o[0] = n0;
-                o[HW] = n1;
-                o[2 * HW] = n2;
+                o[0] = st.n0;
+                o[HW] = st.n1;
+                o[2 * HW] = st.n2;
             }
-            if (out_depth) out_depth[V.pix_base + p] = D;
-            if (out_alpha) out_alpha[V.pix_base + p] = 1.f - T;
-            if (out_last) out_last[V.pix_base + p] = last;
+            if (out_depth) out_depth[V.pix_base + p] = st.D;
+            if (out_alpha) out_alpha[V.pix_base + p] = 1.f - st.T;
+            if (out_last) out_last[V.pix_base + p] = st.last;
         }
-        __syncthreads();
     }
 }
 
@@ -385,25 +481,19 @@ __global__ void __launch_bounds__(256) fill_empty_kernel(const uint2 *__restrict
 
 int device_sms();
 
-template <int B>
-static cudaError_t launch_blend(const p2e_gaussians *g, const p2e_projected *proj,
-                                const p2e_bins *bins, const Views &P, float *rgb, float *nrm,
-                                float *depth, float *alpha, uint32_t *last, cudaStream_t st) {
-    using S = BlendShape<B>;
-    const size_t smem = sizeof(BlendSmem<B>);
-    static int configured[64] = {0};
+template <int BT>
+static cudaError_t launch_blend(const p2e_gaussians *g, const p2e_projected *proj, const p2e_bins *bins,
+                                const Views &P, float *rgb, float *nrm, float *depth, float *alpha,
+                                uint32_t *last, cudaStream_t st) {
     static int per_sm[64] = {0};
     int dev = 0;
     cudaGetDevice(&dev);
     const int slot = (dev >= 0 && dev < 64) ? dev : 0;
-    if (!configured[slot]) {
-        cudaError_t e = cudaFuncSetAttribute(blend_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
+    if (!per_sm[slot]) {
         int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blend_kernel<B>, S::NT, smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blend_kernel<BT>, kWarps * 32, 0) != cudaSuccess)
+            nb = 0;
         per_sm[slot] = nb > 0 ? nb : 1;
-        configured[slot] = 1;
     }
     cudaError_t e = cudaMemsetAsync(bins->tile_work + 1, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
@@ -413,12 +503,31 @@ static cudaError_t launch_blend(const p2e_gaussians *g, const p2e_projected *pro
     fill_empty_kernel<<<sms * 8, 256, 0, st>>>((const uint2 *)bins->ranges, total_pix, rgb, nrm, depth,
                                                alpha, last, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int64_t sub = P.tile / B;
-    const int64_t grid = std::min<int64_t>((int64_t)sms * per_sm[slot], P.total_tiles * sub * sub);
-    blend_kernel<B><<<(unsigned)grid, S::NT, smem, st>>>(
-        (const uint2 *)bins->ranges, bins->vals[bins->result], bins->tile_work, bins->tile_work + 1,
-        (const float4 *)proj->xy_depth, (const float4 *)proj->conic_op, (const ushort4 *)proj->rect,
-        (const float4 *)g->rgb, (const float4 *)g->normal, rgb, nrm, depth, alpha, last, P);
+    // segment chaining: per-segment states and flags in keys[1 - result]
+    // (8 bytes per key slot), the item table in vals[1 - result]
+    const int other = 1 - bins->result;
+    const int NB = blocks_of(BT);
+    const uint32_t S = seg_of(BT);
+    const int64_t max_slots = bins->capacity / S + 1;
+    const size_t state_bytes = (size_t)max_slots * NB * kStateWords * 32 * sizeof(float);
+    const size_t flag_bytes = (size_t)max_slots * NB * sizeof(uint32_t);
+    const bool allow = bins->keys[other] && bins->vals[other] &&
+                       state_bytes + flag_bytes <= (size_t)bins->capacity * sizeof(uint64_t);
+    float *states = allow ? (float *)bins->keys[other] : nullptr;
+    uint32_t *flags = allow ? (uint32_t *)((char *)bins->keys[other] + state_bytes) : nullptr;
+    uint32_t *item_base = allow ? bins->vals[other] : nullptr;
+    if (allow) {
+        if ((e = cudaMemsetAsync(flags, 0, flag_bytes, st)) != cudaSuccess) return e;
+        render_items_kernel<<<1, 1024, 0, st>>>((const uint2 *)bins->ranges, bins->tile_work, bins->n_keys_dev,
+                                                bins->capacity, 1, BT, item_base);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const int64_t grid = (int64_t)sms * per_sm[slot];
+    blend_kernel<BT><<<(unsigned)grid, kWarps * 32, 0, st>>>(
+        (const uint2 *)bins->ranges, bins->vals[bins->result], bins->tile_work, bins->tile_work + 1, item_base,
+        bins->n_keys_dev, bins->capacity, allow ? 1 : 0, states, flags, (const float4 *)proj->xy_depth,
+        (const float4 *)proj->conic_op, (const ushort4 *)proj->rect, (const float4 *)g->rgb,
+        (const float4 *)g->normal, rgb, nrm, depth, alpha, last, bins->status_dev, P);
     return cudaGetLastError();
 }
 
@@ -426,13 +535,10 @@ cudaError_t launch_render(const p2e_gaussians *g, const p2e_projected *proj, con
                           const Views &P, float *rgb, float *nrm, float *depth, float *alpha,
                           uint32_t *last, cudaStream_t st) {
     if (P.total_tiles == 0) return cudaSuccess;
-    // pixel block of one CTA: 8 x 8 for binning tiles of 8 and 16 (a 16-tile
-    // is shared by four CTAs, each screening the whole list against its
-    // quarter), 16 x 16 for binning tiles of 32
     switch (P.tile) {
         case 8: return launch_blend<8>(g, proj, bins, P, rgb, nrm, depth, alpha, last, st);
-        case 16: return launch_blend<8>(g, proj, bins, P, rgb, nrm, depth, alpha, last, st);
-        case 32: return launch_blend<16>(g, proj, bins, P, rgb, nrm, depth, alpha, last, st);
+        case 16: return launch_blend<16>(g, proj, bins, P, rgb, nrm, depth, alpha, last, st);
+        case 32: return launch_blend<32>(g, proj, bins, P, rgb, nrm, depth, alpha, last, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -357,34 +357,65 @@ __device__ __forceinline__ float4 shepperd_f(const float R[3][3]) {
     return make_float4(w, x, y, z);
 }
 
-constexpr int kRad = 6;       // trial radii of the first pass, in cell sizes
-constexpr int kBuf = 48;      // candidates kept by the second pass
+constexpr int kRad = 6;       // trial radii of the full-block attempt, in cell sizes (0.40 .. 1.00)
+constexpr int kRadA = 8;      // radii of the culled first attempt (0.40 .. 0.75, ratio ~1.09)
+constexpr int kBuf = 32;      // candidates kept by the second pass
 
-// Iterates the candidate points of rings 0..1 around the query's cell
-// (points of the 3x3x3 block, taken from the cell-ordered copy).
+// Iterates the candidate points of the cells of the 3x3x3 block around the
+// query's cell that may hold a point within distance sqrt(R2) of the query
+// (all 27 cells when R2 is infinite), taken from the cell-ordered copy.  A
+// cell is skipped only when its box is farther than the radius by more than
+// 1e-3 cell sizes, far above the rounding of the cell assignment.
 template <typename F>
-__device__ __forceinline__ void for_block(const GridParams &g, const EstScratch &S, const int c0[3], F &&f) {
+__device__ __forceinline__ void for_block(const GridParams &g, const EstScratch &S, const int c0[3],
+                                          const float4 &p, float R2, F &&f) {
+    const float pv[3] = {p.x, p.y, p.z};
+    float lo2[3], hi2[3];  // squared distance to the own cell's lower / upper face, plus margin slack
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float face = g.lo[k] + (float)c0[k] * g.h;
+        const float dl = fmaxf(pv[k] - face - 1e-3f * g.h, 0.f);
+        const float dh = fmaxf(face + g.h - pv[k] - 1e-3f * g.h, 0.f);
+        lo2[k] = dl * dl;
+        hi2[k] = dh * dh;
+    }
     for (int dz = -1; dz <= 1; ++dz) {
         const int cz = c0[2] + dz;
         if (cz < 0 || cz >= g.dim[2]) continue;
+        const float ez = dz < 0 ? lo2[2] : (dz > 0 ? hi2[2] : 0.f);
+        if (ez > R2) continue;
         for (int dy = -1; dy <= 1; ++dy) {
             const int cy = c0[1] + dy;
             if (cy < 0 || cy >= g.dim[1]) continue;
-            const int x0 = max(c0[0] - 1, 0), x1 = min(c0[0] + 1, g.dim[0] - 1);
+            const float ey = ez + (dy < 0 ? lo2[1] : (dy > 0 ? hi2[1] : 0.f));
+            if (ey > R2) continue;
+            const int x0 = (c0[0] > 0 && ey + lo2[0] <= R2) ? c0[0] - 1 : c0[0];
+            const int x1 = (c0[0] + 1 < g.dim[0] && ey + hi2[0] <= R2) ? c0[0] + 1 : c0[0];
             const uint32_t row = (uint32_t)(((int64_t)cz * g.dim[1] + cy) * g.dim[0]);
             // cells x0..x1 of a row are contiguous in the cell-ordered points
             const uint32_t s0 = S.start[row + x0], e0 = S.start[row + x1 + 1];
-            for (uint32_t q = s0; q < e0; ++q) f(S.spts[q]);
+            uint32_t q = s0;
+            for (; q + 4 <= e0; q += 4) {  // four independent loads in flight
+                const float4 a0 = S.spts[q], a1 = S.spts[q + 1], a2 = S.spts[q + 2], a3 = S.spts[q + 3];
+                f(a0);
+                f(a1);
+                f(a2);
+                f(a3);
+            }
+            for (; q < e0; ++q) f(S.spts[q]);
         }
     }
 }
 
 // One thread per query point (points taken in cell order).  Exact 16
 // nearest other points, ties by index:
-//   pass 1  count the block's candidates within kRad trial radii (branch
-//           free) and pick the smallest radius that holds 16 of them; that
-//           radius is at most one cell size, so every point within it lies
-//           in the 3x3x3 block;
+//   pass 1  count the candidates within trial radii (branch free) and pick
+//           the smallest radius that holds 16 of them.  First attempt:
+//           radii up to 0.75 cell sizes over only the cells of the 3x3x3
+//           block that such a ball can reach (about 60 % of the block's
+//           points); if none holds 16, radii up to one cell size over the
+//           whole block.  Every point within the chosen radius lies in the
+//           cells scanned;
 //   pass 2  keep the candidates within the radius (at most kBuf) in shared
 //           memory and select the 16 smallest.
 // A query whose block holds fewer than 16 points within a cell size, or
@@ -405,7 +436,6 @@ __global__ void __launch_bounds__(kKnnThreads) knn_pca_kernel(const float4 *__re
     const float4 p = pq;
     int c0[3];
     cell_of(g, p.x, p.y, p.z, c0);
-    // ---- pass 1: counts within the trial radii (the query itself included)
     float r2[kRad];
 #pragma unroll
     for (int k = 0; k < kRad; ++k) {
@@ -413,25 +443,47 @@ __global__ void __launch_bounds__(kKnnThreads) knn_pca_kernel(const float4 *__re
         const float rr = fminf(f, 1.f) * g.h * (1.f - 1e-4f) - 1e-6f;
         r2[k] = rr * rr;
     }
-    int cnt[kRad] = {0, 0, 0, 0, 0, 0};
-    for_block(g, S, c0, [&](const float4 &pj) {
-        const float ex = pj.x - p.x, ey = pj.y - p.y, ez = pj.z - p.z;
-        const float d = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+    // ---- pass 1, first attempt: culled block, radii 0.40 .. 0.75 cell sizes
+    float rA[kRadA];
 #pragma unroll
-        for (int k = 0; k < kRad; ++k) cnt[k] += d < r2[k] ? 1 : 0;
-    });
-    float T = -1.f;
-    int nbuf = 0;
+    for (int k = 0; k < kRadA; ++k) {
+        const float rr = (0.40f + 0.05f * k) * g.h * (1.f - 1e-4f) - 1e-6f;
+        rA[k] = rr * rr;
+    }
+    float T = -1.f, Rscan = rA[kRadA - 1];
+    {
+        int cnt[kRadA] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for_block(g, S, c0, p, Rscan, [&](const float4 &pj) {
+            const float ex = pj.x - p.x, ey = pj.y - p.y, ez = pj.z - p.z;
+            const float d = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
 #pragma unroll
-    for (int k = kRad - 1; k >= 0; --k)
-        if (cnt[k] >= kK + 1 && cnt[k] <= kBuf + 1) { T = r2[k]; nbuf = cnt[k] - 1; }
+            for (int k = 0; k < kRadA; ++k) cnt[k] += d < rA[k] ? 1 : 0;
+        });
+#pragma unroll
+        for (int k = kRadA - 1; k >= 0; --k)
+            if (cnt[k] >= kK + 1 && cnt[k] <= kBuf + 1) T = rA[k];
+    }
+    if (T < 0.f) {
+        // ---- pass 1, second attempt: the whole block, radii up to one cell
+        Rscan = INFINITY;
+        int cnt[kRad] = {0, 0, 0, 0, 0, 0};
+        for_block(g, S, c0, p, Rscan, [&](const float4 &pj) {
+            const float ex = pj.x - p.x, ey = pj.y - p.y, ez = pj.z - p.z;
+            const float d = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+#pragma unroll
+            for (int k = 0; k < kRad; ++k) cnt[k] += d < r2[k] ? 1 : 0;
+        });
+#pragma unroll
+        for (int k = kRad - 1; k >= 0; --k)
+            if (cnt[k] >= kK + 1 && cnt[k] <= kBuf + 1) T = r2[k];
+    }
     float *bd = s_d + threadIdx.x;
     uint32_t *bj = s_j + threadIdx.x;
     KnnList best{bd, bj};
     if (T > 0.f) {
         // ---- pass 2: the candidates within T, then the 16 smallest
         int m = 0;
-        for_block(g, S, c0, [&](const float4 &pj) {
+        for_block(g, S, c0, p, Rscan, [&](const float4 &pj) {
             const uint32_t j = __float_as_uint(pj.w);
             const float ex = pj.x - p.x, ey = pj.y - p.y, ez = pj.z - p.z;
             const float d = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
@@ -446,6 +498,7 @@ __global__ void __launch_bounds__(kKnnThreads) knn_pca_kernel(const float4 *__re
             int best_k = a;
             float dbst = bd[a * kKnnThreads];
             uint32_t jbst = bj[a * kKnnThreads];
+#pragma unroll 4
             for (int b = a + 1; b < m; ++b) {
                 const float db = bd[b * kKnnThreads];
                 const uint32_t jb = bj[b * kKnnThreads];
@@ -456,7 +509,6 @@ __global__ void __launch_bounds__(kKnnThreads) knn_pca_kernel(const float4 *__re
             bd[a * kKnnThreads] = dbst;
             bj[a * kKnnThreads] = jbst;
         }
-        (void)nbuf;
     } else {
         // ---- fallback: incremental search over growing rings
         for (int k = 0; k < kK; ++k) { best.D(k) = INFINITY; best.J(k) = 0xffffffffu; }

@@ -342,10 +342,11 @@ cudaError_t launch_mlp_estimate(const float *xyz, const float *rgb, int64_t n, c
     }
     static int per_sm[64] = {0};
     if (!per_sm[slot]) {
-        int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mlp_estimate_kernel, kTM, smem);
-        // TMEM: 64 columns per CTA of the SM's 512
-        per_sm[slot] = std::max(1, std::min(nb, 512 / (int)kTmemCols));
+        // resident CTAs per SM: shared memory (1 KB reserved per CTA) and
+        // TMEM (64 columns per CTA of the SM's 512); registers allow more
+        int smem_sm = 0;
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        per_sm[slot] = std::max(1, std::min(smem_sm / (int)(smem + 1024), 512 / (int)kTmemCols));
     }
     const int64_t ntiles = (n + kTM - 1) / kTM;
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms * per_sm[slot]);
