@@ -56,17 +56,29 @@ constexpr int kBW = 8, kBH = 4;    // pixel block of one warp
 constexpr int kWarps = 8;          // warps per CTA
 constexpr int kStateWords = 9;     // T, C0..2, N0..2, D, last | done << 31
 constexpr uint32_t kDoneBit = 1u << 31;
+constexpr uint32_t kIncl = 2u;  // segment flag: inclusive state published
 
 __host__ __device__ constexpr int blocks_of(int tile) { return (tile / kBW) * (tile / kBH); }
 __host__ __device__ constexpr uint32_t seg_of(int tile) { return 256u * (uint32_t)blocks_of(tile); }
 
-struct StageRec {          // the staged splats of one warp
-    float4 off[32];        // (0.5 - frac u, 0.5 - frac v, floor u - x0, floor v - y0)
+struct StageBuf {          // one chunk of staged splats (raw records)
+    float4 xy[32];         // xy_depth record
     float4 co[32];         // (A, B, C, o)
-    float4 cz[32];         // (r, g, b, depth)
+    float4 cc[32];         // rgb
     float4 nr[32];         // (nx, ny, nz, -)
     uint32_t pos[32];      // list position
 };
+struct StageRec {          // per warp: two buffers, filled by cp.async in turn
+    StageBuf b[2];
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 struct PixState {
     float T, c0, c1, c2, n0, n1, n2, D;
@@ -83,26 +95,35 @@ __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool chain_enabled(int allow_chain, const int64_t *n_keys_dev, int64_t capacity,
-                                              uint32_t n_work) {
-    return allow_chain && *n_keys_dev <= capacity && (int64_t)n_work + 1 <= capacity;
-}
+// Layout of the free half of the key double buffer while p2e_render runs:
+//   vals[1 - result] (uint32): [0] chain mode (1 = segments chained),
+//                    [1, n_work + 1] item_base, [n_work + 2, 2 n_work + 2] seg_base
+//   keys[1 - result] (bytes):  segment states (seg-major, kStateWords x 32
+//                    words per block), then one arrival counter and one
+//                    ready flag per (segment, block)
+// item_base[w] / seg_base[w]: first item / first segment of work entry w.
+constexpr int kStateBytes = kStateWords * 32 * 4;
 
-// Item table: item_base[w] = first item of work entry w (exclusive scan of
-// blocks x segments over the work list), item_base[n_work] = total.
-// Chaining (segments of seg_of(tile) splats) is used only when the key
-// count fits the capacity and the table fits vals[1 - result]; otherwise
-// every (tile, block) is one item and no table is needed.
+// Item table (one CTA): exclusive scans of blocks x segments and of
+// segments over the work list, the chain decision, and zeroed counters and
+// flags for the segments in use.  Chaining needs the key count within the
+// capacity and the tables and states within the free buffers; otherwise
+// every (tile, block) is one item and nothing else is written.
 __global__ void __launch_bounds__(1024) render_items_kernel(const uint2 *__restrict__ ranges,
                                                             const uint32_t *__restrict__ work,
                                                             const int64_t *__restrict__ n_keys_dev,
                                                             int64_t capacity, int allow_chain, int tile,
-                                                            uint32_t *__restrict__ item_base) {
+                                                            uint32_t *__restrict__ table, char *__restrict__ store) {
     __shared__ uint32_t s_sum[32], s_off[32];
     __shared__ uint32_t s_carry, s_tot;
     const uint32_t n_work = work[0];
     const uint32_t nb = (uint32_t)blocks_of(tile), S = seg_of(tile);
-    if (!chain_enabled(allow_chain, n_keys_dev, capacity, n_work)) return;
+    const bool fits = allow_chain && *n_keys_dev <= capacity && 2 * (int64_t)n_work + 3 <= capacity;
+    if (!fits) {
+        if (threadIdx.x == 0 && capacity > 0) table[0] = 0u;
+        return;
+    }
+    uint32_t *item_base = table + 1, *seg_base = table + 2 + n_work;
     if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -112,7 +133,7 @@ __global__ void __launch_bounds__(1024) render_items_kernel(const uint2 *__restr
         uint32_t v = 0;
         if (w < n_work) {
             const uint2 r = ranges[work[2 + w]];
-            v = nb * ((r.y - r.x + S - 1) / S);
+            v = (r.y - r.x + S - 1) / S;  // segments of the tile
         }
         uint32_t x = v;  // inclusive scan within the warp
 #pragma unroll
@@ -135,12 +156,26 @@ __global__ void __launch_bounds__(1024) render_items_kernel(const uint2 *__restr
         }
         __syncthreads();
         const uint32_t carry = s_carry;
-        if (w < n_work) item_base[w] = carry + s_off[wid] + x - v;
+        if (w < n_work) {
+            const uint32_t e = carry + s_off[wid] + x - v;
+            seg_base[w] = e;
+            item_base[w] = e * nb;
+        }
         __syncthreads();
         if (threadIdx.x == 0) s_carry = carry + s_tot;
         __syncthreads();
     }
-    if (threadIdx.x == 0) item_base[n_work] = s_carry;
+    const uint32_t total_segs = s_carry;
+    const bool ok = (int64_t)total_segs * nb * (kStateBytes + 8) <= capacity * 8;
+    if (threadIdx.x == 0) {
+        seg_base[n_work] = total_segs;
+        item_base[n_work] = total_segs * nb;
+        table[0] = ok ? 1u : 0u;
+    }
+    if (ok) {  // arrival counters and ready flags of every (segment, block)
+        uint32_t *words = (uint32_t *)(store + (size_t)total_segs * nb * kStateBytes);
+        for (uint32_t t = threadIdx.x; t < 2 * total_segs * nb; t += blockDim.x) words[t] = 0u;
+    }
 }
 
 __device__ __forceinline__ void fresh_state(PixState &s, bool inside) {
@@ -150,30 +185,30 @@ __device__ __forceinline__ void fresh_state(PixState &s, bool inside) {
     s.done = !inside;
 }
 
-// per-lane state words, word-major ([word][lane]: coalesced)
+// per-lane state words, word-major ([word][lane]: coalesced), through L2
 __device__ __forceinline__ void load_state(const float *src, int lane, PixState &s) {
-    s.T = src[0 * 32 + lane];
-    s.c0 = src[1 * 32 + lane];
-    s.c1 = src[2 * 32 + lane];
-    s.c2 = src[3 * 32 + lane];
-    s.n0 = src[4 * 32 + lane];
-    s.n1 = src[5 * 32 + lane];
-    s.n2 = src[6 * 32 + lane];
-    s.D = src[7 * 32 + lane];
-    const uint32_t w = __float_as_uint(src[8 * 32 + lane]);
+    s.T = __ldcg(src + 0 * 32 + lane);
+    s.c0 = __ldcg(src + 1 * 32 + lane);
+    s.c1 = __ldcg(src + 2 * 32 + lane);
+    s.c2 = __ldcg(src + 3 * 32 + lane);
+    s.n0 = __ldcg(src + 4 * 32 + lane);
+    s.n1 = __ldcg(src + 5 * 32 + lane);
+    s.n2 = __ldcg(src + 6 * 32 + lane);
+    s.D = __ldcg(src + 7 * 32 + lane);
+    const uint32_t w = __float_as_uint(__ldcg(src + 8 * 32 + lane));
     s.last = w & ~kDoneBit;
     s.done = (w & kDoneBit) != 0u;
 }
 __device__ __forceinline__ void store_state(float *dst, int lane, const PixState &s) {
-    dst[0 * 32 + lane] = s.T;
-    dst[1 * 32 + lane] = s.c0;
-    dst[2 * 32 + lane] = s.c1;
-    dst[3 * 32 + lane] = s.c2;
-    dst[4 * 32 + lane] = s.n0;
-    dst[5 * 32 + lane] = s.n1;
-    dst[6 * 32 + lane] = s.n2;
-    dst[7 * 32 + lane] = s.D;
-    dst[8 * 32 + lane] = __uint_as_float(s.last | (s.done ? kDoneBit : 0u));
+    __stcg(dst + 0 * 32 + lane, s.T);
+    __stcg(dst + 1 * 32 + lane, s.c0);
+    __stcg(dst + 2 * 32 + lane, s.c1);
+    __stcg(dst + 3 * 32 + lane, s.c2);
+    __stcg(dst + 4 * 32 + lane, s.n0);
+    __stcg(dst + 5 * 32 + lane, s.n1);
+    __stcg(dst + 6 * 32 + lane, s.n2);
+    __stcg(dst + 7 * 32 + lane, s.D);
+    __stcg(dst + 8 * 32 + lane, __uint_as_float(s.last | (s.done ? kDoneBit : 0u)));
 }
 
 // Bits of the 8 x 4 block (bit 8y + x) covered by the block-relative
@@ -185,13 +220,50 @@ __device__ __forceinline__ uint32_t rect_bits(int rx0, int rx1, int ry0, int ry1
     return row * spread;
 }
 
-// Streams list positions [s0, s1) for the warp's block: every lane screens
-// four splats per step of 128 (independent loads), the hits of each chunk
-// of 32 are staged in list order and then composited by every lane for its
-// pixel.  kStop: the stop rule of the
-// sequential recurrence; otherwise a pure product from the given state.
-// With a poll flag, returns early (the position reached, a multiple of 128
-// splats past s0) as soon as the flag is set; otherwise returns s1.
+// Composites the nh staged splats of one buffer for the lane's pixel, in
+// list order.  kStop: the stop rule of the sequential recurrence;
+// otherwise a pure product from the given state.
+template <bool kStop>
+__device__ __forceinline__ void composite_chunk(const StageBuf &sb, int nh, int x0, int y0, float lxf, float lyf,
+                                                const Views &P, PixState &st) {
+    if (st.done) return;
+    const float pw_min = -0.5f * P.sigma_mult * P.sigma_mult;
+    const float amax = P.alpha_max, afloor = P.alpha_floor, tmin = P.t_min;
+    for (int j = 0; j < nh; ++j) {
+        const float4 xy = sb.xy[j], co = sb.co[j];
+        const float4 o = splat_offset(xy, x0, y0);
+        const float power = splat_power(o, co, lxf, lyf);
+        if (power < pw_min) continue;
+        float e;
+        bool fr;
+        const float alpha = splat_alpha(co.w, power, amax, e, fr);
+        if (alpha < afloor) continue;
+        const float Tn = st.T * (1.f - alpha);
+        if (kStop && Tn < tmin) {
+            st.done = true;
+            break;
+        }
+        const float wgt = alpha * st.T;
+        const float4 cc = sb.cc[j], nr = sb.nr[j];
+        st.c0 = fmaf(wgt, cc.x, st.c0);
+        st.c1 = fmaf(wgt, cc.y, st.c1);
+        st.c2 = fmaf(wgt, cc.z, st.c2);
+        st.n0 = fmaf(wgt, nr.x, st.n0);
+        st.n1 = fmaf(wgt, nr.y, st.n1);
+        st.n2 = fmaf(wgt, nr.z, st.n2);
+        st.D = fmaf(wgt, xy.z, st.D);
+        st.T = Tn;
+        st.last = sb.pos[j] + 1u;
+    }
+}
+
+// Streams list positions [s0, s1) for the warp's block.  Every lane
+// screens four splats per step of 128 (independent loads; the next step's
+// indices are fetched one step ahead); the hits of each chunk of 32 are
+// copied (cp.async) into one of two stage buffers in list order while the
+// previous chunk is composited from the other.  With a poll flag, returns
+// early (the position reached, a multiple of 128 splats past s0) as soon as
+// the flag is set; otherwise returns s1.
 template <bool kStop>
 __device__ __forceinline__ uint32_t composite_segment(uint32_t s0, uint32_t s1, int64_t gbase, int x0, int y0,
                                                       float lxf, float lyf, const uint32_t *__restrict__ vals,
@@ -202,24 +274,31 @@ __device__ __forceinline__ uint32_t composite_segment(uint32_t s0, uint32_t s1, 
                                                       const float4 *__restrict__ normal, const Views &P,
                                                       StageRec &sg, int lane, PixState &st,
                                                       const uint32_t *poll = nullptr) {
-    const float pw_min = -0.5f * P.sigma_mult * P.sigma_mult;
-    const float amax = P.alpha_max, afloor = P.alpha_floor, tmin = P.t_min;
+    constexpr int kAhead = 4;  // chunks of 32 screened per step
     const uint32_t lt = (1u << lane) - 1u;
-    constexpr int kAhead = 4;  // chunks of 32 screened per step (independent loads)
+    int cur = 0;               // buffer the next chunk is copied into
+    int pend = 0;              // splats staged in buffer cur ^ 1, not yet composited
+    uint32_t gk[kAhead];
+    auto fetch = [&](uint32_t b, uint32_t (&g)[kAhead]) {
+#pragma unroll
+        for (int k = 0; k < kAhead; ++k) {
+            const uint32_t idx = b + 32u * k + (uint32_t)lane;
+            g[k] = idx < s1 ? __ldg(vals + idx) : 0xffffffffu;
+        }
+    };
+    fetch(s0, gk);
+    uint32_t reached = s1;
     for (uint32_t base = s0; base < s1; base += 32 * kAhead) {
         if (poll) {
             uint32_t ready = 0;
-            if (lane == 0) ready = ld_acquire_u32(poll);
-            if (__shfl_sync(0xffffffffu, ready, 0)) return base;
+            if (lane == 0) ready = ld_acquire_u32(poll) & kIncl;
+            if (__shfl_sync(0xffffffffu, ready, 0)) {
+                reached = base;
+                break;
+            }
         }
         const uint32_t live = __ballot_sync(0xffffffffu, !st.done);
         if (!live) break;
-        uint32_t gk[kAhead];
-#pragma unroll
-        for (int k = 0; k < kAhead; ++k) {
-            const uint32_t idx = base + 32u * k + (uint32_t)lane;
-            gk[k] = idx < s1 ? __ldg(vals + idx) : 0xffffffffu;
-        }
         bool hk[kAhead];
 #pragma unroll
         for (int k = 0; k < kAhead; ++k) {
@@ -232,66 +311,89 @@ __device__ __forceinline__ uint32_t composite_segment(uint32_t s0, uint32_t s1, 
                 if (rx0 <= rx1 && ry0 <= ry1) hk[k] = (rect_bits(rx0, rx1, ry0, ry1) & live) != 0u;
             }
         }
+        uint32_t gcur[kAhead];
+#pragma unroll
+        for (int k = 0; k < kAhead; ++k) gcur[k] = gk[k];
+        if (base + 32 * kAhead < s1) fetch(base + 32 * kAhead, gk);  // next step's indices, in flight
 #pragma unroll
         for (int k = 0; k < kAhead; ++k) {
             const uint32_t hits = __ballot_sync(0xffffffffu, hk[k]);
             if (!hits) continue;
-            const uint32_t g = gk[k];
+            StageBuf &sb = sg.b[cur];
             if (hk[k]) {
                 const int q = __popc(hits & lt);
-                const float4 xy = __ldg(xy_depth + gbase + g);
-                const float4 cc = __ldg(rgb + g);
-                sg.off[q] = splat_offset(xy, x0, y0);
-                sg.co[q] = __ldg(conic_op + gbase + g);
-                sg.cz[q] = make_float4(cc.x, cc.y, cc.z, xy.z);
-                sg.nr[q] = __ldg(normal + g);
-                sg.pos[q] = base + 32u * k + (uint32_t)lane;
+                const uint32_t g = gcur[k];
+                cp_async16(&sb.xy[q], xy_depth + gbase + g);
+                cp_async16(&sb.co[q], conic_op + gbase + g);
+                cp_async16(&sb.cc[q], rgb + g);
+                cp_async16(&sb.nr[q], normal + g);
+                sb.pos[q] = base + 32u * k + (uint32_t)lane;
             }
-            __syncwarp();
-            const int nh = __popc(hits);
-            if (!st.done) {
-                for (int j = 0; j < nh; ++j) {
-                    const float4 o = sg.off[j], co = sg.co[j];
-                    const float power = splat_power(o, co, lxf, lyf);
-                    if (power < pw_min) continue;
-                    float e;
-                    bool fr;
-                    const float alpha = splat_alpha(co.w, power, amax, e, fr);
-                    if (alpha < afloor) continue;
-                    const float Tn = st.T * (1.f - alpha);
-                    if (kStop && Tn < tmin) {
-                        st.done = true;
-                        break;
-                    }
-                    const float wgt = alpha * st.T;
-                    const float4 cz = sg.cz[j], nr = sg.nr[j];
-                    st.c0 = fmaf(wgt, cz.x, st.c0);
-                    st.c1 = fmaf(wgt, cz.y, st.c1);
-                    st.c2 = fmaf(wgt, cz.z, st.c2);
-                    st.n0 = fmaf(wgt, nr.x, st.n0);
-                    st.n1 = fmaf(wgt, nr.y, st.n1);
-                    st.n2 = fmaf(wgt, nr.z, st.n2);
-                    st.D = fmaf(wgt, cz.w, st.D);
-                    st.T = Tn;
-                    st.last = sg.pos[j] + 1u;
-                }
+            cp_async_commit();
+            if (pend) {
+                cp_async_wait_all_but_one();
+                __syncwarp();
+                composite_chunk<kStop>(sg.b[cur ^ 1], pend, x0, y0, lxf, lyf, P, st);
+                __syncwarp();  // buffer cur ^ 1 is free again
             }
-            __syncwarp();
+            pend = __popc(hits);
+            cur ^= 1;
         }
     }
-    return s1;
+    if (pend) {
+        cp_async_wait_all();
+        __syncwarp();
+        composite_chunk<kStop>(sg.b[cur ^ 1], pend, x0, y0, lxf, lyf, P, st);
+        __syncwarp();
+    }
+    return reached;
+}
+
+// C = C_a + T_a C_b, T = T_a T_b: segment b composited after state a.
+__device__ __forceinline__ PixState fold(const PixState &a, const PixState &b) {
+    PixState o;
+    o.c0 = fmaf(a.T, b.c0, a.c0);
+    o.c1 = fmaf(a.T, b.c1, a.c1);
+    o.c2 = fmaf(a.T, b.c2, a.c2);
+    o.n0 = fmaf(a.T, b.n0, a.n0);
+    o.n1 = fmaf(a.T, b.n1, a.n1);
+    o.n2 = fmaf(a.T, b.n2, a.n2);
+    o.D = fmaf(a.T, b.D, a.D);
+    o.T = a.T * b.T;
+    o.last = b.last ? b.last : a.last;
+    o.done = false;
+    return o;
+}
+
+__device__ __forceinline__ uint32_t atomic_add_acq_rel(uint32_t *p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// Publication of a state by the whole warp: every lane's stores, a fence by
+// every lane, then one arrival on `counter` (lane 0, acquire-release).
+// Returns the counter's previous value (uniform); a caller that sees 1
+// arrived second and may read the other party's state.
+__device__ __forceinline__ uint32_t arrive(uint32_t *counter, int lane) {
+    __threadfence();
+    __syncwarp();
+    uint32_t old = 0;
+    if (lane == 0) old = atomic_add_acq_rel(counter, 1u);
+    old = __shfl_sync(0xffffffffu, old, 0);
+    __syncwarp();
+    __threadfence();
+    return old;
 }
 
 template <int BT>
 __global__ void __launch_bounds__(kWarps * 32) blend_kernel(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ work,
-    uint32_t *__restrict__ work_counter, const uint32_t *__restrict__ item_base,
-    const int64_t *__restrict__ n_keys_dev, int64_t capacity, int allow_chain, float *__restrict__ states,
-    uint32_t *__restrict__ flags, const float4 *__restrict__ xy_depth, const float4 *__restrict__ conic_op,
-    const ushort4 *__restrict__ rect, const float4 *__restrict__ rgb, const float4 *__restrict__ normal,
-    float *__restrict__ out_rgb, float *__restrict__ out_nrm, float *__restrict__ out_depth,
-    float *__restrict__ out_alpha, uint32_t *__restrict__ out_last, int32_t *__restrict__ status,
-    __grid_constant__ const Views P) {
+    uint32_t *__restrict__ work_counter, const uint32_t *__restrict__ table, char *__restrict__ store,
+    const float4 *__restrict__ xy_depth, const float4 *__restrict__ conic_op, const ushort4 *__restrict__ rect,
+    const float4 *__restrict__ rgb, const float4 *__restrict__ normal, float *__restrict__ out_rgb,
+    float *__restrict__ out_nrm, float *__restrict__ out_depth, float *__restrict__ out_alpha,
+    uint32_t *__restrict__ out_last, __grid_constant__ const Views P) {
     constexpr int NBX = BT / kBW, NB = blocks_of(BT);
     constexpr uint32_t S = seg_of(BT);
     constexpr int SW = kStateWords * 32;  // state floats of one (segment, block)
@@ -302,8 +404,14 @@ __global__ void __launch_bounds__(kWarps * 32) blend_kernel(
     const float lxf = (float)lx, lyf = (float)ly;
     const float tmin = P.t_min;
     const uint32_t n_work = work[0];
-    const bool chained = chain_enabled(allow_chain, n_keys_dev, capacity, n_work);
+    const bool chained = table && table[0] == 1u;
+    const uint32_t *item_base = chained ? table + 1 : nullptr;
+    const uint32_t *seg_base = chained ? table + 2 + n_work : nullptr;
     const uint32_t total = chained ? item_base[n_work] : n_work * (uint32_t)NB;
+    const uint32_t total_segs = chained ? seg_base[n_work] : 0u;
+    float *states = (float *)store;
+    uint32_t *counters = chained ? (uint32_t *)(store + (size_t)total_segs * NB * kStateBytes) : nullptr;
+    uint32_t *ready = chained ? counters + (size_t)total_segs * NB : nullptr;
 
     for (;;) {
         uint32_t item = 0;
@@ -337,107 +445,111 @@ __global__ void __launch_bounds__(kWarps * 32) blend_kernel(
         const uint2 r = ranges[tile];
         const int64_t gbase = (int64_t)vi * P.n;
         const uint32_t nseg = chained ? (r.y - r.x + S - 1) / S : 1u;
-        const uint32_t s0 = chained ? r.x + seg * S : r.x;
-        const uint32_t s1 = chained ? min(r.y, s0 + S) : r.y;
+        auto seg_lo = [&](uint32_t si) { return chained ? r.x + si * S : r.x; };
+        auto seg_hi = [&](uint32_t si) { return chained ? min(r.y, r.x + (si + 1) * S) : r.y; };
+        // (segment, block) index of the chain's bookkeeping
+        auto sidx = [&](uint32_t si) -> size_t { return ((size_t)__ldg(seg_base + w) + si) * NB + blk; };
 
-        PixState st;
-        fresh_state(st, inside);
+        PixState cur;       // the inclusive state through segment m
+        uint32_t m = seg;
+        fresh_state(cur, inside);
         if (seg == 0) {
-            composite_segment<true>(s0, s1, gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect, rgb, normal,
-                                    P, sg, lane, st);
+            composite_segment<true>(seg_lo(0), seg_hi(0), gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect,
+                                    rgb, normal, P, sg, lane, cur);
         } else {
-            // predecessor: the segment starting S earlier; a non-last segment
-            // starting at list position p keeps its state in slot p / S
-            const size_t pslot = (size_t)((s0 - S) / S) * NB + blk;
-            const uint32_t *pflag = flags + pslot;
-            const float *pstate = states + pslot * SW;
+            // speculate: the segment from T = 1 without stopping (its aggregate)
+            const size_t pi = sidx(seg - 1);
             PixState pr;
-            bool known = __all_sync(0xffffffffu, ld_acquire_u32(pflag) != 0u);
-            if (known) load_state(pstate, lane, pr);
-            // speculate from T = 1 (pure product) for the pixels whose result
-            // may need it; a pixel drops out once the predecessor shows it
-            // done or shows that the stop falls in the part already walked
+            fresh_state(pr, inside);
+            bool known = __all_sync(0xffffffffu, ld_acquire_u32(ready + pi) != 0u);
+            if (known) load_state(states + pi * SW, lane, pr);
+            // pixels the predecessor shows done, or whose stop it shows to lie
+            // in the part already walked, drop out (their result no longer
+            // depends on this aggregate; the latter publish T = 0)
             bool rewalk = false;
-            if (known) st.done = st.done || pr.done;
-            uint32_t reached = composite_segment<false>(s0, s1, gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op,
-                                                        rect, rgb, normal, P, sg, lane, st,
-                                                        known ? nullptr : pflag);
-            if (!known) {
-                // wait (bounded) for the predecessor's inclusive state
-                uint32_t ready = 0;
-                if (lane == 0) {
-                    for (uint32_t it = 0;; ++it) {
-                        ready = ld_acquire_u32(pflag);
-                        // give up at the limit, or at once after another wait gave up
-                        if (ready || it >= kSpinLimit ||
-                            *(volatile int32_t *)status == (int32_t)P2E_ERR_TIMEOUT)
-                            break;
-                        backoff(it);
-                    }
-                    if (!ready) atomicExch(status, (int32_t)P2E_ERR_TIMEOUT);
-                }
-                ready = __shfl_sync(0xffffffffu, ready, 0);
-                if (ready && ld_acquire_u32(pflag)) load_state(pstate, lane, pr);
-                else fresh_state(pr, inside);
-                if (reached < s1) {
-                    rewalk = !pr.done && !st.done && pr.T * st.T < tmin;
-                    st.done = st.done || pr.done || rewalk;
-                    composite_segment<false>(reached, s1, gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect,
-                                             rgb, normal, P, sg, lane, st);
-                }
+            PixState ag;
+            fresh_state(ag, inside);
+            if (known) ag.done = ag.done || pr.done;
+            const uint32_t s0 = seg_lo(seg), s1 = seg_hi(seg);
+            const uint32_t reached = composite_segment<false>(s0, s1, gbase, x0, y0, lxf, lyf, vals, xy_depth,
+                                                              conic_op, rect, rgb, normal, P, sg, lane, ag,
+                                                              known ? nullptr : ready + pi);
+            if (!known && reached < s1) {
+                (void)ld_acquire_u32(ready + pi);
+                load_state(states + pi * SW, lane, pr);
+                rewalk = !pr.done && !ag.done && pr.T * ag.T < tmin;
+                ag.done = ag.done || pr.done || rewalk;
+                composite_segment<false>(reached, s1, gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect, rgb,
+                                         normal, P, sg, lane, ag);
             }
-            // result: the predecessor's state if done; else fold
-            // C = C_in + T_in C_s, T = T_in T_s over the whole segment, unless
-            // the stop falls inside it (T_in T_s < t_min, T non-increasing):
-            // then re-walk the segment from the true state with the stop rule
-            if (pr.done) {
-                st = pr;
-            } else if (!rewalk && pr.T * st.T >= tmin) {
-                st.c0 = fmaf(pr.T, st.c0, pr.c0);
-                st.c1 = fmaf(pr.T, st.c1, pr.c1);
-                st.c2 = fmaf(pr.T, st.c2, pr.c2);
-                st.n0 = fmaf(pr.T, st.n0, pr.n0);
-                st.n1 = fmaf(pr.T, st.n1, pr.n1);
-                st.n2 = fmaf(pr.T, st.n2, pr.n2);
-                st.D = fmaf(pr.T, st.D, pr.D);
-                st.T = pr.T * st.T;
-                if (!st.last) st.last = pr.last;
-                st.done = false;
-            } else {
-                rewalk = true;
+            if (rewalk) ag.T = 0.f;
+            const size_t si = sidx(seg);
+            store_state(states + si * SW, lane, ag);
+            // the second to arrive (this aggregate or the predecessor's
+            // inclusive state) continues the chain
+            if (arrive(counters + si, lane) == 0u) continue;
+            load_state(states + pi * SW, lane, cur);  // the predecessor's inclusive state
+            // combine: fold C = C_in + T_in C_s, T = T_in T_s over the whole
+            // segment, unless the stop falls inside it (T_in T_s < t_min, T
+            // non-increasing): then re-walk it from the true state
+            ag.done = false;
+            bool rw = false;
+            if (!cur.done) {
+                if (cur.T * ag.T >= tmin) cur = fold(cur, ag);
+                else rw = true;
             }
-            if (__any_sync(0xffffffffu, rewalk)) {
-                PixState rw = pr;
-                rw.done = !rewalk;  // only the re-walking pixels take part
+            if (__any_sync(0xffffffffu, rw)) {
+                PixState x = cur;
+                x.done = !rw;  // only the re-walking pixels take part
                 composite_segment<true>(s0, s1, gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect, rgb,
-                                        normal, P, sg, lane, rw);
-                if (rewalk) st = rw;
+                                        normal, P, sg, lane, x);
+                if (rw) cur = x;
             }
         }
-        if (seg + 1 < nseg) {
-            const size_t slot = (size_t)(s0 / S) * NB + blk;
-            store_state(states + slot * SW, lane, st);
+        // publish the chain forward: while the successor's aggregate is
+        // already stored, combine it too
+        while (m + 1 < nseg) {
+            const size_t mi = sidx(m);
+            store_state(states + mi * SW, lane, cur);
             __threadfence();
             __syncwarp();
-            if (lane == 0) st_release_u32(flags + slot, 1u);
-        } else if (inside) {
+            if (lane == 0) st_release_u32(ready + mi, kIncl);  // polled by the successor
+            const size_t ni = sidx(m + 1);
+            if (arrive(counters + ni, lane) == 0u) break;  // the successor continues
+            PixState ag;
+            load_state(states + ni * SW, lane, ag);
+            ++m;
+            bool rw = false;
+            if (!cur.done) {
+                if (cur.T * ag.T >= tmin) cur = fold(cur, ag);
+                else rw = true;
+            }
+            if (__any_sync(0xffffffffu, rw)) {
+                PixState x = cur;
+                x.done = !rw;
+                composite_segment<true>(seg_lo(m), seg_hi(m), gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op,
+                                        rect, rgb, normal, P, sg, lane, x);
+                if (rw) cur = x;
+            }
+        }
+        if (m + 1 == nseg && inside) {  // the last segment's inclusive state is the pixel
             const int64_t HW = (int64_t)V.H * V.W;
             const int64_t p = (int64_t)py * V.W + px;
             if (out_rgb) {
                 float *o = out_rgb + 3 * V.pix_base + p;
-                o[0] = fmaf(st.T, P.bg[0], st.c0);
-                o[HW] = fmaf(st.T, P.bg[1], st.c1);
-                o[2 * HW] = fmaf(st.T, P.bg[2], st.c2);
+                o[0] = fmaf(cur.T, P.bg[0], cur.c0);
+                o[HW] = fmaf(cur.T, P.bg[1], cur.c1);
+                o[2 * HW] = fmaf(cur.T, P.bg[2], cur.c2);
             }
             if (out_nrm) {
                 float *o = out_nrm + 3 * V.pix_base + p;
-                o[0] = st.n0;
-                o[HW] = st.n1;
-                o[2 * HW] = st.n2;
+                o[0] = cur.n0;
+                o[HW] = cur.n1;
+                o[2 * HW] = cur.n2;
             }
-            if (out_depth) out_depth[V.pix_base + p] = st.D;
-            if (out_alpha) out_alpha[V.pix_base + p] = 1.f - st.T;
-            if (out_last) out_last[V.pix_base + p] = st.last;
+            if (out_depth) out_depth[V.pix_base + p] = cur.D;
+            if (out_alpha) out_alpha[V.pix_base + p] = 1.f - cur.T;
+            if (out_last) out_last[V.pix_base + p] = cur.last;
         }
     }
 }
@@ -503,31 +615,22 @@ static cudaError_t launch_blend(const p2e_gaussians *g, const p2e_projected *pro
     fill_empty_kernel<<<sms * 8, 256, 0, st>>>((const uint2 *)bins->ranges, total_pix, rgb, nrm, depth,
                                                alpha, last, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // segment chaining: per-segment states and flags in keys[1 - result]
-    // (8 bytes per key slot), the item table in vals[1 - result]
+    // segment chaining: tables in vals[1 - result], states, counters and
+    // flags in keys[1 - result] (decided on the device by the item table)
     const int other = 1 - bins->result;
-    const int NB = blocks_of(BT);
-    const uint32_t S = seg_of(BT);
-    const int64_t max_slots = bins->capacity / S + 1;
-    const size_t state_bytes = (size_t)max_slots * NB * kStateWords * 32 * sizeof(float);
-    const size_t flag_bytes = (size_t)max_slots * NB * sizeof(uint32_t);
-    const bool allow = bins->keys[other] && bins->vals[other] &&
-                       state_bytes + flag_bytes <= (size_t)bins->capacity * sizeof(uint64_t);
-    float *states = allow ? (float *)bins->keys[other] : nullptr;
-    uint32_t *flags = allow ? (uint32_t *)((char *)bins->keys[other] + state_bytes) : nullptr;
-    uint32_t *item_base = allow ? bins->vals[other] : nullptr;
+    const bool allow = bins->capacity > 0 && bins->keys[other] && bins->vals[other];
+    uint32_t *table = allow ? bins->vals[other] : nullptr;
+    char *store = allow ? (char *)bins->keys[other] : nullptr;
     if (allow) {
-        if ((e = cudaMemsetAsync(flags, 0, flag_bytes, st)) != cudaSuccess) return e;
         render_items_kernel<<<1, 1024, 0, st>>>((const uint2 *)bins->ranges, bins->tile_work, bins->n_keys_dev,
-                                                bins->capacity, 1, BT, item_base);
+                                                bins->capacity, 1, BT, table, store);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int64_t grid = (int64_t)sms * per_sm[slot];
     blend_kernel<BT><<<(unsigned)grid, kWarps * 32, 0, st>>>(
-        (const uint2 *)bins->ranges, bins->vals[bins->result], bins->tile_work, bins->tile_work + 1, item_base,
-        bins->n_keys_dev, bins->capacity, allow ? 1 : 0, states, flags, (const float4 *)proj->xy_depth,
-        (const float4 *)proj->conic_op, (const ushort4 *)proj->rect, (const float4 *)g->rgb,
-        (const float4 *)g->normal, rgb, nrm, depth, alpha, last, bins->status_dev, P);
+        (const uint2 *)bins->ranges, bins->vals[bins->result], bins->tile_work, bins->tile_work + 1, table, store,
+        (const float4 *)proj->xy_depth, (const float4 *)proj->conic_op, (const ushort4 *)proj->rect,
+        (const float4 *)g->rgb, (const float4 *)g->normal, rgb, nrm, depth, alpha, last, P);
     return cudaGetLastError();
 }
 
