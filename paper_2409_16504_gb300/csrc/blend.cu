@@ -5,42 +5,39 @@
 // 2.5 m fills ~150 of 4096 16-px tiles at 1024^2) with long depth lists
 // (up to ~40K splats), so neither a CTA per tile nor a thread per pixel
 // keeps the GPU busy.  Here one WARP owns an 8 x 4 pixel block (lane =
-// pixel) of one binning tile and one SEGMENT of the tile's list (256 splats
-// per block of the tile, e.g. 2048 for 16-px tiles); warps are fully
-// independent (no block-wide barrier) and pull (tile, segment, block) items
-// from a global counter, tiles in work-list order (longest first).
+// pixel) of one binning tile, and a tile's list is cut into SEGMENTS of 128
+// splats per block of the tile (1024 for 16-px tiles).  Warps are fully
+// independent (no block-wide barrier, no waiting) and pull (tile, segment,
+// block) items from a global counter, tiles in work-list order (longest
+// first).
 //
-// Per item the warp streams its segment in chunks of 32 splats: every lane
-// loads one splat's index and pixel rectangle, the warp keeps (ballot) the
-// splats whose rectangle meets a live pixel of the block, stages their
-// records in shared memory in list order, and then every lane composites
-// the staged splats for its pixel in order (broadcast shared-memory reads,
-// one splat per step for all 32 pixels).
+// Per segment the warp streams the list in steps of 128 splats: every lane
+// loads four indices (one step ahead) and pixel rectangles; the warp keeps
+// (ballot) the splats whose rectangle meets a live pixel of the block; their
+// records are copied (cp.async) in list order into one of two shared-memory
+// stage buffers while the previous chunk of 32 is composited from the other
+// (broadcast reads, one splat per step for all 32 pixels).
 //
-// Segments of one (tile, block) are chained like a decoupled look-back
-// scan under the associative "over" operator:
-//   segment 0    composite from T = 1 with the stop rule: exactly the
-//                sequential recurrence;
-//   later ones   composite the segment from T = 1 without stopping (a pure
-//                product), then fold with the predecessor's inclusive state:
-//                C = C_in + T_in C_s, T = T_in T_s.  T is non-increasing, so
-//                the stop can only fall inside the segment when
-//                T_in T_s < t_min; those pixels re-walk the segment from the
-//                true state with the stop rule, which reproduces the
-//                sequential result.  The predecessor is polled every 128
-//                splats: pixels it shows done, or whose stop it shows to lie
-//                in the part already walked, drop out of the speculation
-//                (their result no longer depends on it), so saturated
-//                surfaces cost little.  Which rule gives a pixel's result
-//                depends only on the data, never on timing: results are
-//                deterministic.
-// A segment that is not the last publishes its inclusive per-pixel state
-// (T, C, N, D, last | done) and a ready flag; the last one writes the image.
-// The predecessor holds an earlier item, taken by a running warp, so every
-// wait ends; waits are still bounded and a wait that gives up records
-// P2E_ERR_TIMEOUT.  The per-segment states live in the free half of the key
-// double buffer (keys[1 - result]), the item table in vals[1 - result].
-// Without room there (tiny capacities) every (tile, block) is one exact item.
+// Segments are combined under the associative "over" operator:
+//   segment 0   composited from T = 1 with the stop rule: exactly the
+//               sequential recurrence;
+//   segment s   its aggregate: composited from T = 1 without stopping.  The
+//               state after it is fold(state before, aggregate):
+//               C = C_in + T_in C_s, T = T_in T_s, unless the stop falls
+//               inside the segment (T_in T_s < t_min, T non-increasing):
+//               then the segment is re-walked from the true state with the
+//               stop rule, which reproduces the sequential result.
+// Chained schedule: the aggregate and the predecessor's state are stored in
+// the free half of the key double buffer; whichever of the two arrives
+// second (an acquire-release counter) computes the segment's state and
+// carries the chain on while successors' aggregates are already there; the
+// last segment's state is the pixel.  While it speculates, a warp polls the
+// predecessor's state: pixels it shows done, or whose stop it shows to lie
+// in the part already walked, drop out (their aggregate is not used; the
+// latter publish T = 0).  Without room for the states (small capacities)
+// one warp runs the same segments of a (tile, block) in turn.  Which rule
+// gives a pixel's result depends only on its tile's list: results are
+// bit-identical across schedules, batches and runs.
 //
 // Sub-pixel accuracy: the pixel offset is formed as
 //   (x - (floor(u) - x0)) + (0.5 - frac(u)),
@@ -59,7 +56,10 @@ constexpr uint32_t kDoneBit = 1u << 31;
 constexpr uint32_t kIncl = 2u;  // segment flag: inclusive state published
 
 __host__ __device__ constexpr int blocks_of(int tile) { return (tile / kBW) * (tile / kBH); }
-__host__ __device__ constexpr uint32_t seg_of(int tile) { return 256u * (uint32_t)blocks_of(tile); }
+// Segment length: 128 splats per pixel block of the tile (1024 for 16-px
+// tiles).  It is fixed, so a pixel's arithmetic depends only on its tile's
+// list, never on the capacity, the other views of the call, or timing.
+__host__ __device__ constexpr uint32_t seg_len(int tile) { return 128u * (uint32_t)blocks_of(tile); }
 
 struct StageBuf {          // one chunk of staged splats (raw records)
     float4 xy[32];         // xy_depth record
@@ -96,7 +96,7 @@ __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
 }
 
 // Layout of the free half of the key double buffer while p2e_render runs:
-//   vals[1 - result] (uint32): [0] chain mode (1 = segments chained),
+//   vals[1 - result] (uint32): [0] 1 when segments are chained across warps,
 //                    [1, n_work + 1] item_base, [n_work + 2, 2 n_work + 2] seg_base
 //   keys[1 - result] (bytes):  segment states (seg-major, kStateWords x 32
 //                    words per block), then one arrival counter and one
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(1024) render_items_kernel(const uint2 *__restr
     __shared__ uint32_t s_sum[32], s_off[32];
     __shared__ uint32_t s_carry, s_tot;
     const uint32_t n_work = work[0];
-    const uint32_t nb = (uint32_t)blocks_of(tile), S = seg_of(tile);
+    const uint32_t nb = (uint32_t)blocks_of(tile), S = seg_len(tile);
     const bool fits = allow_chain && *n_keys_dev <= capacity && 2 * (int64_t)n_work + 3 <= capacity;
     if (!fits) {
         if (threadIdx.x == 0 && capacity > 0) table[0] = 0u;
@@ -386,8 +386,34 @@ __device__ __forceinline__ uint32_t arrive(uint32_t *counter, int lane) {
     return old;
 }
 
+// The inclusive state after a segment, from the state before it (cur) and
+// the segment's aggregate (ag: composited from T = 1 without stopping):
+// fold C = C_in + T_in C_s, T = T_in T_s, unless the stop falls inside the
+// segment (T_in T_s < t_min; T is non-increasing): then the segment is
+// re-walked from the true state with the stop rule.  An aggregate with
+// T = 0 marks a pixel whose stop is already known to fall inside.
+__device__ __forceinline__ void combine(PixState &cur, const PixState &ag, uint32_t s0, uint32_t s1,
+                                        int64_t gbase, int x0, int y0, float lxf, float lyf,
+                                        const uint32_t *__restrict__ vals, const float4 *__restrict__ xy_depth,
+                                        const float4 *__restrict__ conic_op, const ushort4 *__restrict__ rect,
+                                        const float4 *__restrict__ rgb, const float4 *__restrict__ normal,
+                                        const Views &P, StageRec &sg, int lane) {
+    bool rw = false;
+    if (!cur.done) {
+        if (cur.T * ag.T >= P.t_min) cur = fold(cur, ag);
+        else rw = true;
+    }
+    if (__any_sync(0xffffffffu, rw)) {
+        PixState x = cur;
+        x.done = !rw;  // only the re-walking pixels take part
+        composite_segment<true>(s0, s1, gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect, rgb, normal, P,
+                                sg, lane, x);
+        if (rw) cur = x;
+    }
+}
+
 template <int BT>
-__global__ void __launch_bounds__(kWarps * 32) blend_kernel(
+__global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ work,
     uint32_t *__restrict__ work_counter, const uint32_t *__restrict__ table, char *__restrict__ store,
     const float4 *__restrict__ xy_depth, const float4 *__restrict__ conic_op, const ushort4 *__restrict__ rect,
@@ -395,7 +421,6 @@ __global__ void __launch_bounds__(kWarps * 32) blend_kernel(
     float *__restrict__ out_nrm, float *__restrict__ out_depth, float *__restrict__ out_alpha,
     uint32_t *__restrict__ out_last, __grid_constant__ const Views P) {
     constexpr int NBX = BT / kBW, NB = blocks_of(BT);
-    constexpr uint32_t S = seg_of(BT);
     constexpr int SW = kStateWords * 32;  // state floats of one (segment, block)
     __shared__ StageRec stage[kWarps];
     const int lane = threadIdx.x & 31;
@@ -404,6 +429,9 @@ __global__ void __launch_bounds__(kWarps * 32) blend_kernel(
     const float lxf = (float)lx, lyf = (float)ly;
     const float tmin = P.t_min;
     const uint32_t n_work = work[0];
+    constexpr uint32_t S = seg_len(BT);
+    // chained: one item per (tile, segment, block); otherwise one per
+    // (tile, block), whose warp runs the same segments in turn
     const bool chained = table && table[0] == 1u;
     const uint32_t *item_base = chained ? table + 1 : nullptr;
     const uint32_t *seg_base = chained ? table + 2 + n_work : nullptr;
@@ -444,16 +472,31 @@ __global__ void __launch_bounds__(kWarps * 32) blend_kernel(
         const bool inside = px < V.W && py < V.H;
         const uint2 r = ranges[tile];
         const int64_t gbase = (int64_t)vi * P.n;
-        const uint32_t nseg = chained ? (r.y - r.x + S - 1) / S : 1u;
-        auto seg_lo = [&](uint32_t si) { return chained ? r.x + si * S : r.x; };
-        auto seg_hi = [&](uint32_t si) { return chained ? min(r.y, r.x + (si + 1) * S) : r.y; };
+        const uint32_t nseg = (r.y - r.x + S - 1) / S;
+        auto seg_lo = [&](uint32_t si) { return r.x + si * S; };
+        auto seg_hi = [&](uint32_t si) { return min(r.y, r.x + (si + 1) * S); };
         // (segment, block) index of the chain's bookkeeping
         auto sidx = [&](uint32_t si) -> size_t { return ((size_t)__ldg(seg_base + w) + si) * NB + blk; };
 
         PixState cur;       // the inclusive state through segment m
         uint32_t m = seg;
         fresh_state(cur, inside);
-        if (seg == 0) {
+        if (!chained) {
+            // the chain in one warp: segment 0 exact, every later one
+            // speculated from T = 1 and combined, as the chained schedule does
+            composite_segment<true>(seg_lo(0), seg_hi(0), gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect,
+                                    rgb, normal, P, sg, lane, cur);
+            for (m = 1; m < nseg; ++m) {
+                PixState ag;
+                fresh_state(ag, inside);
+                ag.done = ag.done || cur.done;
+                composite_segment<false>(seg_lo(m), seg_hi(m), gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op,
+                                         rect, rgb, normal, P, sg, lane, ag);
+                combine(cur, ag, seg_lo(m), seg_hi(m), gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect, rgb,
+                        normal, P, sg, lane);
+            }
+            m = nseg - 1;
+        } else if (seg == 0) {
             composite_segment<true>(seg_lo(0), seg_hi(0), gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect,
                                     rgb, normal, P, sg, lane, cur);
         } else {
@@ -489,26 +532,12 @@ __global__ void __launch_bounds__(kWarps * 32) blend_kernel(
             // inclusive state) continues the chain
             if (arrive(counters + si, lane) == 0u) continue;
             load_state(states + pi * SW, lane, cur);  // the predecessor's inclusive state
-            // combine: fold C = C_in + T_in C_s, T = T_in T_s over the whole
-            // segment, unless the stop falls inside it (T_in T_s < t_min, T
-            // non-increasing): then re-walk it from the true state
-            ag.done = false;
-            bool rw = false;
-            if (!cur.done) {
-                if (cur.T * ag.T >= tmin) cur = fold(cur, ag);
-                else rw = true;
-            }
-            if (__any_sync(0xffffffffu, rw)) {
-                PixState x = cur;
-                x.done = !rw;  // only the re-walking pixels take part
-                composite_segment<true>(s0, s1, gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect, rgb,
-                                        normal, P, sg, lane, x);
-                if (rw) cur = x;
-            }
+            combine(cur, ag, s0, s1, gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect, rgb, normal, P, sg,
+                    lane);
         }
         // publish the chain forward: while the successor's aggregate is
         // already stored, combine it too
-        while (m + 1 < nseg) {
+        while (chained && m + 1 < nseg) {
             const size_t mi = sidx(m);
             store_state(states + mi * SW, lane, cur);
             __threadfence();
@@ -519,18 +548,8 @@ __global__ void __launch_bounds__(kWarps * 32) blend_kernel(
             PixState ag;
             load_state(states + ni * SW, lane, ag);
             ++m;
-            bool rw = false;
-            if (!cur.done) {
-                if (cur.T * ag.T >= tmin) cur = fold(cur, ag);
-                else rw = true;
-            }
-            if (__any_sync(0xffffffffu, rw)) {
-                PixState x = cur;
-                x.done = !rw;
-                composite_segment<true>(seg_lo(m), seg_hi(m), gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op,
-                                        rect, rgb, normal, P, sg, lane, x);
-                if (rw) cur = x;
-            }
+            combine(cur, ag, seg_lo(m), seg_hi(m), gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect, rgb,
+                    normal, P, sg, lane);
         }
         if (m + 1 == nseg && inside) {  // the last segment's inclusive state is the pixel
             const int64_t HW = (int64_t)V.H * V.W;
