@@ -315,6 +315,30 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = a.elapsed_time(b) / e_steps
 
+    # the rows beyond the frame: relighting of the 1024^2 view from its normal
+    # image (HBM bound: 28 B read + 12 B written per pixel) and the global
+    # isotropic estimator (kNN-PCA + mean spacing), each timed alone
+    from paper_2409_16504_gb300 import relight
+    lights = [(0.3, 0.8, -0.5, 0.9), (-1.0, 0.2, 0.1, 0.3)]
+    shaded = torch.empty_like(img.rgb)
+
+    def timed_op(fn, reps=20):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1)
+            x0, x1 = ev(), ev()
+            x0.record(st)
+            fn()
+            x1.record(st)
+            torch.cuda.synchronize()
+            ts.append(x0.elapsed_time(x1))
+        return float(np.median(ts))
+    relight_ms = timed_op(lambda: relight(img, lights, ambient=0.15, out=shaded))
+    relight_gbs = RES * RES * 40 / (relight_ms / 1e3) / 1e9
+    glob_ms = timed_op(lambda: est.global_(cx, cc, 1.5, out=gs))
+
     # roofline of the dominant stage (one C-ABI call, timed by CUDA events on
     # its stream): algorithmic DRAM bytes per call / its mean duration
     peaks, src_peak = measured_peaks()
@@ -365,7 +389,10 @@ def main():
             "clocks": clocks, "gpu_launches": sum(launches_per_frame[p] for p in paths) * args.steps,
             "e2e": {"value": world * RES * RES / (e2e_ms / 1e3) / 1e6, "unit": "Mpix/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "roofline": roof}
+            "roofline": roof,
+            "beyond_frame": {"relight_1024": {"ms": relight_ms, "achieved_gbs": relight_gbs,
+                                              "frac_hbm": relight_gbs / peaks["hbm_gbs"]},
+                             "global_estimate_800k_ms": glob_ms}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(head_path)
     if rank == 0:

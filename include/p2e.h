@@ -48,6 +48,7 @@ typedef enum {
 } p2e_status;
 
 #define P2E_MAX_VIEWS 64
+#define P2E_MAX_LIGHTS 8
 
 /* Pinhole camera (Sec. 3.1, Eq. 3-4), host memory.
  * viewmat: row-major 3x4 [T | t] mapping world to camera coordinates
@@ -318,6 +319,35 @@ p2e_status p2e_adam(float *params, float *grad, float *m, float *v, int64_t coun
                     float beta1, float beta2, float eps, int32_t step, void *blob, void *stream);
 
 /* Human-readable name of a status code (static storage). */
+/* ---- the global isotropic baseline and relighting ------------------- */
+
+/* p2e_estimate_global -- the comparison estimator of Sec. 4.1 ("surface
+ * splatting using the same isotropic Gaussian representing each point"):
+ * every Gaussian gets the isotropic scale sigma_rel * d, d the average
+ * distance of a point to its nearest neighbour over the cloud (the global
+ * point density), the identity rotation and opacity `opacity`; the normal
+ * is the kNN-PCA normal (so the normal image can still be rendered).
+ * sigma_rel > 0 (the paper compares 1.2, 1.5 and 1.7).  Arguments
+ * otherwise as p2e_estimate (same scratch size). */
+p2e_status p2e_estimate_global(const float *xyz, const float *rgb, int64_t n, float sigma_rel, float opacity,
+                               p2e_gaussians *out, uint32_t *knn_idx, void *scratch, int64_t scratch_bytes,
+                               void *stream);
+
+/* p2e_relight -- late shading of rendered views from their normal images
+ * (Sec. 3.1: the normal map feeds a pixel shader).  Lambertian with
+ * directional lights and an ambient term, per pixel:
+ *   C = rgb - (1 - alpha) bg,  n^ = normal / |normal|,
+ *   s = ambient + sum_l I_l max(0, n^ . l_l),  out = C s + (1 - alpha) bg;
+ * a pixel whose |normal| <= 1e-12 keeps s = 1.
+ * rgb, normal, alpha: device planar images as p2e_render writes them (views
+ * concatenated); view_pixels (host) holds H*W of each of n_views views.
+ * lights (host): n_lights (<= P2E_MAX_LIGHTS) x (dx, dy, dz, intensity),
+ * directions in the normals' (world) frame, normalised here; bg (host,
+ * 3 floats) or NULL for black.  out: device planar rgb (may alias rgb). */
+p2e_status p2e_relight(const float *rgb, const float *normal, const float *alpha, const int64_t *view_pixels,
+                       int32_t n_views, const float *lights, int32_t n_lights, float ambient, const float *bg,
+                       float *out, void *stream);
+
 const char *p2e_status_string(p2e_status s);
 
 #ifdef __cplusplus

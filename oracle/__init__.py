@@ -257,6 +257,49 @@ def estimate_pca(xyz, rgb, opacity: float = 0.9, kappa: float = 1.0, flat: float
                 rgb=np.asarray(rgb, np.float32), normal=e["normal"].astype(np.float32))
 
 
+def mean_nn_distance(xyz) -> float:
+    """The cloud's average point distance d: the mean over points of the
+    distance to the nearest other point (FP64)."""
+    _, d2 = knn(xyz)
+    return float(np.sqrt(d2[:, 0]).mean())
+
+
+def estimate_global(xyz, rgb, sigma_rel: float, opacity: float = 0.9) -> dict:
+    """The comparison estimator of Sec. 4.1 (one isotropic Gaussian size for
+    the whole cloud, from the global point density): scale sigma_rel * d
+    on every axis, identity rotation; the normal is the kNN-PCA normal."""
+    idx, d2 = knn(xyz)
+    e = pca(xyz, idx)
+    n = len(xyz)
+    d = float(np.sqrt(d2[:, 0]).mean())
+    return dict(mean=np.asarray(xyz, np.float32), scale=np.full((n, 3), sigma_rel * d, np.float32),
+                quat=np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)), opacity=np.full(n, opacity, np.float32),
+                rgb=np.asarray(rgb, np.float32), normal=e["normal"].astype(np.float32), dbar=d)
+
+
+def relight(rgb, normal, alpha, lights, ambient: float, bg=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """Late shading of one view from its rendered normal image (Sec. 3.1: a
+    pixel shader on the normal map), Lambertian directional lights plus
+    ambient, in FP64: C = rgb - (1 - alpha) bg, n^ = N / |N|,
+    s = ambient + sum_l I_l max(0, n^ . l^_l) (s = 1 where |N| <= 1e-12),
+    out = C s + (1 - alpha) bg.  rgb, normal: (3, H, W); alpha: (H, W)."""
+    rgb = np.asarray(rgb, np.float64)
+    N = np.asarray(normal, np.float64)
+    a = np.asarray(alpha, np.float64)
+    bgv = np.asarray(bg, np.float64)[:, None, None]
+    C = rgb - (1.0 - a)[None] * bgv
+    norm = np.sqrt((N * N).sum(0))
+    has = norm > 1e-12
+    nh = np.where(has[None], N / np.where(has, norm, 1.0)[None], 0.0)
+    s = np.full(a.shape, float(ambient))
+    for lx, ly, lz, inten in lights:
+        l = np.array([lx, ly, lz], np.float64)
+        l = l / np.linalg.norm(l)
+        s = s + inten * np.maximum(0.0, np.einsum("chw,c->hw", nh, l))
+    s = np.where(has, s, 1.0)
+    return C * s[None] + (1.0 - a)[None] * bgv
+
+
 def sigma_of(scale, quat) -> np.ndarray:
     """Sigma = R diag(s^2) R^T for each row (quaternions normalised)."""
     q = np.asarray(quat, np.float64)

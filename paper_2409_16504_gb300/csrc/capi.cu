@@ -16,6 +16,9 @@ size_t sort_scratch_bytes(int64_t n_total, int64_t capacity);
 int sort_passes(int64_t total_tiles);
 size_t backward_scratch_bytes(int64_t n_total);
 size_t estimate_scratch_bytes(int64_t n);
+cudaError_t launch_estimate_global(const float *xyz, const float *rgb, int64_t n, float sigma_rel, float opacity,
+                                   p2e_gaussians *out, uint32_t *knn_idx, void *scratch, int num_sms,
+                                   cudaStream_t st);
 cudaError_t launch_render_backward(const p2e_gaussians *g, const p2e_projected *proj,
                                    const p2e_bins *bins, const Views &P, const float *alpha,
                                    const uint32_t *last, const float *d_rgb, const float *d_normal,
@@ -257,6 +260,26 @@ p2e_status p2e_estimate(const float *xyz, const float *rgb, int64_t n, int32_t m
     cudaError_t e = launch_estimate(xyz, rgb, n, mode, mlp_weights, pca_opacity, out, knn_idx, scratch,
                                     device_sms(), (cudaStream_t)stream);
     if (e == cudaErrorNotSupported) return P2E_ERR_UNSUPPORTED;
+    return e == cudaSuccess ? P2E_OK : P2E_ERR_CUDA;
+}
+
+p2e_status p2e_estimate_global(const float *xyz, const float *rgb, int64_t n, float sigma_rel, float opacity,
+                               p2e_gaussians *out, uint32_t *knn_idx, void *scratch, int64_t scratch_bytes,
+                               void *stream) {
+    if (n < 0 || n >= (int64_t(1) << 31) || !out) return P2E_ERR_INVALID_ARG;
+    if (!fin(opacity) || opacity < 0.f || opacity > 1.f || !fin(sigma_rel) || !(sigma_rel > 0.f))
+        return P2E_ERR_INVALID_ARG;
+    if (n == 0) return P2E_OK;
+    if (n < 17) return P2E_ERR_INVALID_ARG;
+    if (!xyz || !rgb || !aligned16(xyz) || !aligned16(rgb)) return P2E_ERR_INVALID_ARG;
+    if (!out->mean_op || !out->scale || !out->quat || !out->rgb || !out->normal) return P2E_ERR_INVALID_ARG;
+    if (!aligned16(out->mean_op) || !aligned16(out->scale) || !aligned16(out->quat) ||
+        !aligned16(out->rgb) || !aligned16(out->normal))
+        return P2E_ERR_INVALID_ARG;
+    if (scratch_bytes < (int64_t)estimate_scratch_bytes(n) || !scratch || ((uintptr_t)scratch & 255u))
+        return P2E_ERR_INVALID_ARG;
+    cudaError_t e = launch_estimate_global(xyz, rgb, n, sigma_rel, opacity, out, knn_idx, scratch, device_sms(),
+                                           (cudaStream_t)stream);
     return e == cudaSuccess ? P2E_OK : P2E_ERR_CUDA;
 }
 

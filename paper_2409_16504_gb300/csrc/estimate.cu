@@ -663,4 +663,51 @@ cudaError_t launch_estimate(const float *xyz, const float *rgb, int64_t n, int32
     return cudaSuccess;
 }
 
+// The global isotropic baseline: the mean nearest-neighbour distance over
+// the cloud (double sum, one atomic per CTA), then every Gaussian gets scale
+// sigma_rel times it, the identity rotation; mean, opacity, colour and the
+// PCA normal stay as the kNN-PCA pass wrote them.
+__global__ void __launch_bounds__(256) nn_dist_sum_kernel(const float4 *__restrict__ xyz, int64_t n,
+                                                          const uint32_t *__restrict__ knn, double *sum) {
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 p = __ldg(xyz + i), q = __ldg(xyz + knn[i * kK]);
+        const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+        acc += (double)sqrtf(dx * dx + dy * dy + dz * dz);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double s_w[8];
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_w[w];
+        atomicAdd(sum, t);
+    }
+}
+
+__global__ void __launch_bounds__(256) global_scale_kernel(int64_t n, const double *sum, float sigma_rel,
+                                                           float4 *__restrict__ scale, float4 *__restrict__ quat) {
+    const float s = (float)((double)sigma_rel * (*sum / (double)n));
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        scale[i] = make_float4(s, s, s, 0.f);
+        quat[i] = make_float4(1.f, 0.f, 0.f, 0.f);
+    }
+}
+
+cudaError_t launch_estimate_global(const float *xyz, const float *rgb, int64_t n, float sigma_rel, float opacity,
+                                   p2e_gaussians *out, uint32_t *knn_idx, void *scratch, int num_sms,
+                                   cudaStream_t st) {
+    EstScratch S;
+    est_layout(n, scratch, &S);
+    uint32_t *knn = knn_idx ? knn_idx : S.knn;
+    cudaError_t e = launch_estimate(xyz, rgb, n, 0, nullptr, opacity, out, knn, scratch, num_sms, st);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(S.sum, 0, sizeof(double), st)) != cudaSuccess) return e;
+    nn_dist_sum_kernel<<<num_sms * 2, 256, 0, st>>>((const float4 *)xyz, n, knn, S.sum);
+    global_scale_kernel<<<num_sms * 4, 256, 0, st>>>(n, S.sum, sigma_rel, (float4 *)out->scale,
+                                                     (float4 *)out->quat);
+    return cudaGetLastError();
+}
+
 }  // namespace p2e

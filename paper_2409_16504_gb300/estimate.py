@@ -47,6 +47,22 @@ class Estimator:
         return out
 
 
+    def global_(self, xyz: torch.Tensor, rgb: torch.Tensor, sigma_rel: float, opacity: float = 0.9,
+                out: GaussianSet | None = None, knn: torch.Tensor | None = None, stream=None) -> GaussianSet:
+        """The global isotropic baseline: scale sigma_rel x the cloud's mean
+        nearest-neighbour distance for every point (p2e_estimate_global)."""
+        n = xyz.shape[0]
+        assert xyz.shape == (n, 4) and rgb.shape == (n, 4)
+        self._grow(n)
+        out = out or GaussianSet.empty(n, xyz.device)
+        gs = out.c_struct()
+        sp = (self.scratch.data_ptr() + 255) & ~255
+        check("p2e_estimate_global", _lib.load().p2e_estimate_global(
+            _ptr(xyz), _ptr(rgb), n, C.c_float(sigma_rel), C.c_float(opacity), C.byref(gs), _ptr(knn),
+            C.c_void_p(sp), self.scratch_bytes, _stream(stream)))
+        return out
+
+
 def cloud_tensors(xyz, rgb, device="cuda"):
     """(n,3) numpy point/colour arrays -> float4 device tensors."""
     import numpy as np

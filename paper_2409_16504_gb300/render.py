@@ -263,6 +263,25 @@ class Renderer:
         raise _lib.P2EError("p2e_sort_bin", _lib.P2E_ERR_CAPACITY)
 
 
+def relight(img: Images, lights, ambient: float = 0.2, bg=(0.0, 0.0, 0.0), out: torch.Tensor | None = None,
+            stream=None) -> torch.Tensor:
+    """Late shading of rendered views from their normal images
+    (p2e_relight): Lambertian directional lights plus ambient.  ``lights``:
+    sequence of (dx, dy, dz, intensity) in the normals' world frame.  Returns
+    the planar rgb of all views (``out`` may be ``img.rgb``)."""
+    lib = _lib.load()
+    lt = [float(v) for l4 in lights for v in l4]
+    if len(lt) % 4:
+        raise ValueError("lights are (dx, dy, dz, intensity) tuples")
+    la = (C.c_float * max(len(lt), 1))(*lt)
+    bga = (C.c_float * 3)(*[float(b) for b in bg])
+    vp = (C.c_int64 * len(img.sizes))(*[h * w for h, w in img.sizes])
+    out = out if out is not None else torch.empty_like(img.rgb)
+    check("p2e_relight", lib.p2e_relight(_ptr(img.rgb), _ptr(img.normal), _ptr(img.alpha), vp, len(img.sizes), la,
+                                         len(lt) // 4, C.c_float(ambient), bga, _ptr(out), _stream(stream)))
+    return out
+
+
 # ---------------------------------------------------------------- backward
 def p2e_render_backward(g: GaussianSet, proj: Projected, bins: Bins, cams: list, cfg: dict | None,
                         alpha: torch.Tensor, last: torch.Tensor, d_rgb=None, d_normal=None,
