@@ -338,6 +338,9 @@ def main():
     relight_ms = timed_op(lambda: relight(img, lights, ambient=0.15, out=shaded))
     relight_gbs = RES * RES * 40 / (relight_ms / 1e3) / 1e9
     glob_ms = timed_op(lambda: est.global_(cx, cc, 1.5, out=gs))
+    from paper_2409_16504_gb300 import point_raster
+    raster_img = Images([cams[0]], dev)
+    raster_ms = timed_op(lambda: point_raster(cx, cc, [cams[0]], out=raster_img))
 
     # roofline of the dominant stage (one C-ABI call, timed by CUDA events on
     # its stream): algorithmic DRAM bytes per call / its mean duration
@@ -392,7 +395,7 @@ def main():
             "roofline": roof,
             "beyond_frame": {"relight_1024": {"ms": relight_ms, "achieved_gbs": relight_gbs,
                                               "frac_hbm": relight_gbs / peaks["hbm_gbs"]},
-                             "global_estimate_800k_ms": glob_ms}}
+                             "global_estimate_800k_ms": glob_ms, "point_raster_800k_1024_ms": raster_ms}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(head_path)
     if rank == 0:

@@ -348,6 +348,22 @@ p2e_status p2e_relight(const float *rgb, const float *normal, const float *alpha
                        int32_t n_views, const float *lights, int32_t n_lights, float ambient, const float *bg,
                        float *out, void *stream);
 
+/* p2e_point_raster -- the point-rasterisation baseline of Sec. 4.1 (each
+ * point drawn as a 1-pixel square with a depth test, "OpenGL"): a point
+ * covers the pixel (floor(u), floor(v)) containing its projection
+ * u = fx x/z + cx, v = fy y/z + cy (camera transform and projection in
+ * fp32, each operation correctly rounded, in the order written: x = ((T00 px
+ * + T01 py) + T02 pz) + t0, ...), when z > near_z and the pixel is in the
+ * image; the nearest point wins, ties by the lower index; the pixel gets
+ * its colour, uncovered pixels get bg (host, 3 floats, or NULL for black).
+ * xyz, rgb: device float4[n].  zbuf: device uint64 scratch of the total
+ * pixel count (overwritten).  out_rgb: device planar rgb, views
+ * concatenated as p2e_render; out_depth (may be NULL): the winning z, 0
+ * where uncovered. */
+p2e_status p2e_point_raster(const float *xyz, const float *rgb, int64_t n, const p2e_camera *cams,
+                            int32_t n_views, const float *bg, uint64_t *zbuf, float *out_rgb, float *out_depth,
+                            void *stream);
+
 const char *p2e_status_string(p2e_status s);
 
 #ifdef __cplusplus

@@ -300,6 +300,49 @@ def relight(rgb, normal, alpha, lights, ambient: float, bg=(0.0, 0.0, 0.0)) -> n
     return C * s[None] + (1.0 - a)[None] * bgv
 
 
+def point_raster(xyz, rgb, cam: dict, bg=(0.0, 0.0, 0.0)) -> dict:
+    """The point-rasterisation baseline of Sec. 4.1 ("OpenGL": each point a
+    1-pixel square with a depth test).  A point covers the pixel
+    (floor(u), floor(v)) containing its projection, computed in fp32 with
+    every operation rounded in the order written:
+    x = ((T00 px + T01 py) + T02 pz) + t0 (likewise y, z), u = fx (x / z) + cx,
+    v = fy (y / z) + cy; it is drawn when z > near and the pixel lies in the
+    image.  The nearest point wins (ties by the lower index).  Returns
+    ``rgb (3,H,W)`` (bg where nothing is drawn), ``depth (H,W)`` (0 there)
+    and ``winner (H,W)`` (point index, -1)."""
+    f32 = np.float32
+    p = np.asarray(xyz, f32)
+    V = np.asarray(cam["viewmat"], f32).reshape(3, 4)
+    W, H = int(cam["width"]), int(cam["height"])
+
+    def row(r):
+        return ((V[r, 0] * p[:, 0] + V[r, 1] * p[:, 1]) + V[r, 2] * p[:, 2]) + V[r, 3]
+
+    x, y, z = row(0), row(1), row(2)
+    near = f32(cam.get("near", 0.01))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        u = f32(cam["fx"]) * (x / z) + f32(cam["cx"])
+        v = f32(cam["fy"]) * (y / z) + f32(cam["cy"])
+        ok = (z > near) & (z > 0) & (u >= 0) & (v >= 0) & (u < f32(W)) & (v < f32(H))
+    idx = np.nonzero(ok)[0]
+    pi = np.minimum(np.floor(u[idx]).astype(np.int64), W - 1)
+    pj = np.minimum(np.floor(v[idx]).astype(np.int64), H - 1)
+    pix = pj * W + pi
+    order = np.lexsort((idx, z[idx], pix))          # by pixel, then depth, then index
+    first = np.ones(len(order), bool)
+    first[1:] = pix[order][1:] != pix[order][:-1]
+    win = order[first]
+    winner = np.full(H * W, -1, np.int64)
+    winner[pix[win]] = idx[win]
+    depth = np.zeros(H * W, f32)
+    depth[pix[win]] = z[idx[win]]
+    out = np.empty((3, H * W), f32)
+    out[:] = np.asarray(bg, f32)[:, None]
+    col = np.asarray(rgb, f32)
+    out[:, pix[win]] = col[idx[win], :3].T
+    return dict(rgb=out.reshape(3, H, W), depth=depth.reshape(H, W), winner=winner.reshape(H, W))
+
+
 def sigma_of(scale, quat) -> np.ndarray:
     """Sigma = R diag(s^2) R^T for each row (quaternions normalised)."""
     q = np.asarray(quat, np.float64)

@@ -7,5 +7,5 @@ The compute path lives in ``libp2e.so`` (``csrc/``, C ABI in
 """
 from ._lib import P2EError, load  # noqa: F401
 from .render import (DEFAULT_CONFIG, Bins, GaussianSet, Images, Projected, Renderer,  # noqa: F401
-                     p2e_bins_check, p2e_project, p2e_render, p2e_render_backward, p2e_sort_bin, relight,
+                     p2e_bins_check, p2e_project, p2e_render, p2e_render_backward, p2e_sort_bin, point_raster, relight,
                      render_differentiable, total_tiles)

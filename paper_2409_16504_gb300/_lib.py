@@ -23,7 +23,7 @@ P2E_SCRATCH_SORT, P2E_SCRATCH_ESTIMATE, P2E_SCRATCH_BACKWARD = 0, 1, 2
 EXPORTS = ("p2e_default_config", "p2e_total_tiles", "p2e_scratch_bytes", "p2e_project",
            "p2e_sort_bin", "p2e_sort_bin_noalloc", "p2e_bins_check", "p2e_render",
            "p2e_render_backward", "p2e_estimate", "p2e_loss_eq5", "p2e_mlp_backward", "p2e_adam",
-           "p2e_estimate_global", "p2e_relight", "p2e_status_string")
+           "p2e_estimate_global", "p2e_relight", "p2e_point_raster", "p2e_status_string")
 P2E_MAX_LIGHTS = 8
 MLP_PARAMS = 15568
 NOALLOC_MAX_N = 1 << 22
@@ -121,6 +121,9 @@ def load(path: str | None = None):
         lib.p2e_relight.restype = C.c_int
         lib.p2e_relight.argtypes = [vp, vp, vp, C.POINTER(C.c_int64), i32, C.POINTER(C.c_float), i32, C.c_float,
                                     C.POINTER(C.c_float), vp, vp]
+        lib.p2e_point_raster.restype = C.c_int
+        lib.p2e_point_raster.argtypes = [vp, vp, i64, C.POINTER(P2ECamera), i32, C.POINTER(C.c_float), vp, vp, vp,
+                                         vp]
         _lib = lib
         return lib
 

@@ -282,6 +282,22 @@ def relight(img: Images, lights, ambient: float = 0.2, bg=(0.0, 0.0, 0.0), out: 
     return out
 
 
+def point_raster(xyz: torch.Tensor, rgb: torch.Tensor, cams: list, bg=(0.0, 0.0, 0.0), out: Images | None = None,
+                 stream=None) -> Images:
+    """The 1-pixel point-rasterisation baseline (p2e_point_raster) of a
+    float4 cloud: rgb and depth planes of every view (alpha, normal and
+    last of ``out`` are left untouched)."""
+    lib = _lib.load()
+    n = xyz.shape[0]
+    out = out or Images(cams, xyz.device)
+    zbuf = torch.empty((out.npix,), dtype=torch.int64, device=xyz.device)
+    ca = make_cameras(cams)
+    bga = (C.c_float * 3)(*[float(b) for b in bg])
+    check("p2e_point_raster", lib.p2e_point_raster(_ptr(xyz), _ptr(rgb), n, ca, len(cams), bga, _ptr(zbuf),
+                                                   _ptr(out.rgb), _ptr(out.depth), _stream(stream)))
+    return out
+
+
 # ---------------------------------------------------------------- backward
 def p2e_render_backward(g: GaussianSet, proj: Projected, bins: Bins, cams: list, cfg: dict | None,
                         alpha: torch.Tensor, last: torch.Tensor, d_rgb=None, d_normal=None,

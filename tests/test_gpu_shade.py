@@ -7,9 +7,13 @@ GPU, against the oracle.
 * p2e_estimate_global vs the oracle: the mean nearest-neighbour distance
   within 1e-6 relative (an fp64 sum of fp32 distances), isotropic scales,
   identity rotations, and the kNN-PCA normals bit for bit.
-* The baseline's quality on held-out scenes next to kNN-PCA and the
+* p2e_point_raster (the 1-pixel "OpenGL" baseline) vs the oracle: the same
+  winning point per pixel (fp32 projection in the same operation order on
+  both sides), so rgb and depth are bit-identical.
+* The baselines' quality on held-out scenes next to kNN-PCA and the
   trained estimator (the comparison of Sec. 4.2 and the texture
-  experiment): the learned estimate beats every global size.
+  experiment): the learned estimate beats every global size and the point
+  raster.
 """
 import math
 
@@ -89,6 +93,23 @@ def test_global_estimate_matches_oracle():
     assert torch.equal(g.normal, p.normal)
 
 
+def test_point_raster_matches_oracle():
+    from paper_2409_16504_gb300 import point_raster
+    from paper_2409_16504_gb300.estimate import cloud_tensors
+    xyz, rgb, _, _ = scenes.humanoid_cloud(200_000, seed=9)
+    a, b = cloud_tensors(xyz, rgb)
+    rng = np.random.default_rng(5)
+    cams = [scenes.sphere_camera(xyz.mean(0), 2.5, rng, 512, 512), scenes.sphere_camera(xyz.mean(0), 1.2, rng, 384, 256)]
+    img = point_raster(a, b, cams, bg=(0.2, 0.1, 0.0))
+    torch.cuda.synchronize()
+    for v, cam in enumerate(cams):
+        ref = oracle.point_raster(xyz, rgb, cam, bg=(0.2, 0.1, 0.0))
+        vw = img.view(v)
+        assert (ref["winner"] >= 0).sum() > 2000
+        np.testing.assert_array_equal(vw["rgb"].cpu().numpy(), ref["rgb"])
+        np.testing.assert_array_equal(vw["depth"].cpu().numpy(), ref["depth"])
+
+
 def test_global_baseline_quality_vs_pca_and_learned():
     from paper_2409_16504_gb300 import Renderer, mlp
     from paper_2409_16504_gb300.estimate import Estimator
@@ -110,7 +131,16 @@ def test_global_baseline_quality_vs_pca_and_learned():
             g = est.global_(sc.xyz, sc.rgb, rel)
             vals.append(psnr(Renderer(capacity=1 << 21).render(g, sc.cams), sc))
         res[f"global {rel}"] = float(np.mean(vals))
+    from paper_2409_16504_gb300 import point_raster
+    res["point raster"] = float(np.mean([psnr(point_raster(sc.xyz, sc.rgb, sc.cams), sc) for sc in scs]))
     res["kNN-PCA"] = float(np.mean([tr.evaluate(sc, learned=False)["psnr"] for sc in scs]))
     res["learned"] = float(np.mean([tr.evaluate(sc, learned=True)["psnr"] for sc in scs]))
-    print("held-out PSNR (dB):", {k: round(v, 2) for k, v in res.items()})
+    print("held-out PSNR (dB), 150K points at 256^2:", {k: round(v, 2) for k, v in res.items()})
     assert res["learned"] > max(res[k] for k in res if k.startswith("global"))
+    # sparser clouds: 1-pixel points leave holes that splats close
+    sparse = [Scene(2300 + s, 20_000, 4, 512) for s in range(2)]
+    tr2 = Trainer(20_000, params=params)
+    r_raster = float(np.mean([psnr(point_raster(sc.xyz, sc.rgb, sc.cams), sc) for sc in sparse]))
+    r_learned = float(np.mean([tr2.evaluate(sc, learned=True)["psnr"] for sc in sparse]))
+    print(f"held-out PSNR (dB), 20K points at 512^2: point raster {r_raster:.2f}, learned {r_learned:.2f}")
+    assert r_learned > r_raster

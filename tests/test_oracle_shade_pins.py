@@ -86,3 +86,52 @@ def test_global_estimate_is_isotropic_at_the_mean_spacing():
     # within the tilt of a 16-point patch of the curved surface)
     np.testing.assert_array_equal(e["normal"], oracle.pca(x, oracle.knn(x)[0])["normal"].astype(np.float32))
     assert np.abs(np.abs((e["normal"] * x).sum(1)) - 1).max() < 1e-2
+
+
+# ------------------------------------------------------------ point raster
+def _cam(W=5, H=4, f=10.0):
+    return dict(viewmat=[1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], fx=f, fy=f, cx=W / 2, cy=H / 2, width=W, height=H,
+                near=0.01)
+
+
+def test_point_raster_hand_example():
+    cam = _cam()
+    xyz = np.array([[0.0, 0.0, 1.0],     # u = 2.5, v = 2.0 -> pixel (2, 2)
+                    [0.0, 0.0, 0.5],     # same pixel, nearer: wins
+                    [0.0, 0.0, 0.5],     # same depth, higher index: loses
+                    [0.0, 0.0, -1.0],    # behind the camera
+                    [1.0, 0.0, 1.0],     # u = 12.5: outside
+                    [-0.2, -0.15, 1.0]], np.float32)  # u = 0.5, v = 0.5 -> pixel (0, 0)
+    rgb = np.arange(18, dtype=np.float32).reshape(6, 3) / 20
+    r = oracle.point_raster(xyz, rgb, cam, bg=(0.5, 0.5, 0.5))
+    assert r["winner"][2, 2] == 1 and r["winner"][0, 0] == 5
+    assert (r["winner"] >= 0).sum() == 2
+    np.testing.assert_array_equal(r["rgb"][:, 2, 2], rgb[1])
+    np.testing.assert_array_equal(r["rgb"][:, 1, 1], [0.5, 0.5, 0.5])
+    assert r["depth"][2, 2] == np.float32(0.5) and r["depth"][1, 1] == 0
+
+
+def test_point_raster_matches_brute_force():
+    rng = np.random.default_rng(4)
+    cam = _cam(13, 9, 7.0)
+    xyz = np.concatenate([rng.uniform(-1, 1, (400, 2)), rng.uniform(-0.5, 3, (400, 1))], 1).astype(np.float32)
+    xyz[::7] = xyz[3]                         # duplicates: equal depths, ties by index
+    rgb = rng.random((400, 3)).astype(np.float32)
+    r = oracle.point_raster(xyz, rgb, cam)
+    f32 = np.float32
+    best = {}
+    for i, (px, py, pz) in enumerate(xyz):
+        x, y, z = f32(px), f32(py), f32(pz)       # identity camera: x, y, z exact
+        if not (z > f32(0.01)):
+            continue
+        u = f32(7.0) * f32(x / z) + f32(6.5)
+        v = f32(7.0) * f32(y / z) + f32(4.5)
+        if not (0 <= u < 13 and 0 <= v < 9):
+            continue
+        key = (int(np.floor(v)), int(np.floor(u)))
+        if key not in best or (z, i) < best[key]:
+            best[key] = (z, i)
+    w = np.full((9, 13), -1)
+    for (j, i), (_, k) in best.items():
+        w[j, i] = k
+    np.testing.assert_array_equal(r["winner"], w)
