@@ -257,6 +257,7 @@ p2e_status p2e_estimate(const float *xyz, const float *rgb, int64_t n, int32_t m
         return P2E_ERR_INVALID_ARG;
     if (scratch_bytes < (int64_t)estimate_scratch_bytes(n) || !scratch || ((uintptr_t)scratch & 255u))
         return P2E_ERR_INVALID_ARG;
+    if (knn_idx && !aligned16(knn_idx)) return P2E_ERR_INVALID_ARG;
     cudaError_t e = launch_estimate(xyz, rgb, n, mode, mlp_weights, pca_opacity, out, knn_idx, scratch,
                                     device_sms(), (cudaStream_t)stream);
     if (e == cudaErrorNotSupported) return P2E_ERR_UNSUPPORTED;
@@ -278,6 +279,7 @@ p2e_status p2e_estimate_global(const float *xyz, const float *rgb, int64_t n, fl
         return P2E_ERR_INVALID_ARG;
     if (scratch_bytes < (int64_t)estimate_scratch_bytes(n) || !scratch || ((uintptr_t)scratch & 255u))
         return P2E_ERR_INVALID_ARG;
+    if (knn_idx && !aligned16(knn_idx)) return P2E_ERR_INVALID_ARG;
     cudaError_t e = launch_estimate_global(xyz, rgb, n, sigma_rel, opacity, out, knn_idx, scratch, device_sms(),
                                            (cudaStream_t)stream);
     return e == cudaSuccess ? P2E_OK : P2E_ERR_CUDA;
