@@ -52,10 +52,22 @@ class Scene:
     ground-truth RGB and normal images in the renderer's planar layout."""
 
     def __init__(self, seed: int, n_points: int, n_views: int, res: int, jitter: float = 0.15,
-                 device="cuda"):
+                 device="cuda", degrade=None):
+        """``degrade``: None, ("quant", alpha) for a 10-bit voxelised input
+        coarsened by alpha, or ("sub", beta) for a random beta-subset (the
+        input augmentations of Sec. 3.3); the ground truth stays exact."""
         import scenes
         prims = scenes.humanoid_primitives(seed, jitter=jitter)
         xyz, rgb, _, _ = scenes.humanoid_cloud(n_points, seed=seed, prims=prims)
+        if degrade is not None:
+            kind, amount = degrade
+            if kind == "quant":
+                xyz, rgb = scenes.quantize_cloud(xyz, rgb, alpha=amount)
+            elif kind == "sub":
+                xyz, rgb = scenes.subsample_cloud(xyz, rgb, amount, seed + 11)
+            else:
+                raise ValueError(f"unknown degradation {kind}")
+            n_points = len(xyz)
         rng = np.random.default_rng(seed + 7)
         center = xyz.mean(0)
         self.cams = [scenes.sphere_camera(center, 2.5, rng, res, res) for _ in range(n_views)]
@@ -66,6 +78,27 @@ class Scene:
         self.gt_normal = torch.from_numpy(
             np.concatenate([g["normal"].reshape(-1) for g in gt]).astype(np.float32)).to(device)
         self.view_pixels = (C.c_int64 * n_views)(*[res * res] * n_views)
+
+
+    def degraded(self, degrade, seed: int = 0, device="cuda") -> "Scene":
+        """The same views and ground truth with a degraded input cloud
+        (("quant", alpha) or ("sub", beta), as the constructor)."""
+        import copy
+
+        import scenes
+        xyz = self.xyz[:, :3].cpu().numpy()
+        rgb = self.rgb[:, :3].cpu().numpy()
+        kind, amount = degrade
+        if kind == "quant":
+            xyz, rgb = scenes.quantize_cloud(xyz, rgb, alpha=amount)
+        elif kind == "sub":
+            xyz, rgb = scenes.subsample_cloud(xyz, rgb, amount, seed)
+        else:
+            raise ValueError(f"unknown degradation {kind}")
+        out = copy.copy(self)
+        out.xyz, out.rgb = cloud_tensors(xyz, rgb, device)
+        out.n = len(xyz)
+        return out
 
 
 class Trainer:
@@ -138,12 +171,22 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--eval-scenes", type=int, default=4)
     ap.add_argument("--out", default=mlp.TRAINED)
+    ap.add_argument("--augment", type=float, default=0.0,
+                    help="fraction of training scenes with degraded inputs (10-bit voxels coarsened by "
+                         "alpha in [0.25, 1], or a beta in [0.125, 1] random subset)")
     a = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
         sys.path.insert(0, root)
     t0 = time.time()
-    pool = [Scene(1000 + s, a.points, a.views, a.res) for s in range(a.scenes)]
+    rng = np.random.default_rng(0)
+
+    def degrade_of(s):
+        if rng.random() >= a.augment:
+            return None
+        return ("quant", float(rng.uniform(0.25, 1.0))) if rng.random() < 0.5 else \
+            ("sub", float(rng.uniform(0.125, 1.0)))
+    pool = [Scene(1000 + s, a.points, a.views, a.res, degrade=degrade_of(s)) for s in range(a.scenes)]
     held = [Scene(2000 + s, a.points, 12, a.res) for s in range(a.eval_scenes)]
     print(f"scenes ready in {time.time() - t0:.1f} s", flush=True)
     tr = Trainer(a.points, lr=a.lr)

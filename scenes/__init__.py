@@ -426,6 +426,40 @@ def humanoid_cloud(n: int, seed: int, prims=None, noise: float = 1e-3):
     return pts.astype(np.float32), rgb.astype(np.float32), nrm, prims
 
 
+def quantize_cloud(xyz, rgb, alpha: float = 1.0, bits: int = 10):
+    """Voxelised input as in the paper's training data (Sec. 3.3): the cloud
+    is normalised into the 2 x 2 x 2 box centred at the origin (its largest
+    extent fills the box), coordinates are scaled by 2^(bits - 1) (512 for
+    10 bits) and rounded to integers; ``alpha`` in (0, 1] further coarsens
+    them (round(alpha x) / alpha, the density augmentation of quantised
+    inputs).  Points falling into one voxel merge (mean colour).  Returns
+    float32 ``(xyz, rgb)`` back in the cloud's original frame."""
+    p = np.asarray(xyz, np.float64)
+    lo, hi = p.min(0), p.max(0)
+    c = 0.5 * (lo + hi)
+    s = 2.0 / max(float((hi - lo).max()), 1e-12)
+    u = (p - c) * s * 2.0 ** (bits - 1)              # in [-512, 512] for 10 bits
+    q = np.round(alpha * u).astype(np.int64)           # voxel ids at the (alpha-coarsened) step
+    _, first, inv, cnt = np.unique(q, axis=0, return_index=True, return_inverse=True, return_counts=True)
+    inv = inv.reshape(-1)
+    col = np.zeros((len(first), 3))
+    np.add.at(col, inv, np.asarray(rgb, np.float64))
+    col /= cnt[:, None]
+    grid = q[first].astype(np.float64) / alpha         # back to the 10-bit scale
+    out = grid / 2.0 ** (bits - 1) / s + c
+    return out.astype(np.float32), col.astype(np.float32)
+
+
+def subsample_cloud(xyz, rgb, beta: float, seed: int):
+    """Random subset of round(beta N) points (the density augmentation of
+    non-quantised inputs, Sec. 3.3)."""
+    rng = np.random.default_rng(seed)
+    n = len(xyz)
+    k = max(17, int(round(beta * n)))
+    idx = np.sort(rng.choice(n, size=min(k, n), replace=False))
+    return np.asarray(xyz, np.float32)[idx], np.asarray(rgb, np.float32)[idx]
+
+
 def mean_spacing(n: int, prims, rng=None) -> float:
     """Average point spacing sqrt(area / n) of an n-point sample on ``prims``."""
     rng = rng or np.random.default_rng(0)
