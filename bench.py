@@ -103,6 +103,23 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest value over all ranks (the slowest rank's time)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, pixels_per_step: int, max_ms: float) -> float:
+    """Whole-job Mpix/s: the pixels every rank rendered over the slowest
+    rank's time (each rank renders its own frames: replicas)."""
+    return world * steps * pixels_per_step / (max_ms / 1e3) / 1e6
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -273,12 +290,8 @@ def main():
 
     def summary(stage):
         fm = stage.sum(1)
-        tot = float(fm.sum())
-        if world > 1:
-            t = torch.tensor([tot], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
-        return dict(value=world * args.steps * RES * RES / (tot / 1e3) / 1e6, ms=tot / args.steps,
+        tot = max_over_ranks(float(fm.sum()), world, dev)
+        return dict(value=job_throughput(world, args.steps, RES * RES, tot), ms=tot / args.steps,
                     p50=float(np.percentile(fm, 50)), p99=float(np.percentile(fm, 99)),
                     stage={nm: float(x) for nm, x in zip(["estimate", "project", "sort_bin", "blend"],
                                                          stage.mean(0))})
