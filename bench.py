@@ -299,32 +299,58 @@ def main():
     head_path = paths[0]
     hs = sums[head_path]
 
-    # end to end through the public API: the cloud comes from pinned host
-    # memory every frame, the rgb/normal/depth images go back to the host
+    # end to end through the public API: every frame's cloud is uploaded
+    # from pinned host memory and its rgb/normal/depth images are read back
+    # to pinned host memory.  Uploads, compute (estimation + rendering) and
+    # read-backs run on three streams, double-buffered, so that frame i+1's
+    # upload and frame i-1's read-back overlap frame i's compute.
     hx, hc = cx.cpu().pin_memory(), cc.cpu().pin_memory()
-    out_host = torch.empty((7 * RES * RES,), dtype=torch.float32).pin_memory()
-    dx, dc = torch.empty_like(cx), torch.empty_like(cc)
+    outs = [torch.empty((7 * RES * RES,), dtype=torch.float32).pin_memory() for _ in range(2)]
+    dxs, dcs = [torch.empty_like(cx) for _ in range(2)], [torch.empty_like(cc) for _ in range(2)]
+    imgs = [Images([cams[0]], dev) for _ in range(2)]
     h2d = (hx.numel() + hc.numel()) * 4
-    d2h = out_host.numel() * 4
+    d2h = outs[0].numel() * 4
     mode = LEARNED if head_path == "learned" else PCA
+    cps, kst, dns = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    up_done = [torch.cuda.Event() for _ in range(2)]
+    comp_done = [torch.cuda.Event() for _ in range(2)]
+    down_done = [torch.cuda.Event() for _ in range(2)]
+    torch.cuda.synchronize()
+    for k in range(2):  # start from recorded events
+        comp_done[k].record(kst)
+        down_done[k].record(dns)
 
-    def e2e_frame(cam):
-        dx.copy_(hx, non_blocking=True)
-        dc.copy_(hc, non_blocking=True)
-        src = est(dx, dc, mode=mode, mlp_blob=mlp_blob, out=gs) if head_path != "render" else g_static
-        rend.render(src, [cam], out=img, check=False)
-        out_host[: 3 * RES * RES].copy_(img.rgb, non_blocking=True)
-        out_host[3 * RES * RES: 6 * RES * RES].copy_(img.normal, non_blocking=True)
-        out_host[6 * RES * RES:].copy_(img.depth, non_blocking=True)
+    def e2e_frame(i, cam):
+        k = i & 1
+        with torch.cuda.stream(cps):
+            cps.wait_event(comp_done[k])            # frame i-2 done reading dxs[k]
+            dxs[k].copy_(hx, non_blocking=True)
+            dcs[k].copy_(hc, non_blocking=True)
+            up_done[k].record(cps)
+        with torch.cuda.stream(kst):
+            kst.wait_event(up_done[k])
+            kst.wait_event(down_done[k])            # frame i-2's images read back
+            src = (est(dxs[k], dcs[k], mode=mode, mlp_blob=mlp_blob, out=gs, stream=kst)
+                   if head_path != "render" else g_static)
+            rend.render(src, [cam], out=imgs[k], check=False, stream=kst)
+            comp_done[k].record(kst)
+        with torch.cuda.stream(dns):
+            dns.wait_event(comp_done[k])
+            o = outs[k]
+            o[: 3 * RES * RES].copy_(imgs[k].rgb, non_blocking=True)
+            o[3 * RES * RES: 6 * RES * RES].copy_(imgs[k].normal, non_blocking=True)
+            o[6 * RES * RES:].copy_(imgs[k].depth, non_blocking=True)
+            down_done[k].record(dns)
 
-    for w in range(2):
-        e2e_frame(cams[w])
+    for w in range(4):
+        e2e_frame(w, cams[w])
     torch.cuda.synchronize()
     a, b = ev(), ev()
-    a.record(st)
+    a.record(cps)
     for i in range(e_steps):
-        e2e_frame(cams[args.warmup + i])
-    b.record(st)
+        e2e_frame(i, cams[args.warmup + i])
+    cps.wait_stream(dns)
+    b.record(cps)
     torch.cuda.synchronize()
     e2e_ms = a.elapsed_time(b) / e_steps
 
