@@ -12,9 +12,9 @@
 //             cell-ordered copy of the points): exact 16 nearest other
 //             points (ties by index) by a two-pass threshold search of the
 //             3x3x3 cell block (count within trial radii, then buffer and
-//             select), or, where the block cannot certify the answer, by
-//             rings of cells searched until the 16th distance is below the
-//             distance to the next ring; then the neighbours' covariance, a cyclic Jacobi
+//             select); the few queries that block cannot certify go to a
+//             second kernel, one warp per query over the 5x5x5 block (ring
+//             search beyond it); then the neighbours' covariance, a cyclic Jacobi
 //             eigen-decomposition, scale = sqrt(lambda) (smallest axis at
 //             least 0.1 of the middle one), rotation in a canonical frame
 //             (normal = smallest axis turned away from the centroid, first
@@ -43,7 +43,6 @@ struct EstScratch {
     uint32_t *cell;       // n
     uint32_t *order;      // n
     uint32_t *counts;     // ncell_max
-    uint32_t *fill;       // ncell_max
     uint32_t *start;      // ncell_max + 1
     uint64_t *scan_state; // scan tiles + 1
     uint32_t *ticket;
@@ -55,7 +54,7 @@ struct EstScratch {
 
 __host__ __device__ inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 static int64_t ncell_cap(int64_t n) { return std::max<int64_t>(2 * n, 1 << 16); }
-constexpr int kScanT = 1024;
+constexpr int kScanT = 4096;
 size_t mlp_scratch_bytes(int64_t n);
 
 static size_t est_layout(int64_t n, void *base, EstScratch *S) {
@@ -75,7 +74,6 @@ static size_t est_layout(int64_t n, void *base, EstScratch *S) {
     s.cell = (uint32_t *)take((size_t)n * 4);
     s.order = (uint32_t *)take((size_t)n * 4);
     s.counts = (uint32_t *)take((size_t)nc * 4);
-    s.fill = (uint32_t *)take((size_t)nc * 4);
     s.start = (uint32_t *)take((size_t)(nc + 1) * 4);
     s.scan_state = (uint64_t *)take((size_t)(st + 1) * 8);
     s.ticket = (uint32_t *)take(64);
@@ -204,7 +202,8 @@ __device__ __forceinline__ void st_rel64(uint64_t *p, uint64_t v) {
 }
 
 // Exclusive scan of counts[0, len) into start[0, len] (start[len] = total),
-// single pass with decoupled look-back; 1024 elements per block.
+// single pass with decoupled look-back; kScanT elements per block (16 per
+// thread), the look-back by one warp over 32 predecessors at a time.
 __global__ void __launch_bounds__(256) scan_counts_kernel(const uint32_t *__restrict__ counts, int64_t len,
                                                           uint32_t *__restrict__ start, EstScratch S,
                                                           int32_t *status) {
@@ -214,13 +213,21 @@ __global__ void __launch_bounds__(256) scan_counts_kernel(const uint32_t *__rest
     if (threadIdx.x == 0) s_tile = atomicAdd(S.ticket, 1u);
     __syncthreads();
     const int64_t tile = s_tile;
-    const int64_t base = tile * kScanT + threadIdx.x * 4;
-    uint32_t v[4], loc = 0;
+    const int64_t base = tile * kScanT + threadIdx.x * 16;
+    uint32_t v[16], loc = 0;
+    if (base + 16 <= len) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(counts + base);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        v[k] = base + k < len ? counts[base + k] : 0u;
-        loc += v[k];
+        for (int k = 0; k < 4; ++k) {
+            const uint4 u = src[k];
+            v[4 * k] = u.x; v[4 * k + 1] = u.y; v[4 * k + 2] = u.z; v[4 * k + 3] = u.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = base + k < len ? counts[base + k] : 0u;
     }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) loc += v[k];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t x = loc;
 #pragma unroll
@@ -235,42 +242,68 @@ __global__ void __launch_bounds__(256) scan_counts_kernel(const uint32_t *__rest
         if (q < w) wpre += s_w[q];
         tot += s_w[q];
     }
-    if (threadIdx.x == 0) {
+    if (w == 0) {
+        constexpr uint64_t kAgg = 1ull << 62, kPre = 2ull << 62, kVal = (1ull << 62) - 1;
         uint64_t prefix = 0;
         if (tile == 0) {
-            st_rel64(&S.scan_state[0], (2ull << 62) | tot);
+            if (lane == 0) st_rel64(&S.scan_state[0], kPre | tot);
         } else {
-            st_rel64(&S.scan_state[tile], (1ull << 62) | tot);
-            int64_t p = tile - 1;
+            if (lane == 0) st_rel64(&S.scan_state[tile], kAgg | tot);
+            int64_t p = tile - 1;  // window [p - 31, p], lane l reads p - l
             uint32_t spins = 0;
-            while (p >= 0) {
-                const uint64_t wd = ld_acq64(&S.scan_state[p]);
-                if ((wd >> 62) == 0) {
-                    if (++spins > kSpinLimit) { atomicExch(status, (int32_t)P2E_ERR_TIMEOUT); break; }
+            while (true) {
+                const int64_t idx = p - lane;
+                const uint64_t wd = idx >= 0 ? ld_acq64(&S.scan_state[idx]) : kPre;
+                const uint32_t flag = (uint32_t)(wd >> 62);
+                const unsigned pre = __ballot_sync(0xffffffffu, flag == 2u);
+                const unsigned notready = __ballot_sync(0xffffffffu, flag == 0u);
+                const int first = pre ? __ffs(pre) - 1 : 32;  // nearest inclusive prefix
+                const unsigned need = first >= 31 ? 0xffffffffu : ((2u << first) - 1u);
+                if (notready & need) {
+                    if (++spins > kSpinLimit) {
+                        if (lane == 0) atomicExch(status, (int32_t)P2E_ERR_TIMEOUT);
+                        break;
+                    }
                     backoff(spins);
                     continue;
                 }
-                prefix += wd & ((1ull << 62) - 1);
-                if ((wd >> 62) == 2) break;
-                --p;
+                uint64_t add = lane <= first ? (wd & kVal) : 0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
+                prefix += add;
+                if (first < 32) break;
+                p -= 32;
             }
-            st_rel64(&S.scan_state[tile], (2ull << 62) | (prefix + tot));
+            if (lane == 0) st_rel64(&S.scan_state[tile], kPre | (prefix + tot));
         }
-        s_prefix = prefix;
+        if (lane == 0) s_prefix = prefix;
     }
     __syncthreads();
     uint32_t run = (uint32_t)s_prefix + wpre + x - loc;
+    if (base + 16 <= len) {
+        uint32_t o[16];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (base + k <= len) start[base + k] = run;
-        run += v[k];
+        for (int k = 0; k < 16; ++k) {
+            o[k] = run;
+            run += v[k];
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(start + base);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dst[k] = make_uint4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
+        if (base + 16 == len) start[len] = run;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if (base + k <= len) start[base + k] = run;
+            run += v[k];
+        }
     }
 }
 
 __global__ void __launch_bounds__(256) scatter_kernel(const float4 *__restrict__ xyz, int64_t n, EstScratch S) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t c = S.cell[i];
-        const uint32_t q = S.start[c] + atomicAdd(&S.fill[c], 1u);
+        const uint32_t q = S.start[c] + atomicSub(&S.counts[c], 1u) - 1u;  // the count runs down to 0
         S.order[q] = (uint32_t)i;
         const float4 p = __ldg(xyz + i);
         S.spts[q] = make_float4(p.x, p.y, p.z, __uint_as_float((uint32_t)i));
@@ -279,14 +312,13 @@ __global__ void __launch_bounds__(256) scatter_kernel(const float4 *__restrict__
 
 constexpr int kKnnThreads = 128;
 
-// Per-thread list of the 16 best (distance, index) pairs, kept sorted in
-// shared memory ([slot][thread], conflict-free); an insertion shifts only the
-// entries that follow it.
+// List of the 16 best (distance, index) pairs, kept sorted in shared
+// memory; an insertion shifts only the entries that follow it.
 struct KnnList {
     float *d;
     uint32_t *j;
-    __device__ __forceinline__ float &D(int k) { return d[k * kKnnThreads]; }
-    __device__ __forceinline__ uint32_t &J(int k) { return j[k * kKnnThreads]; }
+    __device__ __forceinline__ float &D(int k) { return d[k]; }
+    __device__ __forceinline__ uint32_t &J(int k) { return j[k]; }
     __device__ __forceinline__ void insert(float dd, uint32_t jj) {
         int k = kK - 1;
         while (k > 0 && (dd < D(k - 1) || (dd == D(k - 1) && jj < J(k - 1)))) {
@@ -357,9 +389,8 @@ __device__ __forceinline__ float4 shepperd_f(const float R[3][3]) {
     return make_float4(w, x, y, z);
 }
 
-constexpr int kRad = 6;       // trial radii of the full-block attempt, in cell sizes (0.40 .. 1.00)
-constexpr int kRadA = 8;      // radii of the culled first attempt (0.40 .. 0.75, ratio ~1.09)
-constexpr int kBuf = 32;      // candidates kept by the second pass
+constexpr int kRadA = 5;      // trial radii of the fast path, in cell sizes (0.40 .. 0.75)
+constexpr int kBuf = 32;      // candidates the fast path keeps
 
 // Iterates the candidate points of the cells of the 3x3x3 block around the
 // query's cell that may hold a point within distance sqrt(R2) of the query
@@ -407,169 +438,35 @@ __device__ __forceinline__ void for_block(const GridParams &g, const EstScratch 
     }
 }
 
-// One thread per query point (points taken in cell order).  Exact 16
-// nearest other points, ties by index:
-//   pass 1  count the candidates within trial radii (branch free) and pick
-//           the smallest radius that holds 16 of them.  First attempt:
-//           radii up to 0.75 cell sizes over only the cells of the 3x3x3
-//           block that such a ball can reach (about 60 % of the block's
-//           points); if none holds 16, radii up to one cell size over the
-//           whole block.  Every point within the chosen radius lies in the
-//           cells scanned;
-//   pass 2  keep the candidates within the radius (at most kBuf) in shared
-//           memory and select the 16 smallest.
-// A query whose block holds fewer than 16 points within a cell size, or
-// whose buffer would overflow, takes the incremental ring search instead.
-__global__ void __launch_bounds__(kKnnThreads) knn_pca_kernel(const float4 *__restrict__ xyz,
-                                                      const float4 *__restrict__ rgb, int64_t n,
-                                                      float opacity, EstScratch S, uint32_t *__restrict__ knn_out,
-                                                      float4 *__restrict__ mean_op, float4 *__restrict__ scale,
-                                                      float4 *__restrict__ quat, float4 *__restrict__ rgb_out,
-                                                      float4 *__restrict__ normal) {
-    __shared__ float s_d[kBuf * kKnnThreads];
-    __shared__ uint32_t s_j[kBuf * kKnnThreads];
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const GridParams g = *S.gp;
-    const float4 pq = S.spts[t];
-    const uint32_t i = __float_as_uint(pq.w);
-    const float4 p = pq;
-    int c0[3];
-    cell_of(g, p.x, p.y, p.z, c0);
-    float r2[kRad];
-#pragma unroll
-    for (int k = 0; k < kRad; ++k) {
-        const float f = 0.40f + 0.12f * k;   // 0.40 .. 1.00 cell sizes
-        const float rr = fminf(f, 1.f) * g.h * (1.f - 1e-4f) - 1e-6f;
-        r2[k] = rr * rr;
-    }
-    // ---- pass 1, first attempt: culled block, radii 0.40 .. 0.75 cell sizes
-    float rA[kRadA];
-#pragma unroll
-    for (int k = 0; k < kRadA; ++k) {
-        const float rr = (0.40f + 0.05f * k) * g.h * (1.f - 1e-4f) - 1e-6f;
-        rA[k] = rr * rr;
-    }
-    float T = -1.f, Rscan = rA[kRadA - 1];
-    {
-        int cnt[kRadA] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for_block(g, S, c0, p, Rscan, [&](const float4 &pj) {
-            const float ex = pj.x - p.x, ey = pj.y - p.y, ez = pj.z - p.z;
-            const float d = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-#pragma unroll
-            for (int k = 0; k < kRadA; ++k) cnt[k] += d < rA[k] ? 1 : 0;
-        });
-#pragma unroll
-        for (int k = kRadA - 1; k >= 0; --k)
-            if (cnt[k] >= kK + 1 && cnt[k] <= kBuf + 1) T = rA[k];
-    }
-    if (T < 0.f) {
-        // ---- pass 1, second attempt: the whole block, radii up to one cell
-        Rscan = INFINITY;
-        int cnt[kRad] = {0, 0, 0, 0, 0, 0};
-        for_block(g, S, c0, p, Rscan, [&](const float4 &pj) {
-            const float ex = pj.x - p.x, ey = pj.y - p.y, ez = pj.z - p.z;
-            const float d = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-#pragma unroll
-            for (int k = 0; k < kRad; ++k) cnt[k] += d < r2[k] ? 1 : 0;
-        });
-#pragma unroll
-        for (int k = kRad - 1; k >= 0; --k)
-            if (cnt[k] >= kK + 1 && cnt[k] <= kBuf + 1) T = r2[k];
-    }
-    float *bd = s_d + threadIdx.x;
-    uint32_t *bj = s_j + threadIdx.x;
-    KnnList best{bd, bj};
-    if (T > 0.f) {
-        // ---- pass 2: the candidates within T, then the 16 smallest
-        int m = 0;
-        for_block(g, S, c0, p, Rscan, [&](const float4 &pj) {
-            const uint32_t j = __float_as_uint(pj.w);
-            const float ex = pj.x - p.x, ey = pj.y - p.y, ez = pj.z - p.z;
-            const float d = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-            if (d < T && j != i && m < kBuf) {
-                bd[m * kKnnThreads] = d;
-                bj[m * kKnnThreads] = j;
-                ++m;
-            }
-        });
-        // partial selection sort: the 16 smallest (d, j) to the front
-        for (int a = 0; a < kK; ++a) {
-            int best_k = a;
-            float dbst = bd[a * kKnnThreads];
-            uint32_t jbst = bj[a * kKnnThreads];
-#pragma unroll 4
-            for (int b = a + 1; b < m; ++b) {
-                const float db = bd[b * kKnnThreads];
-                const uint32_t jb = bj[b * kKnnThreads];
-                if (db < dbst || (db == dbst && jb < jbst)) { best_k = b; dbst = db; jbst = jb; }
-            }
-            bd[best_k * kKnnThreads] = bd[a * kKnnThreads];
-            bj[best_k * kKnnThreads] = bj[a * kKnnThreads];
-            bd[a * kKnnThreads] = dbst;
-            bj[a * kKnnThreads] = jbst;
-        }
-    } else {
-        // ---- fallback: incremental search over growing rings
-        for (int k = 0; k < kK; ++k) { best.D(k) = INFINITY; best.J(k) = 0xffffffffu; }
-        float thr = INFINITY;
-        uint32_t thr_j = 0xffffffffu;
-        const int rmax = max(g.dim[0], max(g.dim[1], g.dim[2]));
-        for (int r = 0; r <= rmax; ++r) {
-            for (int dz = -r; dz <= r; ++dz) {
-                const int cz = c0[2] + dz;
-                if (cz < 0 || cz >= g.dim[2]) continue;
-                for (int dy = -r; dy <= r; ++dy) {
-                    const int cy = c0[1] + dy;
-                    if (cy < 0 || cy >= g.dim[1]) continue;
-                    const bool shell = (dz == -r || dz == r || dy == -r || dy == r);
-                    for (int dx = -r; dx <= r; dx += (shell ? 1 : 2 * r)) {
-                        const int cx = c0[0] + dx;
-                        if (cx >= 0 && cx < g.dim[0]) {
-                            const uint32_t c = (uint32_t)(((int64_t)cz * g.dim[1] + cy) * g.dim[0] + cx);
-                            for (uint32_t q = S.start[c]; q < S.start[c + 1]; ++q) {
-                                const float4 pj = S.spts[q];
-                                const uint32_t j = __float_as_uint(pj.w);
-                                if (j == i) continue;
-                                const float ex = pj.x - p.x, ey = pj.y - p.y, ez = pj.z - p.z;
-                                const float d = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                                if (d < thr || (d == thr && j < thr_j)) {
-                                    best.insert(d, j);
-                                    thr = best.D(kK - 1);
-                                    thr_j = best.J(kK - 1);
-                                }
-                            }
-                        }
-                        if (r == 0) break;
-                    }
-                }
-            }
-            const float bound = fmaxf(0.f, (float)r * g.h * (1.f - 1e-4f) - 1e-6f);
-            if (thr_j != 0xffffffffu && thr < bound * bound) break;
-        }
-    }
-    {
-        if (knn_out)
-            for (int k = 0; k < kK; ++k) knn_out[(int64_t)i * kK + k] = best.J(k);
-    // covariance of the neighbours about their centroid
+// The neighbours' covariance about their centroid, its cyclic Jacobi
+// eigen-decomposition and the canonical frame, written out for query point
+// i at p.  nb(k) returns neighbour k (k-th nearest; .w = bits of its
+// index).
+template <typename NB>
+__device__ __forceinline__ void pca_out(const GridParams &g, const float4 &p, uint32_t i, float opacity, NB &&nb,
+                                        const float4 *__restrict__ rgb, uint32_t *__restrict__ knn_out,
+                                        float4 *__restrict__ mean_op, float4 *__restrict__ scale,
+                                        float4 *__restrict__ quat, float4 *__restrict__ rgb_out,
+                                        float4 *__restrict__ normal) {
     float m[3] = {0, 0, 0};
     for (int k = 0; k < kK; ++k) {
-        const float4 qk = __ldg(xyz + best.J(k));
+        const float4 qk = nb(k);
+        if (knn_out) knn_out[(int64_t)i * kK + k] = __float_as_uint(qk.w);
         m[0] += qk.x; m[1] += qk.y; m[2] += qk.z;
     }
     for (int k = 0; k < 3; ++k) m[k] *= (1.f / kK);
     float C[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-        for (int k = 0; k < kK; ++k) {
-        const float4 qk = __ldg(xyz + best.J(k));  // second pass, from L1
+    for (int k = 0; k < kK; ++k) {
+        const float4 qk = nb(k);  // second pass, from L1
         const float d[3] = {qk.x - m[0], qk.y - m[1], qk.z - m[2]};
-        #pragma unroll
+#pragma unroll
         for (int a = 0; a < 3; ++a)
-            #pragma unroll
+#pragma unroll
             for (int b = a; b < 3; ++b) C[a][b] = fmaf(d[a], d[b], C[a][b]);
     }
-    #pragma unroll
+#pragma unroll
     for (int a = 0; a < 3; ++a)
-        #pragma unroll
+#pragma unroll
         for (int b = a; b < 3; ++b) {
             C[a][b] *= (1.f / kK);
             C[b][a] = C[a][b];
@@ -598,20 +495,20 @@ __global__ void __launch_bounds__(kKnnThreads) knn_pca_kernel(const float4 *__re
     // component positive, e2 = e3 x e1
     const float sg = (p.x - g.cen[0]) * R[0][2] + (p.y - g.cen[1]) * R[1][2] + (p.z - g.cen[2]) * R[2][2];
     if (sg < 0.f)
-        #pragma unroll
+#pragma unroll
         for (int k = 0; k < 3; ++k) R[k][2] = -R[k][2];
     {
         const float a0 = fabsf(R[0][0]), a1 = fabsf(R[1][0]), a2 = fabsf(R[2][0]);
         const float big = (a1 > a0) ? ((a2 > a1) ? R[2][0] : R[1][0]) : ((a2 > a0) ? R[2][0] : R[0][0]);
         if (big < 0.f)
-            #pragma unroll
+#pragma unroll
             for (int k = 0; k < 3; ++k) R[k][0] = -R[k][0];
     }
     R[0][1] = R[1][2] * R[2][0] - R[2][2] * R[1][0];
     R[1][1] = R[2][2] * R[0][0] - R[0][2] * R[2][0];
     R[2][1] = R[0][2] * R[1][0] - R[1][2] * R[0][0];
     float s[3];
-    #pragma unroll
+#pragma unroll
     for (int a = 0; a < 3; ++a) s[a] = sqrtf(fmaxf(lamv[a], 0.f));
     s[2] = fmaxf(s[2], 0.1f * s[1]);
     mean_op[i] = make_float4(p.x, p.y, p.z, opacity);
@@ -619,6 +516,268 @@ __global__ void __launch_bounds__(kKnnThreads) knn_pca_kernel(const float4 *__re
     quat[i] = shepperd_f(R);
     rgb_out[i] = __ldg(rgb + i);
     normal[i] = make_float4(R[0][2], R[1][2], R[2][2], 0.f);
+}
+
+// Squared distance, one expression for every pass (counts and collections
+// must agree bit for bit).
+__device__ __forceinline__ float dist2(const float4 &a, const float4 &p) {
+    const float ex = a.x - p.x, ey = a.y - p.y, ez = a.z - p.z;
+    return fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+}
+
+// Fast path, one thread per query point (points taken in cell order).
+// Exact 16 nearest other points, ties by index:
+//   pass 1  count the candidates within five trial radii (0.40 .. 0.75 cell
+//           sizes, branch free) over only the cells of the 3x3x3 block that
+//           the largest ball can reach, and pick the smallest radius T that
+//           holds 16 others (and at most kBuf);
+//   pass 2  keep the candidates within T (the cells that ball reaches) in
+//           shared memory and select the 16 smallest.
+// A query for which no trial radius qualifies (about 0.5 % of the points of
+// a surface scan: sparse or ragged regions) is appended to a list (S.cell
+// reused, its length in S.ticket[12]) for knn_pca_slow_kernel, so that no
+// warp carries one lane's long search.
+__global__ void __launch_bounds__(kKnnThreads, 6) knn_pca_kernel(const float4 *__restrict__ xyz,
+                                                              const float4 *__restrict__ rgb, int64_t n,
+                                                              float opacity, EstScratch S,
+                                                              uint32_t *__restrict__ knn_out,
+                                                              float4 *__restrict__ mean_op,
+                                                              float4 *__restrict__ scale,
+                                                              float4 *__restrict__ quat,
+                                                              float4 *__restrict__ rgb_out,
+                                                              float4 *__restrict__ normal) {
+    __shared__ float s_d[kBuf * kKnnThreads];
+    __shared__ uint32_t s_j[kBuf * kKnnThreads];
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const GridParams g = *S.gp;
+    const float4 p = S.spts[t];
+    const uint32_t i = __float_as_uint(p.w);
+    int c0[3];
+    cell_of(g, p.x, p.y, p.z, c0);
+    float rA[kRadA];
+#pragma unroll
+    for (int k = 0; k < kRadA; ++k) {
+        const float rr = (0.40f + 0.0875f * k) * g.h * (1.f - 1e-4f) - 1e-6f;
+        rA[k] = rr * rr;
+    }
+    float T = -1.f;
+    {
+        int cnt[kRadA] = {0, 0, 0, 0, 0};
+        for_block(g, S, c0, p, rA[kRadA - 1], [&](const float4 &pj) {
+            const float d = dist2(pj, p);
+#pragma unroll
+            for (int k = 0; k < kRadA; ++k) cnt[k] += d < rA[k] ? 1 : 0;
+        });
+#pragma unroll
+        for (int k = kRadA - 1; k >= 0; --k)
+            if (cnt[k] >= kK + 1 && cnt[k] <= kBuf + 1) T = rA[k];
+    }
+    if (T < 0.f) {
+        S.cell[atomicAdd(S.ticket + 12, 1u)] = (uint32_t)t;
+        return;
+    }
+    float *bd = s_d + threadIdx.x;
+    uint32_t *bj = s_j + threadIdx.x;
+    int m = 0;
+    for_block(g, S, c0, p, T, [&](const float4 &pj) {
+        const uint32_t j = __float_as_uint(pj.w);
+        const float d = dist2(pj, p);
+        if (d < T && j != i && m < kBuf) {
+            bd[m * kKnnThreads] = d;
+            bj[m * kKnnThreads] = j;
+            ++m;
+        }
+    });
+    // partial selection sort: the 16 smallest (d, j) to the front
+    for (int a = 0; a < kK; ++a) {
+        int best_k = a;
+        float dbst = bd[a * kKnnThreads];
+        uint32_t jbst = bj[a * kKnnThreads];
+#pragma unroll 4
+        for (int b = a + 1; b < m; ++b) {
+            const float db = bd[b * kKnnThreads];
+            const uint32_t jb = bj[b * kKnnThreads];
+            if (db < dbst || (db == dbst && jb < jbst)) { best_k = b; dbst = db; jbst = jb; }
+        }
+        bd[best_k * kKnnThreads] = bd[a * kKnnThreads];
+        bj[best_k * kKnnThreads] = bj[a * kKnnThreads];
+        bd[a * kKnnThreads] = dbst;
+        bj[a * kKnnThreads] = jbst;
+    }
+    pca_out(g, p, i, opacity, [&](int k) {
+        const uint32_t j = bj[k * kKnnThreads];
+        const float4 q = __ldg(xyz + j);
+        return make_float4(q.x, q.y, q.z, __uint_as_float(j));
+    }, rgb, knn_out, mean_op, scale, quat, rgb_out, normal);
+}
+
+constexpr int kSlowWarps = 4;   // one query per warp at a time
+constexpr int kSlowBuf = 64;    // candidates one warp keeps
+constexpr int kLad = 16;        // trial radii 0.40 .. 2.00 cell sizes (ratio ~1.113)
+
+// Slow path, one warp per listed query.  The 5x5x5 block of cells around
+// the query's cell reaches at least two cell sizes from it; lane r < 25
+// holds the extent of row r of the block (the row's five cells are
+// contiguous in the cell-ordered copy) and the lanes stride over each row:
+//   pass 1  counts within 16 trial radii, summed over the warp; T = the
+//           smallest radius holding 16 others (and at most kSlowBuf);
+//   pass 2  the candidates within T gathered in shared memory by ballot;
+//           each candidate's rank among them by (distance, index) puts the
+//           16 smallest in order.
+// Where no radius qualifies (fewer than 16 others within two cell sizes,
+// or many points at one distance), lane 0 searches rings of cells around
+// the query's cell until the 16th distance is below the distance to the
+// next ring.  Lane 0 computes the PCA and writes the outputs.
+__global__ void __launch_bounds__(kSlowWarps * 32) knn_pca_slow_kernel(const float4 *__restrict__ xyz,
+                                                                       const float4 *__restrict__ rgb,
+                                                                       float opacity, EstScratch S,
+                                                                       uint32_t *__restrict__ knn_out,
+                                                                       float4 *__restrict__ mean_op,
+                                                                       float4 *__restrict__ scale,
+                                                                       float4 *__restrict__ quat,
+                                                                       float4 *__restrict__ rgb_out,
+                                                                       float4 *__restrict__ normal) {
+    __shared__ float s_d[kSlowWarps][kSlowBuf];
+    __shared__ uint32_t s_j[kSlowWarps][kSlowBuf];
+    __shared__ uint32_t s_nb[kSlowWarps][kK];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const GridParams g = *S.gp;
+    const uint32_t nq = S.ticket[12];
+    float lad[kLad];
+    {
+        float f = 0.40f;
+#pragma unroll
+        for (int k = 0; k < kLad; ++k) {
+            const float rr = fminf(f, 2.f) * g.h * (1.f - 1e-4f) - 1e-6f;
+            lad[k] = rr * rr;
+            f *= 1.1133f;
+        }
+    }
+    float *wd = s_d[w];
+    uint32_t *wj = s_j[w];
+    for (uint32_t e = blockIdx.x * kSlowWarps + w; e < nq; e += gridDim.x * kSlowWarps) {
+        const uint32_t t = S.cell[e];
+        const float4 p = S.spts[t];
+        const uint32_t i = __float_as_uint(p.w);
+        int c0[3];
+        cell_of(g, p.x, p.y, p.z, c0);
+        uint32_t rs = 0, re = 0;
+        if (lane < 25) {
+            const int cz = c0[2] + lane / 5 - 2, cy = c0[1] + lane % 5 - 2;
+            if (cz >= 0 && cz < g.dim[2] && cy >= 0 && cy < g.dim[1]) {
+                const int x0 = max(c0[0] - 2, 0), x1 = min(c0[0] + 2, g.dim[0] - 1);
+                const uint32_t row = (uint32_t)(((int64_t)cz * g.dim[1] + cy) * g.dim[0]);
+                rs = S.start[row + x0];
+                re = S.start[row + x1 + 1];
+            }
+        }
+        // ---- pass 1: counts within the trial radii
+        int cnt[kLad];
+#pragma unroll
+        for (int k = 0; k < kLad; ++k) cnt[k] = 0;
+        for (int r = 0; r < 25; ++r) {
+            const uint32_t s0 = __shfl_sync(0xffffffffu, rs, r), e0 = __shfl_sync(0xffffffffu, re, r);
+            for (uint32_t q = s0 + lane; q < e0; q += 32) {
+                const float d = dist2(S.spts[q], p);
+#pragma unroll
+                for (int k = 0; k < kLad; ++k) cnt[k] += d < lad[k] ? 1 : 0;
+            }
+        }
+        float T = -1.f;
+#pragma unroll
+        for (int k = kLad - 1; k >= 0; --k) {
+            int c = cnt[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if (c >= kK + 1 && c <= kSlowBuf + 1) T = lad[k];
+        }
+        if (T > 0.f) {
+            // ---- pass 2: the candidates within T, ranked
+            int m = 0;
+            for (int r = 0; r < 25; ++r) {
+                const uint32_t s0 = __shfl_sync(0xffffffffu, rs, r), e0 = __shfl_sync(0xffffffffu, re, r);
+                for (uint32_t b = s0; b < e0; b += 32) {
+                    const uint32_t q = b + lane;
+                    bool keep = false;
+                    float d = 0.f;
+                    uint32_t j = 0;
+                    if (q < e0) {
+                        const float4 pj = S.spts[q];
+                        j = __float_as_uint(pj.w);
+                        d = dist2(pj, p);
+                        keep = d < T && j != i;
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                    const int pos = m + __popc(bal & ((1u << lane) - 1u));
+                    if (keep && pos < kSlowBuf) {
+                        wd[pos] = d;
+                        wj[pos] = j;
+                    }
+                    m += __popc(bal);
+                }
+            }
+            m = min(m, kSlowBuf);
+            __syncwarp();
+            for (int a = lane; a < m; a += 32) {
+                const float da = wd[a];
+                const uint32_t ja = wj[a];
+                int rank = 0;
+                for (int b = 0; b < m; ++b) {
+                    const float db = wd[b];
+                    const uint32_t jb = wj[b];
+                    rank += (db < da || (db == da && jb < ja)) ? 1 : 0;
+                }
+                if (rank < kK) s_nb[w][rank] = ja;
+            }
+        } else if (lane == 0) {
+            // ---- last resort: incremental search over growing rings
+            KnnList best{wd, wj};
+            for (int k = 0; k < kK; ++k) { best.D(k) = INFINITY; best.J(k) = 0xffffffffu; }
+            float thr = INFINITY;
+            uint32_t thr_j = 0xffffffffu;
+            const int rmax = max(g.dim[0], max(g.dim[1], g.dim[2]));
+            for (int r = 0; r <= rmax; ++r) {
+                for (int dz = -r; dz <= r; ++dz) {
+                    const int cz = c0[2] + dz;
+                    if (cz < 0 || cz >= g.dim[2]) continue;
+                    for (int dy = -r; dy <= r; ++dy) {
+                        const int cy = c0[1] + dy;
+                        if (cy < 0 || cy >= g.dim[1]) continue;
+                        const bool shell = (dz == -r || dz == r || dy == -r || dy == r);
+                        for (int dx = -r; dx <= r; dx += (shell ? 1 : 2 * r)) {
+                            const int cx = c0[0] + dx;
+                            if (cx >= 0 && cx < g.dim[0]) {
+                                const uint32_t c = (uint32_t)(((int64_t)cz * g.dim[1] + cy) * g.dim[0] + cx);
+                                for (uint32_t q = S.start[c]; q < S.start[c + 1]; ++q) {
+                                    const float4 pj = S.spts[q];
+                                    const uint32_t j = __float_as_uint(pj.w);
+                                    if (j == i) continue;
+                                    const float d = dist2(pj, p);
+                                    if (d < thr || (d == thr && j < thr_j)) {
+                                        best.insert(d, j);
+                                        thr = best.D(kK - 1);
+                                        thr_j = best.J(kK - 1);
+                                    }
+                                }
+                            }
+                            if (r == 0) break;
+                        }
+                    }
+                }
+                const float bound = fmaxf(0.f, (float)r * g.h * (1.f - 1e-4f) - 1e-6f);
+                if (thr_j != 0xffffffffu && thr < bound * bound) break;
+            }
+            for (int k = 0; k < kK; ++k) s_nb[w][k] = best.J(k);
+        }
+        __syncwarp();
+        if (lane == 0)
+            pca_out(g, p, i, opacity, [&](int k) {
+                const uint32_t j = s_nb[w][k];
+                const float4 q = __ldg(xyz + j);
+                return make_float4(q.x, q.y, q.z, __uint_as_float(j));
+            }, rgb, knn_out, mean_op, scale, quat, rgb_out, normal);
+        __syncwarp();
     }
 }
 
@@ -640,10 +799,9 @@ cudaError_t launch_estimate(const float *xyz, const float *rgb, int64_t n, int32
     EstScratch S;
     est_layout(n, scratch, &S);
     cudaError_t e;
-    // bbox starts at (+inf, -inf); sums, counts, fill, tickets, look-back at 0
+    // bbox starts at (+inf, -inf); sums, counts, tickets, look-back at 0
     est_init_kernel<<<1, 32, 0, st>>>(S);
     if ((e = cudaMemsetAsync(S.counts, 0, (size_t)S.ncell_max * 4, st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(S.fill, 0, (size_t)S.ncell_max * 4, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(S.scan_state, 0, (size_t)(S.scan_tiles + 1) * 8, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(S.ticket, 0, 64, st)) != cudaSuccess) return e;
     int32_t *status = (int32_t *)(S.ticket + 8);
@@ -657,6 +815,10 @@ cudaError_t launch_estimate(const float *xyz, const float *rgb, int64_t n, int32
     uint32_t *knn = knn_idx ? knn_idx : S.knn;
     knn_pca_kernel<<<(unsigned)((n + kKnnThreads - 1) / kKnnThreads), kKnnThreads, 0, st>>>(
         (const float4 *)xyz, (const float4 *)rgb, n, pca_opacity, S, knn, (float4 *)out->mean_op,
+        (float4 *)out->scale, (float4 *)out->quat, (float4 *)out->rgb, (float4 *)out->normal);
+    // the listed queries, one warp each (their number is on the device)
+    knn_pca_slow_kernel<<<num_sms * 8, kSlowWarps * 32, 0, st>>>(
+        (const float4 *)xyz, (const float4 *)rgb, pca_opacity, S, knn, (float4 *)out->mean_op,
         (float4 *)out->scale, (float4 *)out->quat, (float4 *)out->rgb, (float4 *)out->normal);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (mode == 1) return launch_mlp_estimate(xyz, rgb, n, mlp, knn, out, S.mlp_scratch, num_sms, st);
