@@ -125,20 +125,32 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 64 consecutive fp32 accumulator columns of this thread's TMEM lane (one
+// load, one wait)
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+    uint32_t r[64];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+                 : "=r"(r[0]),"=r"(r[1]),"=r"(r[2]),"=r"(r[3]),"=r"(r[4]),"=r"(r[5]),"=r"(r[6]),"=r"(r[7]),"=r"(r[8]),"=r"(r[9]),"=r"(r[10]),"=r"(r[11]),"=r"(r[12]),"=r"(r[13]),"=r"(r[14]),"=r"(r[15]),"=r"(r[16]),"=r"(r[17]),"=r"(r[18]),"=r"(r[19]),"=r"(r[20]),"=r"(r[21]),"=r"(r[22]),"=r"(r[23]),"=r"(r[24]),"=r"(r[25]),"=r"(r[26]),"=r"(r[27]),"=r"(r[28]),"=r"(r[29]),"=r"(r[30]),"=r"(r[31]),"=r"(r[32]),"=r"(r[33]),"=r"(r[34]),"=r"(r[35]),"=r"(r[36]),"=r"(r[37]),"=r"(r[38]),"=r"(r[39]),"=r"(r[40]),"=r"(r[41]),"=r"(r[42]),"=r"(r[43]),"=r"(r[44]),"=r"(r[45]),"=r"(r[46]),"=r"(r[47]),"=r"(r[48]),"=r"(r[49]),"=r"(r[50]),"=r"(r[51]),"=r"(r[52]),"=r"(r[53]),"=r"(r[54]),"=r"(r[55]),"=r"(r[56]),"=r"(r[57]),"=r"(r[58]),"=r"(r[59]),"=r"(r[60]),"=r"(r[61]),"=r"(r[62]),"=r"(r[63])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]),"+r"(r[1]),"+r"(r[2]),"+r"(r[3]),"+r"(r[4]),"+r"(r[5]),"+r"(r[6]),"+r"(r[7]),"+r"(r[8]),"+r"(r[9]),"+r"(r[10]),"+r"(r[11]),"+r"(r[12]),"+r"(r[13]),"+r"(r[14]),"+r"(r[15]),"+r"(r[16]),"+r"(r[17]),"+r"(r[18]),"+r"(r[19]),"+r"(r[20]),"+r"(r[21]),"+r"(r[22]),"+r"(r[23]),"+r"(r[24]),"+r"(r[25]),"+r"(r[26]),"+r"(r[27]),"+r"(r[28]),"+r"(r[29]),"+r"(r[30]),"+r"(r[31]),"+r"(r[32]),"+r"(r[33]),"+r"(r[34]),"+r"(r[35]),"+r"(r[36]),"+r"(r[37]),"+r"(r[38]),"+r"(r[39]),"+r"(r[40]),"+r"(r[41]),"+r"(r[42]),"+r"(r[43]),"+r"(r[44]),"+r"(r[45]),"+r"(r[46]),"+r"(r[47]),"+r"(r[48]),"+r"(r[49]),"+r"(r[50]),"+r"(r[51]),"+r"(r[52]),"+r"(r[53]),"+r"(r[54]),"+r"(r[55]),"+r"(r[56]),"+r"(r[57]),"+r"(r[58]),"+r"(r[59]),"+r"(r[60]),"+r"(r[61]),"+r"(r[62]),"+r"(r[63]) : : "memory");
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // bias + ReLU + bf16 of a 64-wide accumulator row into the next A operand
 __device__ __forceinline__ void epilogue_hidden(uint32_t taddr, const float *bias, __nv_bfloat16 *H, int row) {
+    float v[kHid];
+    tmem_ld64(taddr, v);
 #pragma unroll
     for (int c16 = 0; c16 < kHid / 16; ++c16) {
-        float v[16];
-        tmem_ld16(taddr + c16 * 16, v);
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             uint32_t w[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int k = c16 * 16 + half * 8 + 2 * e;
-                const float lo = fmaxf(v[half * 8 + 2 * e] + bias[k], 0.f);
-                const float hi = fmaxf(v[half * 8 + 2 * e + 1] + bias[k + 1], 0.f);
+                const float lo = fmaxf(v[k] + bias[k], 0.f);
+                const float hi = fmaxf(v[k + 1] + bias[k + 1], 0.f);
                 const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
                 w[e] = *reinterpret_cast<const uint32_t *>(&p);
             }
@@ -165,7 +177,7 @@ __device__ __forceinline__ float4 qmul(float4 a, float4 b) {
                        a.x * b.z - a.y * b.w + a.z * b.x + a.w * b.y, a.x * b.w + a.y * b.z - a.z * b.y + a.w * b.x);
 }
 
-__global__ void __launch_bounds__(kTM) mlp_estimate_kernel(const float4 *__restrict__ xyz,
+__global__ void __launch_bounds__(kTM, 3) mlp_estimate_kernel(const float4 *__restrict__ xyz,
                                                            const float4 *__restrict__ rgb, int64_t n,
                                                            const unsigned char *__restrict__ blob,
                                                            const uint32_t *__restrict__ knn,
@@ -212,15 +224,52 @@ __global__ void __launch_bounds__(kTM) mlp_estimate_kernel(const float4 *__restr
     uint32_t phase = 0;
     const int64_t ntiles = (n + kTM - 1) / kTM;
 
+    // operands of a tile that need no gather, loaded one tile ahead so that
+    // their latency hides behind the previous tile's layers
+    struct Ahead {
+        float4 p, c, q, s0, m;
+        uint4 kn[4];
+    };
+    auto load_ahead = [&](int64_t tile, Ahead &A) {
+        const int64_t i = tile * kTM + tid;
+        if (tile < ntiles && i < n) {
+            A.p = __ldg(xyz + i);
+            A.c = __ldg(rgb + i);
+            A.q = quat[i];
+            A.s0 = scale[i];
+            A.m = mean_op[i];
+            const uint4 *kp = reinterpret_cast<const uint4 *>(knn + i * kNb);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) A.kn[k] = __ldg(kp + k);
+        } else {
+            A.p = A.c = A.s0 = A.m = make_float4(0.f, 0.f, 0.f, 0.f);
+            A.q = make_float4(1.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) A.kn[k] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    };
+    Ahead cur;
+    load_ahead(blockIdx.x, cur);
+
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t i = tile * kTM + tid;
         const bool live = i < n;
-        // ---- features of point i -> row tid of A
-        float4 p = make_float4(0, 0, 0, 0), c = p, q = make_float4(1, 0, 0, 0);
-        if (live) {
-            p = __ldg(xyz + i);
-            c = __ldg(rgb + i);
-            q = quat[i];
+        // ---- features of point i -> row tid of A; the 16 neighbours'
+        // positions and colours are all requested before any is used
+        const float4 p = cur.p, c = cur.c, q = cur.q;
+        const uint32_t nb[kNb] = {cur.kn[0].x, cur.kn[0].y, cur.kn[0].z, cur.kn[0].w,
+                                  cur.kn[1].x, cur.kn[1].y, cur.kn[1].z, cur.kn[1].w,
+                                  cur.kn[2].x, cur.kn[2].y, cur.kn[2].z, cur.kn[2].w,
+                                  cur.kn[3].x, cur.kn[3].y, cur.kn[3].z, cur.kn[3].w};
+        float4 pn[kNb], cn[kNb];
+#pragma unroll
+        for (int u = 0; u < kNb; ++u) {
+            pn[u] = p;
+            cn[u] = c;
+            if (live) {
+                pn[u] = __ldg(xyz + nb[u]);
+                cn[u] = __ldg(rgb + nb[u]);
+            }
         }
         const float w = q.x, x = q.y, y = q.z, z = q.w;
         const float R00 = 1.f - 2.f * (y * y + z * z), R01 = 2.f * (x * y - w * z), R02 = 2.f * (x * z + w * y);
@@ -228,22 +277,17 @@ __global__ void __launch_bounds__(kTM) mlp_estimate_kernel(const float4 *__restr
         const float R20 = 2.f * (x * z - w * y), R21 = 2.f * (y * z + w * x), R22 = 1.f - 2.f * (x * x + y * y);
         float inv_r = 0.f;
         if (live) {
-            const float4 pl = __ldg(xyz + knn[i * kNb + kNb - 1]);
+            const float4 pl = pn[kNb - 1];
             const float dx = pl.x - p.x, dy = pl.y - p.y, dz = pl.z - p.z;
             inv_r = 1.f / fmaxf(sqrtf(dx * dx + dy * dy + dz * dz), 1e-12f);
         }
-#pragma unroll 4
+#pragma unroll
         for (int k = 0; k < kNb; k += 4) {
             // 4 neighbours = 24 features = 3 core-matrix rows of 8
             float f[24];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                float4 pj = p, cj = c;
-                if (live) {
-                    const uint32_t j = knn[i * kNb + k + u];
-                    pj = __ldg(xyz + j);
-                    cj = __ldg(rgb + j);
-                }
+                const float4 pj = pn[k + u], cj = cn[k + u];
                 const float dx = pj.x - p.x, dy = pj.y - p.y, dz = pj.z - p.z;
                 f[6 * u + 0] = (R00 * dx + R10 * dy + R20 * dz) * inv_r;
                 f[6 * u + 1] = (R01 * dx + R11 * dy + R21 * dz) * inv_r;
@@ -267,21 +311,28 @@ __global__ void __launch_bounds__(kTM) mlp_estimate_kernel(const float4 *__restr
         proxy_fence();
         tc_fence_before();
         __syncthreads();
+        Ahead nxt;
+        load_ahead(tile + gridDim.x, nxt);
         // ---- four layers
         bool ok = true;
         const __nv_bfloat16 *Bs[4] = {sm.W1, sm.W2, sm.W3, sm.W4};
         for (int L = 0; L < 4 && ok; ++L) {
             if (tid == 0) issue_layer(tmem, L == 0 ? sm.A : H, Bs[L], L == 0 ? kIn : kHid, L == 3 ? kOutPad : kHid,
                                       &sm.mbar);
-            ok = !__syncthreads_or(!mbar_wait(&sm.mbar, phase));  // uniform decision
-            phase ^= 1u;
-            tc_fence_after();
-            if (!ok) break;
             if (L < 3) {
+                // the layer's one barrier also makes a wait that gave up
+                // known to all (the epilogue then read stale columns, unused)
+                const bool waited = mbar_wait(&sm.mbar, phase);
+                phase ^= 1u;
+                tc_fence_after();
                 epilogue_hidden(my_lane, sm.b + L * kHid, H, tid);
                 proxy_fence();
                 tc_fence_before();
-                __syncthreads();
+                ok = !__syncthreads_or(!waited);
+            } else {
+                ok = !__syncthreads_or(!mbar_wait(&sm.mbar, phase));  // uniform decision
+                phase ^= 1u;
+                tc_fence_after();
             }
         }
         if (!ok) {
@@ -296,7 +347,7 @@ __global__ void __launch_bounds__(kTM) mlp_estimate_kernel(const float4 *__restr
             float yy[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) yy[e] = yv[e] + sm.b[3 * kHid + e];
-            const float4 s0 = scale[i];
+            const float4 s0 = cur.s0;
             scale[i] = make_float4(s0.x * __expf(fminf(fmaxf(yy[0], -4.f), 4.f)),
                                    s0.y * __expf(fminf(fmaxf(yy[1], -4.f), 4.f)),
                                    s0.z * __expf(fminf(fmaxf(yy[2], -4.f), 4.f)), 0.f);
@@ -305,13 +356,14 @@ __global__ void __launch_bounds__(kTM) mlp_estimate_kernel(const float4 *__restr
             dq = make_float4(dq.x * dn, dq.y * dn, dq.z * dn, dq.w * dn);
             const float4 qf = qmul(q, dq);
             quat[i] = qf;
-            const float4 m = mean_op[i];
+            const float4 m = cur.m;
             const float o0 = fminf(fmaxf(m.w, 1e-6f), 1.f - 1e-6f);
             const float o = 1.f / (1.f + __expf(-(__logf(o0 / (1.f - o0)) + yy[7])));
             mean_op[i] = make_float4(m.x, m.y, m.z, o);
             const float W = qf.x, X = qf.y, Y = qf.z, Z = qf.w;
             normal[i] = make_float4(2.f * (X * Z + W * Y), 2.f * (Y * Z - W * X), 1.f - 2.f * (X * X + Y * Y), 0.f);
         }
+        cur = nxt;
         tc_fence_before();
         __syncthreads();
     }
@@ -342,11 +394,18 @@ cudaError_t launch_mlp_estimate(const float *xyz, const float *rgb, int64_t n, c
     }
     static int per_sm[64] = {0};
     if (!per_sm[slot]) {
-        // resident CTAs per SM: shared memory (1 KB reserved per CTA) and
-        // TMEM (64 columns per CTA of the SM's 512); registers allow more
-        int smem_sm = 0;
+        // resident CTAs per SM: shared memory (1 KB reserved per CTA),
+        // TMEM (64 columns per CTA of the SM's 512) and registers, so that
+        // every CTA of the persistent grid is resident from the start
+        int smem_sm = 0, occ = 0;
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        per_sm[slot] = std::max(1, std::min(smem_sm / (int)(smem + 1024), 512 / (int)kTmemCols));
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, mlp_estimate_kernel) == cudaSuccess && fa.numRegs > 0) {
+            const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;  // allocation unit: 256 per warp
+            occ = 65536 / (warp_regs * (kTM / 32));
+        }
+        occ = std::max(occ, 1);
+        per_sm[slot] = std::max(1, std::min(std::min(smem_sm / (int)(smem + 1024), 512 / (int)kTmemCols), occ));
     }
     const int64_t ntiles = (n + kTM - 1) / kTM;
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms * per_sm[slot]);
