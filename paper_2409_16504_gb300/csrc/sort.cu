@@ -1,13 +1,21 @@
 // K2-K5: duplication into (tile id | depth) keys, LSD radix sort, tile
 // ranges.  Depth ordering of the splats that cover a pixel (Sec. 3.1) is
-// realised per screen tile: keys are ((tile id) << 32 | fp32 depth bits), so
-// one stable sort on the significant bits orders every tile's list by
-// depth, ties by Gaussian index (keys are emitted in index order).
+// realised per screen tile: keys are ((tile id) << 32 | fp32 depth bits), and
+// every tile's list comes out ordered by depth, ties by Gaussian index.
 //
-// K2+K3  scan_emit:  single-pass exclusive scan of the per-Gaussian tile
-//        counts (decoupled look-back) fused with key emission.
-// K4     radix sort: a global digit histogram pass, then one kernel per
-//        8-bit digit: stable warp-level multisplit ranking in shared memory,
+// Depth first (the key buffers hold at least one entry per Gaussian):
+//   depth_keys (keys and digit histograms) + 4 radix passes: the Gaussians
+//        sorted by depth (the 32 depth bits of (depth << 32 | index) keys,
+//        stable), into buffer 1;
+//   scan_emit: single-pass exclusive scan of the tile counts in that order
+//        (decoupled look-back) fused with key emission, into buffer 0;
+//   1-2 radix passes on the tile bits only (stable), so each tile keeps the
+//        depth order of emission.  Two passes over the tile keys instead of
+//        six: the depth digits are sorted once per Gaussian, not per key.
+// Otherwise: emission in index order and passes over all 32 + tile bits.
+//
+// K4 radix pass: a global digit histogram pass, then one kernel per 8-bit
+//        digit: stable warp-level multisplit ranking in shared memory,
 //        decoupled look-back across tiles for the digit offsets, and a
 //        shared-memory staged scatter so that writes are runs of equal digit.
 // K5     tile_ranges: [start, end) of every tile in the sorted keys.
@@ -18,6 +26,11 @@
 #include "common.cuh"
 
 namespace p2e {
+
+// look-back waits: spin (one L2 round trip per try) before sleeping
+__device__ __forceinline__ void backoff_lb(uint32_t it) {
+    if (it > 64) __nanosleep(it < 1024 ? 32 : 256);
+}
 
 // ---------------------------------------------------------------------------
 // scratch layout (see sort_scratch_bytes)
@@ -36,6 +49,7 @@ constexpr int kMaxPasses = 8;
 struct SortScratch {
     uint32_t *hist;        // [kMaxPasses][256] digit totals
     uint32_t *tickets;     // [16]: [0] scan, [1 + p] sort pass p
+    int64_t *n_depth;      // number of Gaussians in the depth sort
     uint64_t *scan_state;  // [scan tiles] look-back words (flag << 62 | value)
     uint32_t *sort_state;  // [kMaxPasses][sort tiles][256] (flag << 30 | count)
     int64_t scan_tiles, sort_tiles;
@@ -46,7 +60,7 @@ __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_
 size_t sort_scratch_bytes(int64_t n_total, int64_t capacity) {
     const int64_t st = (n_total + kScanTile - 1) / kScanTile;
     const int64_t kt = (capacity + kSortTile - 1) / kSortTile;
-    return align256(kMaxPasses * kRadix * 4) + align256(16 * 4) + align256((size_t)(st + 1) * 8) +
+    return align256(kMaxPasses * kRadix * 4) + align256(16 * 4) + align256(8) + align256((size_t)(st + 1) * 8) +
            align256((size_t)kMaxPasses * (size_t)(kt + 1) * kRadix * 4);
 }
 
@@ -59,6 +73,8 @@ static SortScratch carve(void *base, int64_t n_total, int64_t capacity) {
     p += align256(kMaxPasses * kRadix * 4);
     s.tickets = (uint32_t *)p;
     p += align256(16 * 4);
+    s.n_depth = (int64_t *)p;
+    p += align256(8);
     s.scan_state = (uint64_t *)p;
     p += align256((size_t)(s.scan_tiles + 1) * 8);
     s.sort_state = (uint32_t *)p;
@@ -113,7 +129,8 @@ __device__ __forceinline__ uint64_t block_excl_sum(uint64_t v, uint64_t &total, 
 
 __global__ void __launch_bounds__(kScanThreads) scan_emit_kernel(
     const uint32_t *__restrict__ ntiles, const ushort4 *__restrict__ rect,
-    const float4 *__restrict__ xy_depth, int64_t n_total, uint64_t *__restrict__ keys,
+    const float4 *__restrict__ xy_depth, const uint32_t *__restrict__ order, int64_t n_total,
+    uint64_t *__restrict__ keys,
     uint32_t *__restrict__ vals, int64_t capacity, SortScratch S, int64_t *n_keys_dev,
     int32_t *status, __grid_constant__ const Views P) {
     __shared__ uint64_t sm[kScanThreads / 32];
@@ -123,47 +140,62 @@ __global__ void __launch_bounds__(kScanThreads) scan_emit_kernel(
     __syncthreads();
     const int64_t tile = s_tile;
     const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    uint32_t cnt[kScanItems];
+    uint32_t cnt[kScanItems], src[kScanItems];
     uint64_t local = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-        const int64_t e = base + i;
-        cnt[i] = e < n_total ? __ldg(ntiles + e) : 0u;
+        const int64_t r = base + i;  // position in emission order: Gaussian order[r] (or r)
+        src[i] = r < n_total ? (order ? __ldg(order + r) : (uint32_t)r) : 0u;
+        cnt[i] = r < n_total ? __ldg(ntiles + src[i]) : 0u;
         local += cnt[i];
     }
     uint64_t total;
     const uint64_t texcl = block_excl_sum<kScanThreads>(local, total, sm);
-    // decoupled look-back (one thread; tiles usually find their predecessor's
-    // inclusive prefix immediately)
-    if (threadIdx.x == 0) {
+    // decoupled look-back by warp 0, 32 predecessors per round trip
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
         uint64_t prefix = 0;
         if (tile == 0) {
-            st_release_u64(&S.scan_state[0], kFlagPre | total);
+            if (lane == 0) st_release_u64(&S.scan_state[0], kFlagPre | total);
         } else {
-            st_release_u64(&S.scan_state[tile], kFlagAgg | total);
-            int64_t p = tile - 1;
+            if (lane == 0) st_release_u64(&S.scan_state[tile], kFlagAgg | total);
+            int64_t p = tile - 1;  // lane l reads p - l
             uint32_t spins = 0;
-            while (p >= 0) {
-                const uint64_t w = ld_acquire_u64(&S.scan_state[p]);
-                if ((w >> 62) == 0) {
-                    if (++spins > kSpinLimit) { atomicExch(status, (int32_t)P2E_ERR_TIMEOUT); break; }
-                    backoff(spins);
+            while (true) {
+                const int64_t idx = p - lane;
+                const uint64_t w = idx >= 0 ? ld_acquire_u64(&S.scan_state[idx]) : kFlagPre;
+                const uint32_t flag = (uint32_t)(w >> 62);
+                const unsigned pre = __ballot_sync(0xffffffffu, flag == 2u);
+                const unsigned notready = __ballot_sync(0xffffffffu, flag == 0u);
+                const int first = pre ? __ffs(pre) - 1 : 32;
+                const unsigned need = first >= 31 ? 0xffffffffu : ((2u << first) - 1u);
+                if (notready & need) {
+                    if (++spins > kSpinLimit) {
+                        if (lane == 0) atomicExch(status, (int32_t)P2E_ERR_TIMEOUT);
+                        break;
+                    }
+                    backoff_lb(spins);
                     continue;
                 }
-                prefix += w & kValMask;
-                if ((w >> 62) == 2) break;
-                --p;
+                uint64_t add = lane <= first ? (w & kValMask) : 0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
+                prefix += add;
+                if (first < 32) break;
+                p -= 32;
             }
-            st_release_u64(&S.scan_state[tile], kFlagPre | (prefix + total));
+            if (lane == 0) st_release_u64(&S.scan_state[tile], kFlagPre | (prefix + total));
         }
-        s_prefix = prefix;
-        if (tile == S.scan_tiles - 1) *n_keys_dev = (int64_t)(prefix + total);
+        if (lane == 0) {
+            s_prefix = prefix;
+            if (tile == S.scan_tiles - 1) *n_keys_dev = (int64_t)(prefix + total);
+        }
     }
     __syncthreads();
     uint64_t off = s_prefix + texcl;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-        const int64_t e = base + i;
+        const int64_t e = src[i];
         if (cnt[i] != 0u) {
             const int vi = (int)(e / P.n);
             const View &V = P.v[vi];
@@ -187,6 +219,44 @@ __global__ void __launch_bounds__(kScanThreads) scan_emit_kernel(
     }
 }
 
+// Depth keys of all Gaussians (every view): (fp32 depth bits << 32 | e),
+// value e; a Gaussian that covers no tile sorts last.  The histograms of
+// the four depth bytes (the depth passes' digits) are counted on the way.
+__global__ void __launch_bounds__(256) depth_keys_kernel(const uint32_t *__restrict__ ntiles,
+                                                         const float4 *__restrict__ xy_depth, int64_t n_total,
+                                                         uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                                         int64_t *n_depth, uint32_t *__restrict__ hist) {
+    __shared__ uint32_t sh[4 * kRadix];
+    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_depth = n_total;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n_total; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = base + threadIdx.x;
+        const bool valid = e < n_total;
+        uint32_t zb = 0xffffffffu;
+        if (valid) {
+            if (__ldg(ntiles + e)) zb = __float_as_uint(__ldg(&xy_depth[e].z));
+            keys[e] = ((uint64_t)zb << 32) | (uint64_t)e;
+            vals[e] = (uint32_t)e;
+        }
+        // the low bytes spread over the bins; the high ones (sign, exponent)
+        // crowd a few, so equal digits of a warp are added once
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            if (valid) atomicAdd(&sh[b * kRadix + ((zb >> (8 * b)) & 255u)], 1u);
+#pragma unroll
+        for (int b = 2; b < 4; ++b) {
+            const uint32_t d = valid ? (zb >> (8 * b)) & 255u : 256u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (valid && lane == 31 - __clz(peers)) atomicAdd(&sh[b * kRadix + d], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
 // ---------------------------------------------------------------------------
 // K4: radix sort
 // ---------------------------------------------------------------------------
@@ -197,7 +267,7 @@ __device__ __forceinline__ int64_t sort_count(const int64_t *n_keys_dev, int64_t
 
 __global__ void __launch_bounds__(256) digit_hist_kernel(const uint64_t *__restrict__ keys,
                                                          const int64_t *n_keys_dev, int64_t capacity,
-                                                         int passes, uint32_t *__restrict__ hist) {
+                                                         int shift0, int passes, uint32_t *__restrict__ hist) {
     __shared__ uint32_t sh[kMaxPasses * kRadix];
     for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) sh[i] = 0;
     __syncthreads();
@@ -208,7 +278,7 @@ __global__ void __launch_bounds__(256) digit_hist_kernel(const uint64_t *__restr
         const bool valid = i < K;
         const uint64_t k = valid ? keys[i] : 0ull;
         for (int p = 0; p < passes; ++p) {
-            const uint32_t d = valid ? (uint32_t)(k >> (8 * p)) & 255u : 256u;
+            const uint32_t d = valid ? (uint32_t)(k >> (shift0 + 8 * p)) & 255u : 256u;
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
             if (valid && lane == 31 - __clz(peers)) atomicAdd(&sh[p * kRadix + d], (uint32_t)__popc(peers));
         }
@@ -301,7 +371,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
             const uint32_t w = ld_acquire_u32(sort_state + (size_t)p * kRadix + d);
             if ((w >> 30) == 0) {
                 if (++spins > kSpinLimit) { atomicExch(status, (int32_t)P2E_ERR_TIMEOUT); break; }
-                backoff(spins);
+                backoff_lb(spins);
                 continue;
             }
             prefix += w & kSValMask;
@@ -401,18 +471,6 @@ cudaError_t launch_sort_bin(const p2e_projected *proj, const Views &P, p2e_bins 
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(io->n_keys_dev, 0, sizeof(int64_t), st);
     if (e != cudaSuccess) return e;
-    if (n_total > 0) {
-        const unsigned g = (unsigned)S.scan_tiles;
-        scan_emit_kernel<<<g, kScanThreads, 0, st>>>(proj->ntiles, (const ushort4 *)proj->rect,
-                                                     (const float4 *)proj->xy_depth, n_total,
-                                                     io->keys[0], io->vals[0], io->capacity, S,
-                                                     io->n_keys_dev, io->status_dev, P);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    // digit histograms of every pass in one read of the keys
-    digit_hist_kernel<<<num_sms * 4, 256, 0, st>>>(io->keys[0], io->n_keys_dev, io->capacity,
-                                                   passes, S.hist);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t smem = sizeof(SortSmem);
     static bool attr_set = false;
     if (!attr_set) {
@@ -420,15 +478,52 @@ cudaError_t launch_sort_bin(const p2e_projected *proj, const Views &P, p2e_bins 
         attr_set = true;
     }
     const unsigned sort_grid = (unsigned)(S.sort_tiles > 0 ? S.sort_tiles : 1);
-    for (int p = 0; p < passes; ++p) {
-        const int src = p & 1, dst = src ^ 1;
-        radix_pass_kernel<<<sort_grid, kSortThreads, smem, st>>>(
-            io->keys[src], io->vals[src], io->keys[dst], io->vals[dst], io->n_keys_dev, io->capacity,
-            8 * p, S.hist + p * kRadix, S.sort_state + (size_t)p * (S.sort_tiles + 1) * kRadix,
-            S.tickets + 1 + p, io->status_dev);
+    auto pass = [&](int slot, int src, int shift, const int64_t *count, unsigned grid) {
+        radix_pass_kernel<<<grid, kSortThreads, smem, st>>>(
+            io->keys[src], io->vals[src], io->keys[src ^ 1], io->vals[src ^ 1], count, io->capacity, shift,
+            S.hist + slot * kRadix, S.sort_state + (size_t)slot * (S.sort_tiles + 1) * kRadix,
+            S.tickets + 1 + slot, io->status_dev);
+        return cudaGetLastError();
+    };
+    const unsigned scan_grid = (unsigned)S.scan_tiles;
+    if (n_total > 0 && n_total <= io->capacity) {
+        // depth first: sort the Gaussians by depth (four passes over n_total
+        // keys, into buffer 1), emit the tile keys in that order, then sort
+        // them stably by tile only
+        const int tpasses = passes - 4;
+        depth_keys_kernel<<<num_sms * 2, 256, 0, st>>>(proj->ntiles, (const float4 *)proj->xy_depth, n_total,
+                                                       io->keys[1], io->vals[1], S.n_depth, S.hist);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const unsigned dgrid = (unsigned)((n_total + kSortTile - 1) / kSortTile);
+        for (int p = 0; p < 4; ++p)
+            if ((e = pass(p, (p & 1) ? 0 : 1, 32 + 8 * p, S.n_depth, dgrid)) != cudaSuccess) return e;
+        scan_emit_kernel<<<scan_grid, kScanThreads, 0, st>>>(proj->ntiles, (const ushort4 *)proj->rect,
+                                                             (const float4 *)proj->xy_depth, io->vals[1], n_total,
+                                                             io->keys[0], io->vals[0], io->capacity, S,
+                                                             io->n_keys_dev, io->status_dev, P);
+        digit_hist_kernel<<<num_sms * 4, 256, 0, st>>>(io->keys[0], io->n_keys_dev, io->capacity, 32, tpasses,
+                                                       S.hist + 4 * kRadix);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        for (int p = 0; p < tpasses; ++p)
+            if ((e = pass(4 + p, p & 1, 32 + 8 * p, io->n_keys_dev, sort_grid)) != cudaSuccess) return e;
+        io->result = tpasses & 1;
+    } else {
+        // all key bits, least significant first
+        if (n_total > 0) {
+            scan_emit_kernel<<<scan_grid, kScanThreads, 0, st>>>(proj->ntiles, (const ushort4 *)proj->rect,
+                                                                 (const float4 *)proj->xy_depth, nullptr, n_total,
+                                                                 io->keys[0], io->vals[0], io->capacity, S,
+                                                                 io->n_keys_dev, io->status_dev, P);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        digit_hist_kernel<<<num_sms * 4, 256, 0, st>>>(io->keys[0], io->n_keys_dev, io->capacity, 0, passes,
+                                                       S.hist);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        for (int p = 0; p < passes; ++p)
+            if ((e = pass(p, p & 1, 8 * p, io->n_keys_dev, sort_grid)) != cudaSuccess) return e;
+        io->result = passes & 1;
     }
-    io->result = passes & 1;
+
     tile_ranges_kernel<<<num_sms * 8, 256, 0, st>>>(io->keys[io->result], io->n_keys_dev, io->capacity,
                                                     P.total_tiles, (uint2 *)io->ranges);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -184,3 +184,31 @@ def test_segment_chains_schedule_independent():
     assert mode(big) == 1 and mode(tight) == 0
     for key in ("rgb", "normal", "depth", "alpha", "last"):
         assert torch.equal(getattr(a, key), getattr(b, key)), key
+
+
+def test_depth_first_and_full_key_binning_agree():
+    """Binning sorts the Gaussians by depth first and then the tile keys by
+    tile only when the key buffers hold an entry per Gaussian; with fewer
+    entries it sorts all key bits.  Both give the same sorted keys, values,
+    tile ranges and images, and both match the oracle's binning."""
+    from paper_2409_16504_gb300 import GaussianSet, Renderer
+    g, cam = humanoid_scene(120_000, 512, 512, seed=7)
+    cam = dict(cam, cx=cam["cx"] - 0.5 * cam["width"])  # half the figure off screen
+    gs = GaussianSet.from_numpy(g)
+    big = Renderer(capacity=1 << 20)
+    a = big.render(gs, [cam])
+    k = big.n_keys
+    n = len(g["mean"])
+    assert 1000 < k < n  # the small buffers cannot take the depth sort
+    small = Renderer(capacity=k)
+    b = small.render(gs, [cam])
+    torch.cuda.synchronize()
+    ka, va = big.bins.sorted()
+    kb, vb = small.bins.sorted()
+    assert torch.equal(ka[:k], kb[:k]) and torch.equal(va[:k], vb[:k])
+    tt = big.bins.ranges.numel()
+    assert torch.equal(big.bins.ranges[:tt], small.bins.ranges[:tt])
+    for key in ("rgb", "normal", "depth", "alpha", "last"):
+        assert torch.equal(getattr(a, key), getattr(b, key)), key
+    _check_bins(big, g, [cam])
+    _check_bins(small, g, [cam])
