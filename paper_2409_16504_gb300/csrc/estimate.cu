@@ -546,8 +546,9 @@ __global__ void __launch_bounds__(kKnnThreads, 6) knn_pca_kernel(const float4 *_
                                                               float4 *__restrict__ quat,
                                                               float4 *__restrict__ rgb_out,
                                                               float4 *__restrict__ normal) {
-    __shared__ float s_d[kBuf * kKnnThreads];
-    __shared__ uint32_t s_j[kBuf * kKnnThreads];
+    // candidates as (fp32 distance bits << 32 | index): d >= 0, so the
+    // unsigned order of the keys is the order by (distance, index)
+    __shared__ uint64_t s_key[kBuf * kKnnThreads];
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     const GridParams g = *S.gp;
@@ -563,50 +564,58 @@ __global__ void __launch_bounds__(kKnnThreads, 6) knn_pca_kernel(const float4 *_
     }
     float T = -1.f;
     {
-        int cnt[kRadA] = {0, 0, 0, 0, 0};
+        // counts kept in fp32 on the FMA pipe: fma(-d, 2^100, r 2^100) is
+        // (r - d) 2^100 rounded once (the scaling is exact): <= 0 when
+        // d >= r, and for d < r at least 2^100 times the fp32 spacing at r,
+        // >= 1 for any r above 2^-76, so the saturated value is 1 exactly when
+        // d < r (pass 2 counts the chosen radius exactly in any case)
+        float rB[kRadA], cf[kRadA];
+#pragma unroll
+        for (int k = 0; k < kRadA; ++k) {
+            rB[k] = rA[k] * 0x1p100f;
+            cf[k] = 0.f;
+        }
         for_block(g, S, c0, p, rA[kRadA - 1], [&](const float4 &pj) {
             const float d = dist2(pj, p);
 #pragma unroll
-            for (int k = 0; k < kRadA; ++k) cnt[k] += d < rA[k] ? 1 : 0;
+            for (int k = 0; k < kRadA; ++k) cf[k] += __saturatef(fmaf(-d, 0x1p100f, rB[k]));
         });
 #pragma unroll
         for (int k = kRadA - 1; k >= 0; --k)
-            if (cnt[k] >= kK + 1 && cnt[k] <= kBuf + 1) T = rA[k];
+            if (cf[k] >= (float)(kK + 1) && cf[k] <= (float)(kBuf + 1)) T = rA[k];
     }
     if (T < 0.f) {
         S.cell[atomicAdd(S.ticket + 12, 1u)] = (uint32_t)t;
         return;
     }
-    float *bd = s_d + threadIdx.x;
-    uint32_t *bj = s_j + threadIdx.x;
-    int m = 0;
+    uint64_t *bk = s_key + threadIdx.x;
+    int m = 0;  // candidates inside T (kept: the first kBuf)
     for_block(g, S, c0, p, T, [&](const float4 &pj) {
         const uint32_t j = __float_as_uint(pj.w);
         const float d = dist2(pj, p);
-        if (d < T && j != i && m < kBuf) {
-            bd[m * kKnnThreads] = d;
-            bj[m * kKnnThreads] = j;
+        if (d < T && j != i) {
+            if (m < kBuf) bk[m * kKnnThreads] = ((uint64_t)__float_as_uint(d) << 32) | j;
             ++m;
         }
     });
-    // partial selection sort: the 16 smallest (d, j) to the front
+    if (m < kK || m > kBuf) {  // only if the counts of pass 1 were off
+        S.cell[atomicAdd(S.ticket + 12, 1u)] = (uint32_t)t;
+        return;
+    }
+    // partial selection sort: the 16 smallest keys to the front
     for (int a = 0; a < kK; ++a) {
         int best_k = a;
-        float dbst = bd[a * kKnnThreads];
-        uint32_t jbst = bj[a * kKnnThreads];
+        uint64_t kbst = bk[a * kKnnThreads];
 #pragma unroll 4
         for (int b = a + 1; b < m; ++b) {
-            const float db = bd[b * kKnnThreads];
-            const uint32_t jb = bj[b * kKnnThreads];
-            if (db < dbst || (db == dbst && jb < jbst)) { best_k = b; dbst = db; jbst = jb; }
+            const uint64_t kb = bk[b * kKnnThreads];
+            if (kb < kbst) { best_k = b; kbst = kb; }
         }
-        bd[best_k * kKnnThreads] = bd[a * kKnnThreads];
-        bj[best_k * kKnnThreads] = bj[a * kKnnThreads];
-        bd[a * kKnnThreads] = dbst;
-        bj[a * kKnnThreads] = jbst;
+        bk[best_k * kKnnThreads] = bk[a * kKnnThreads];
+        bk[a * kKnnThreads] = kbst;
     }
     pca_out(g, p, i, opacity, [&](int k) {
-        const uint32_t j = bj[k * kKnnThreads];
+        const uint32_t j = (uint32_t)bk[k * kKnnThreads];
         const float4 q = __ldg(xyz + j);
         return make_float4(q.x, q.y, q.z, __uint_as_float(j));
     }, rgb, knn_out, mean_op, scale, quat, rgb_out, normal);
