@@ -424,16 +424,17 @@ __device__ __forceinline__ void for_block(const GridParams &g, const EstScratch 
             const int x1 = (c0[0] + 1 < g.dim[0] && ey + hi2[0] <= R2) ? c0[0] + 1 : c0[0];
             const uint32_t row = (uint32_t)(((int64_t)cz * g.dim[1] + cy) * g.dim[0]);
             // cells x0..x1 of a row are contiguous in the cell-ordered points
-            const uint32_t s0 = S.start[row + x0], e0 = S.start[row + x1 + 1];
+            const uint32_t s0 = __ldg(S.start + row + x0), e0 = __ldg(S.start + row + x1 + 1);
             uint32_t q = s0;
             for (; q + 4 <= e0; q += 4) {  // four independent loads in flight
-                const float4 a0 = S.spts[q], a1 = S.spts[q + 1], a2 = S.spts[q + 2], a3 = S.spts[q + 3];
+                const float4 a0 = __ldg(S.spts + q), a1 = __ldg(S.spts + q + 1), a2 = __ldg(S.spts + q + 2),
+                             a3 = __ldg(S.spts + q + 3);
                 f(a0);
                 f(a1);
                 f(a2);
                 f(a3);
             }
-            for (; q < e0; ++q) f(S.spts[q]);
+            for (; q < e0; ++q) f(__ldg(S.spts + q));
         }
     }
 }
@@ -528,11 +529,12 @@ __device__ __forceinline__ float dist2(const float4 &a, const float4 &p) {
 // Fast path, one thread per query point (points taken in cell order).
 // Exact 16 nearest other points, ties by index:
 //   pass 1  count the candidates within five trial radii (0.40 .. 0.75 cell
-//           sizes, branch free) over only the cells of the 3x3x3 block that
-//           the largest ball can reach, and pick the smallest radius T that
-//           holds 16 others (and at most kBuf);
+//           sizes, branch free, on the FMA pipe) over only the cells of the
+//           3x3x3 block that the largest ball can reach, and pick the
+//           smallest radius T that holds 16 others (and at most kBuf);
 //   pass 2  keep the candidates within T (the cells that ball reaches) in
-//           shared memory and select the 16 smallest.
+//           shared memory as (distance bits, index) keys, check their count
+//           and select the 16 smallest keys.
 // A query for which no trial radius qualifies (about 0.5 % of the points of
 // a surface scan: sparse or ragged regions) is appended to a list (S.cell
 // reused, its length in S.ticket[12]) for knn_pca_slow_kernel, so that no
