@@ -47,6 +47,7 @@ struct EstScratch {
     uint64_t *scan_state; // scan tiles + 1
     uint32_t *ticket;
     float4 *spts;         // n points in cell order, .w = bits of the original index
+    float4 *pk;           // 2n: point i's position and colour in one 32-byte record (learned path)
     uint32_t *knn;        // n * 16 (when the caller passes none)
     void *mlp_scratch;    // see mlp.cu
     int64_t ncell_max, scan_tiles;
@@ -79,6 +80,7 @@ static size_t est_layout(int64_t n, void *base, EstScratch *S) {
     s.ticket = (uint32_t *)take(64);
     s.spts = (float4 *)take((size_t)n * 16);
     s.knn = (uint32_t *)take((size_t)n * kK * 4);
+    s.pk = (float4 *)take((size_t)n * 32);
     s.mlp_scratch = take(mlp_scratch_bytes(n));
     s.ncell_max = nc;
     s.scan_tiles = st;
@@ -180,10 +182,17 @@ __device__ __forceinline__ void cell_of(const GridParams &g, float x, float y, f
     }
 }
 
-__global__ void __launch_bounds__(256) cell_count_kernel(const float4 *__restrict__ xyz, int64_t n, EstScratch S) {
+// Cell of every point and the cells' counts; with rgb, also the packed
+// (position, colour) records the MLP gathers (one 32-byte sector per point).
+__global__ void __launch_bounds__(256) cell_count_kernel(const float4 *__restrict__ xyz,
+                                                         const float4 *__restrict__ rgb, int64_t n, EstScratch S) {
     const GridParams g = *S.gp;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float4 p = __ldg(xyz + i);
+        if (rgb) {
+            S.pk[2 * i] = p;
+            S.pk[2 * i + 1] = __ldg(rgb + i);
+        }
         int c[3];
         cell_of(g, p.x, p.y, p.z, c);
         const uint32_t id = (uint32_t)(((int64_t)c[2] * g.dim[1] + c[1]) * g.dim[0] + c[0]);
@@ -800,7 +809,7 @@ __global__ void est_init_kernel(EstScratch S) {
     }
 }
 
-cudaError_t launch_mlp_estimate(const float *xyz, const float *rgb, int64_t n, const void *mlp,
+cudaError_t launch_mlp_estimate(const float4 *pk, int64_t n, const void *mlp,
                                 const uint32_t *knn, p2e_gaussians *out, void *scratch, int num_sms,
                                 cudaStream_t st);
 
@@ -819,7 +828,7 @@ cudaError_t launch_estimate(const float *xyz, const float *rgb, int64_t n, int32
     const int g1 = num_sms * 4;
     bbox_kernel<<<num_sms * 2, 256, 0, st>>>((const float4 *)xyz, n, S);
     grid_setup_kernel<<<1, 1, 0, st>>>(n, S);
-    cell_count_kernel<<<g1, 256, 0, st>>>((const float4 *)xyz, n, S);
+    cell_count_kernel<<<g1, 256, 0, st>>>((const float4 *)xyz, mode == 1 ? (const float4 *)rgb : nullptr, n, S);
     scan_counts_kernel<<<(unsigned)S.scan_tiles, 256, 0, st>>>(S.counts, S.ncell_max, S.start, S, status);
     scatter_kernel<<<g1, 256, 0, st>>>((const float4 *)xyz, n, S);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -832,7 +841,7 @@ cudaError_t launch_estimate(const float *xyz, const float *rgb, int64_t n, int32
         (const float4 *)xyz, (const float4 *)rgb, pca_opacity, S, knn, (float4 *)out->mean_op,
         (float4 *)out->scale, (float4 *)out->quat, (float4 *)out->rgb, (float4 *)out->normal);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (mode == 1) return launch_mlp_estimate(xyz, rgb, n, mlp, knn, out, S.mlp_scratch, num_sms, st);
+    if (mode == 1) return launch_mlp_estimate(S.pk, n, mlp, knn, out, S.mlp_scratch, num_sms, st);
     return cudaSuccess;
 }
 

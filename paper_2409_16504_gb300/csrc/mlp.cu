@@ -177,8 +177,7 @@ __device__ __forceinline__ float4 qmul(float4 a, float4 b) {
                        a.x * b.z - a.y * b.w + a.z * b.x + a.w * b.y, a.x * b.w + a.y * b.z - a.z * b.y + a.w * b.x);
 }
 
-__global__ void __launch_bounds__(kTM, 3) mlp_estimate_kernel(const float4 *__restrict__ xyz,
-                                                           const float4 *__restrict__ rgb, int64_t n,
+__global__ void __launch_bounds__(kTM, 3) mlp_estimate_kernel(const float4 *__restrict__ pk, int64_t n,
                                                            const unsigned char *__restrict__ blob,
                                                            const uint32_t *__restrict__ knn,
                                                            float4 *__restrict__ mean_op, float4 *__restrict__ scale,
@@ -233,8 +232,8 @@ __global__ void __launch_bounds__(kTM, 3) mlp_estimate_kernel(const float4 *__re
     auto load_ahead = [&](int64_t tile, Ahead &A) {
         const int64_t i = tile * kTM + tid;
         if (tile < ntiles && i < n) {
-            A.p = __ldg(xyz + i);
-            A.c = __ldg(rgb + i);
+            A.p = __ldg(pk + 2 * i);
+            A.c = __ldg(pk + 2 * i + 1);
             A.q = quat[i];
             A.s0 = scale[i];
             A.m = mean_op[i];
@@ -266,9 +265,9 @@ __global__ void __launch_bounds__(kTM, 3) mlp_estimate_kernel(const float4 *__re
         for (int u = 0; u < kNb; ++u) {
             pn[u] = p;
             cn[u] = c;
-            if (live) {
-                pn[u] = __ldg(xyz + nb[u]);
-                cn[u] = __ldg(rgb + nb[u]);
+            if (live) {  // both halves of one 32-byte record
+                pn[u] = __ldg(pk + 2 * (size_t)nb[u]);
+                cn[u] = __ldg(pk + 2 * (size_t)nb[u] + 1);
             }
         }
         const float w = q.x, x = q.y, y = q.z, z = q.w;
@@ -376,7 +375,7 @@ __global__ void __launch_bounds__(kTM, 3) mlp_estimate_kernel(const float4 *__re
     }
 }
 
-cudaError_t launch_mlp_estimate(const float *xyz, const float *rgb, int64_t n, const void *mlp,
+cudaError_t launch_mlp_estimate(const float4 *pk, int64_t n, const void *mlp,
                                 const uint32_t *knn, p2e_gaussians *out, void *scratch, int num_sms,
                                 cudaStream_t st) {
     int32_t *status = (int32_t *)scratch;
@@ -409,7 +408,7 @@ cudaError_t launch_mlp_estimate(const float *xyz, const float *rgb, int64_t n, c
     }
     const int64_t ntiles = (n + kTM - 1) / kTM;
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms * per_sm[slot]);
-    mlp_estimate_kernel<<<grid, kTM, smem, st>>>((const float4 *)xyz, (const float4 *)rgb, n,
+    mlp_estimate_kernel<<<grid, kTM, smem, st>>>(pk, n,
                                                  (const unsigned char *)mlp, knn, (float4 *)out->mean_op,
                                                  (float4 *)out->scale, (float4 *)out->quat, (float4 *)out->normal,
                                                  status);

@@ -324,7 +324,7 @@ __device__ __forceinline__ bool project_fp32(const View &V, const Views &P, floa
     return true;
 }
 
-__global__ void __launch_bounds__(256) project_kernel(const float4 *__restrict__ mean_op,
+__global__ void __launch_bounds__(256, 4) project_kernel(const float4 *__restrict__ mean_op,
                                                       const float4 *__restrict__ scale,
                                                       const float4 *__restrict__ quat,
                                                       float4 *__restrict__ xy_depth,
