@@ -392,7 +392,9 @@ def main():
         alg = K * (4 + 16 + 16 + 8 + 16 + 16) + RES * RES * 36
         what = "p2e_render (compositing)"
     elif dom == "sort_bin":
-        alg = n * (4 + 8 + 4) + K * 12 + 6 * K * 24
+        # depth keys of the Gaussians and four passes over them, emission of
+        # the tile keys, two passes over those (12 B read + 12 B written each)
+        alg = n * (4 + 16 + 12) + 4 * n * 24 + n * 16 + K * 12 + 2 * K * 24
         what = "p2e_sort_bin"
     elif dom == "project":
         alg = n * (48 + 44)

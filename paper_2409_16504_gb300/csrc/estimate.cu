@@ -7,7 +7,8 @@
 //
 //   bbox      one reduction: bounding box and centroid of the cloud
 //   grid      uniform cells (about two cells per point at most), counting
-//             sort of the points by cell (count, scan, scatter)
+//             sort of the points by cell (count, scan, scatter into a
+//             cell-ordered copy)
 //   knn+pca   one thread per point, points taken in cell order (a
 //             cell-ordered copy of the points): exact 16 nearest other
 //             points (ties by index) by a two-pass threshold search of the
@@ -41,7 +42,6 @@ struct EstScratch {
     double *sum;          // 3
     GridParams *gp;
     uint32_t *cell;       // n
-    uint32_t *order;      // n
     uint32_t *counts;     // ncell_max
     uint32_t *start;      // ncell_max + 1
     uint64_t *scan_state; // scan tiles + 1
@@ -73,7 +73,6 @@ static size_t est_layout(int64_t n, void *base, EstScratch *S) {
     s.sum = (double *)take(3 * sizeof(double));
     s.gp = (GridParams *)take(sizeof(GridParams));
     s.cell = (uint32_t *)take((size_t)n * 4);
-    s.order = (uint32_t *)take((size_t)n * 4);
     s.counts = (uint32_t *)take((size_t)nc * 4);
     s.start = (uint32_t *)take((size_t)(nc + 1) * 4);
     s.scan_state = (uint64_t *)take((size_t)(st + 1) * 8);
@@ -313,7 +312,6 @@ __global__ void __launch_bounds__(256) scatter_kernel(const float4 *__restrict__
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t c = S.cell[i];
         const uint32_t q = S.start[c] + atomicSub(&S.counts[c], 1u) - 1u;  // the count runs down to 0
-        S.order[q] = (uint32_t)i;
         const float4 p = __ldg(xyz + i);
         S.spts[q] = make_float4(p.x, p.y, p.z, __uint_as_float((uint32_t)i));
     }
