@@ -173,12 +173,17 @@ p2e_status p2e_project(const p2e_gaussians *g, const p2e_camera *cams, int32_t n
 /* p2e_sort_bin -- duplication into (tile id | depth) keys, device radix sort
  * and per-tile ranges (Sec. 3.1: splats covering a pixel sorted by depth).
  * key = ((tile_base_v + ty * ceil(W_v/tile) + tx) << 32) | bits(depth key),
- * val = g, emitted in (view, Gaussian) order; the LSD radix sort is stable
- * and sorts only the 32 + ceil(log2(total tiles)) significant bits, so equal
- * keys keep ascending Gaussian order.  n = g->n used by p2e_project.
+ * val = g; the result is the keys in ascending order, equal keys in
+ * ascending Gaussian order (views in order).  When io->capacity >= n *
+ * n_views the Gaussians are first sorted by depth (stable LSD passes on
+ * the depth bits) and the keys, emitted in that order, are sorted stably
+ * on the tile bits only; otherwise the keys, emitted in (view, Gaussian)
+ * order, are sorted stably on all 32 + ceil(log2(total tiles)) significant
+ * bits.  Both give the same result.  n = g->n used by p2e_project.
  * Writes io->n_keys_dev, the sorted pair io->keys/vals[io->result] and
- * io->ranges.  If the key count exceeds io->capacity nothing is written past
- * it and p2e_bins_check reports P2E_ERR_CAPACITY. */
+ * io->ranges; the other key/value buffers are overwritten (scratch).  If
+ * the key count exceeds io->capacity nothing is written past it and
+ * p2e_bins_check reports P2E_ERR_CAPACITY. */
 p2e_status p2e_sort_bin(const p2e_projected *proj, int64_t n, const p2e_camera *cams,
                         int32_t n_views, const p2e_config *cfg, p2e_bins *io, void *stream);
 
