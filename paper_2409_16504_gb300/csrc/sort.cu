@@ -4,9 +4,10 @@
 // every tile's list comes out ordered by depth, ties by Gaussian index.
 //
 // Depth first (the key buffers hold at least one entry per Gaussian):
-//   depth_keys (keys and digit histograms) + 4 radix passes: the Gaussians
-//        sorted by depth (the 32 depth bits of (depth << 32 | index) keys,
-//        stable), into buffer 1;
+//   depth_min, depth_keys (keys and digit histograms) + 4 radix passes:
+//        the Gaussians sorted by depth (the 32 bits of (depth bits - the
+//        smallest) << 32 | index keys, stable; a pass whose digit is the
+//        same for every key is a copy), into buffer 1;
 //   scan_emit: single-pass exclusive scan of the tile counts in that order
 //        (decoupled look-back) fused with key emission, into buffer 0;
 //   1-2 radix passes on the tile bits only (stable), so each tile keeps the
@@ -50,6 +51,7 @@ struct SortScratch {
     uint32_t *hist;        // [kMaxPasses][256] digit totals
     uint32_t *tickets;     // [16]: [0] scan, [1 + p] sort pass p
     int64_t *n_depth;      // number of Gaussians in the depth sort
+    uint32_t *zmin_inv;    // ~(smallest depth bits of a Gaussian that covers a tile)
     uint64_t *scan_state;  // [scan tiles] look-back words (flag << 62 | value)
     uint32_t *sort_state;  // [kMaxPasses][sort tiles][256] (flag << 30 | count)
     int64_t scan_tiles, sort_tiles;
@@ -60,7 +62,7 @@ __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_
 size_t sort_scratch_bytes(int64_t n_total, int64_t capacity) {
     const int64_t st = (n_total + kScanTile - 1) / kScanTile;
     const int64_t kt = (capacity + kSortTile - 1) / kSortTile;
-    return align256(kMaxPasses * kRadix * 4) + align256(16 * 4) + align256(8) + align256((size_t)(st + 1) * 8) +
+    return align256(kMaxPasses * kRadix * 4) + align256(16 * 4) + align256(16) + align256((size_t)(st + 1) * 8) +
            align256((size_t)kMaxPasses * (size_t)(kt + 1) * kRadix * 4);
 }
 
@@ -74,7 +76,8 @@ static SortScratch carve(void *base, int64_t n_total, int64_t capacity) {
     s.tickets = (uint32_t *)p;
     p += align256(16 * 4);
     s.n_depth = (int64_t *)p;
-    p += align256(8);
+    s.zmin_inv = (uint32_t *)(p + 8);
+    p += align256(16);
     s.scan_state = (uint64_t *)p;
     p += align256((size_t)(s.scan_tiles + 1) * 8);
     s.sort_state = (uint32_t *)p;
@@ -219,14 +222,33 @@ __global__ void __launch_bounds__(kScanThreads) scan_emit_kernel(
     }
 }
 
-// Depth keys of all Gaussians (every view): (fp32 depth bits << 32 | e),
-// value e; a Gaussian that covers no tile sorts last.  The histograms of
-// the four depth bytes (the depth passes' digits) are counted on the way.
+// Smallest depth bits over the Gaussians that cover a tile (as a maximum of
+// the complements, so that the zeroed scratch is the identity).
+__global__ void __launch_bounds__(256) depth_min_kernel(const uint32_t *__restrict__ ntiles,
+                                                        const float4 *__restrict__ xy_depth, int64_t n_total,
+                                                        uint32_t *zmin_inv) {
+    uint32_t best = 0u;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_total;
+         e += (int64_t)gridDim.x * blockDim.x)
+        if (__ldg(ntiles + e)) best = max(best, ~__float_as_uint(__ldg(&xy_depth[e].z)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(zmin_inv, best);
+}
+
+// Depth keys of all Gaussians (every view): ((depth bits - smallest) << 32
+// | e), value e (positive fp32 depths order as their bits, so the offset
+// keeps the order and a narrow depth range leaves the top byte 0, a pass the
+// radix sort then skips); a Gaussian that covers no tile takes key 0 (it
+// emits nothing, so its place is irrelevant).  The histograms of the four
+// depth bytes (the depth passes' digits) are counted on the way.
 __global__ void __launch_bounds__(256) depth_keys_kernel(const uint32_t *__restrict__ ntiles,
                                                          const float4 *__restrict__ xy_depth, int64_t n_total,
                                                          uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                                                         int64_t *n_depth, uint32_t *__restrict__ hist) {
+                                                         int64_t *n_depth, const uint32_t *zmin_inv,
+                                                         uint32_t *__restrict__ hist) {
     __shared__ uint32_t sh[4 * kRadix];
+    const uint32_t zmin = ~*zmin_inv;
     for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) sh[i] = 0;
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) *n_depth = n_total;
@@ -234,9 +256,9 @@ __global__ void __launch_bounds__(256) depth_keys_kernel(const uint32_t *__restr
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n_total; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e = base + threadIdx.x;
         const bool valid = e < n_total;
-        uint32_t zb = 0xffffffffu;
+        uint32_t zb = 0u;
         if (valid) {
-            if (__ldg(ntiles + e)) zb = __float_as_uint(__ldg(&xy_depth[e].z));
+            if (__ldg(ntiles + e)) zb = __float_as_uint(__ldg(&xy_depth[e].z)) - zmin;
             keys[e] = ((uint64_t)zb << 32) | (uint64_t)e;
             vals[e] = (uint32_t)e;
         }
@@ -314,6 +336,15 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
     __syncthreads();
     const int64_t tile = sm.tile;
     if (tile >= ntiles) return;
+    if (__syncthreads_or(threadIdx.x < kRadix && (int64_t)hist[threadIdx.x] == K)) {
+        // every key has the same digit: the stable pass is the identity
+        const int64_t t0 = tile * kSortTile, t1 = min(K, t0 + kSortTile);
+        for (int64_t i = t0 + threadIdx.x; i < t1; i += kSortThreads) {
+            keys_out[i] = keys_in[i];
+            vals_out[i] = vals_in[i];
+        }
+        return;
+    }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
     const int64_t wbase = tile * kSortTile + (int64_t)wid * (32 * kSortItems);
@@ -491,8 +522,10 @@ cudaError_t launch_sort_bin(const p2e_projected *proj, const Views &P, p2e_bins 
         // keys, into buffer 1), emit the tile keys in that order, then sort
         // them stably by tile only
         const int tpasses = passes - 4;
+        depth_min_kernel<<<num_sms * 2, 256, 0, st>>>(proj->ntiles, (const float4 *)proj->xy_depth, n_total,
+                                                      S.zmin_inv);
         depth_keys_kernel<<<num_sms * 2, 256, 0, st>>>(proj->ntiles, (const float4 *)proj->xy_depth, n_total,
-                                                       io->keys[1], io->vals[1], S.n_depth, S.hist);
+                                                       io->keys[1], io->vals[1], S.n_depth, S.zmin_inv, S.hist);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const unsigned dgrid = (unsigned)((n_total + kSortTile - 1) / kSortTile);
         for (int p = 0; p < 4; ++p)
