@@ -10,7 +10,16 @@ Gaussians from the resident point cloud (kNN-PCA, or kNN-PCA + learned MLP)
 followed by projection, key emission + radix sort + tile ranges, and
 compositing.  Per step the L2 is flushed (a 256 MiB write) outside the
 timed interval; each step is timed with CUDA events on the launching
-stream.
+stream, and the dominant kernels inside it with CUDA events that the
+library records around their launches (p2e_set_kernel_probe).
+
+Besides the timed steps the line carries: the per-frame latency
+distribution over 1000 frames per path; the end-to-end latency of single
+frames through the public API (upload of the cloud from pinned memory,
+estimation, rendering, read-back of the images); the overlapped end-to-end
+throughput; a short serving run (Poisson viewpoint requests at 500/s
+against a moving cloud); and the rooflines of the kNN, compositing and MLP
+kernels.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
 on the host cores on a bounded sample of the same workload.
@@ -18,8 +27,9 @@ on the host cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import ctypes as C
+import hashlib
 import json
-import math
 import os
 import subprocess
 import sys
@@ -34,6 +44,48 @@ METRIC = "p50/p99 frame latency (ms) and Mpix/s at 1024², learned vs kNN-PCA pa
 N_POINTS = 800_000
 RES = 1024
 SEED = 2
+LATENCY_FRAMES = 1000
+E2E_LATENCY_FRAMES = 200
+
+# Algorithmic work per unit (the roofline numerators).
+#   kNN: per query ~27 grid cells x ~3 points x 16 B (a float4 per candidate)
+KNN_BYTES_PER_QUERY = 27 * 3 * 16
+#   MLP head: 2 (96*64 + 64*64*2 + 64*8) flop per point
+MLP_FLOP_PER_POINT = 2 * (96 * 64 + 64 * 64 * 2 + 64 * 8)
+#   compositing: per evaluated (pixel, splat) pair ~20 fp32 operations (the
+#   pixel offset 4, the conic form 8, exp + alpha 3, transmittance 2, the
+#   seven weighted sums and the weight 8 for a contributing splat) and one
+#   ex2 on the MUFU pipe; HBM: per key its index and gathered record
+#   (xy_depth, conic, rect, rgb, normal: 4 + 16 + 16 + 8 + 16 + 16 B) and
+#   per pixel the nine output planes
+BLEND_FP32_PER_PAIR = 20
+BLEND_BYTES_PER_KEY = 4 + 16 + 16 + 8 + 16 + 16
+BLEND_BYTES_PER_PIXEL = 9 * 4
+FP32_LANES_PER_SM = 128
+
+# DRAM bytes per launch from one ncu capture of the kernel (dram__bytes_read
+# + dram__bytes_write, profiles/), valid while the kernel's source file is
+# unchanged (its SHA-256 prefix below); otherwise the line reports null.
+NCU_TRAFFIC = {
+    "knn": {"kernel": "knn_pca_kernel", "source": "paper_2409_16504_gb300/csrc/estimate.cu",
+            "sha256_16": None, "bytes": None},
+    "blend": {"kernel": "blend_kernel<16>", "source": "paper_2409_16504_gb300/csrc/blend.cu",
+              "sha256_16": None, "bytes": None},
+    "mlp": {"kernel": "mlp_estimate_kernel", "source": "paper_2409_16504_gb300/csrc/mlp.cu",
+            "sha256_16": None, "bytes": None},
+}
+
+
+def source_digest(rel: str) -> str:
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic(which: str):
+    e = NCU_TRAFFIC[which]
+    if e["bytes"] is None or e["sha256_16"] != source_digest(e["source"]):
+        return None
+    return e["bytes"]
 
 
 def workload_name(path: str) -> str:
@@ -125,7 +177,11 @@ def measured_peaks():
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f), "measured"
     except (OSError, ValueError):
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def pct(a, q):
+    return float(np.percentile(np.asarray(a), q)) if len(a) else None
 
 
 def oracle_frame(xyz, rgb, g, cam, path):
@@ -191,6 +247,41 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+class Probe:
+    """CUDA events (and an optional device counter) that libp2e records
+    around one kernel's launches, one event pair per step."""
+
+    def __init__(self, kernel: int, steps: int, dev, count: bool = False):
+        import torch
+        from paper_2409_16504_gb300 import _lib
+        self.lib, self.kernel = _lib.load(), kernel
+        self.ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(steps)]
+        for a, b in self.ev:   # create the underlying events
+            a.record()
+            b.record()
+        torch.cuda.synchronize()
+        self.count = torch.zeros(1, dtype=torch.int64, device=dev) if count else None
+        self.armed = []
+
+    def arm(self, i: int):
+        from paper_2409_16504_gb300 import _lib
+        a, b = self.ev[i]
+        p = _lib.P2EKernelProbe(a.cuda_event, b.cuda_event,
+                                self.count.data_ptr() if self.count is not None else None)
+        _lib.check("p2e_set_kernel_probe", self.lib.p2e_set_kernel_probe(self.kernel, C.byref(p)))
+        self.armed.append(i)
+
+    def disarm(self):
+        self.lib.p2e_set_kernel_probe(self.kernel, None)
+
+    def mean_ms(self) -> float:
+        return float(np.mean([self.ev[i][0].elapsed_time(self.ev[i][1]) for i in self.armed]))
+
+    def per_step_count(self) -> float:
+        return float(self.count.item()) / max(len(self.armed), 1)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -199,6 +290,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--path", default=None, choices=["render", "pca", "learned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the timed steps (for profiler runs): no latency, end-to-end or serving runs")
     ap.add_argument("--tile", type=int, default=16, choices=[8, 16, 32])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -213,7 +307,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2409_16504_gb300 import GaussianSet, Images, Renderer
+    from paper_2409_16504_gb300 import GaussianSet, Images, Renderer, _lib, p2e_bins_check
     from paper_2409_16504_gb300.estimate import LEARNED, PCA, Estimator, cloud_tensors
     from paper_2409_16504_gb300.render import p2e_project, p2e_render, p2e_sort_bin
 
@@ -225,13 +319,14 @@ def main():
     mlp_blob = learned_weights(dev)
     paths = [args.path] if args.path else (["learned", "pca"] if mlp_blob is not None else ["pca"])
     xyz, rgb, g = make_inputs()
+    n = len(xyz)
     center = xyz.mean(0)
-    e_steps = max(3, min(args.steps, 50))
-    cams = cameras(center, args.warmup + max(args.steps, e_steps), SEED + 100 + rank)
+    n_lat = 0 if args.no_extras else LATENCY_FRAMES
+    cams = cameras(center, args.warmup + max(args.steps, n_lat, E2E_LATENCY_FRAMES), SEED + 100 + rank)
     cx, cc = cloud_tensors(xyz, rgb, dev)
     g_static = GaussianSet.from_numpy(g, dev)
-    est = Estimator(len(xyz), dev)
-    gs = GaussianSet.empty(len(xyz), dev)
+    est = Estimator(n, dev)
+    gs = GaussianSet.empty(n, dev)
     st = torch.cuda.current_stream()
     rend = Renderer({"tile": args.tile}, capacity=1 << 21, device=dev)
     est(cx, cc, out=gs)
@@ -261,6 +356,10 @@ def main():
         return es
 
     def timed(path):
+        """The K timed steps, with the kernel probes armed on every step."""
+        probes = {"knn": Probe(_lib.P2E_PROBE_KNN, args.steps, dev) if path != "render" else None,
+                  "mlp": Probe(_lib.P2E_PROBE_MLP, args.steps, dev) if path == "learned" else None,
+                  "blend": Probe(_lib.P2E_PROBE_BLEND, args.steps, dev, count=True)}
         for i in range(args.warmup):
             flush.fill_(i & 0xFF)
             frame(cams[i], path)
@@ -271,22 +370,44 @@ def main():
         recs = []
         for i in range(args.steps):
             flush.fill_(i & 0xFF)
+            for p in probes.values():
+                if p is not None:
+                    p.arm(i)
             recs.append(frame(cams[args.warmup + i], path))
+        for p in probes.values():
+            if p is not None:
+                p.disarm()
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         stage = np.array([[a.elapsed_time(b) for a, b in zip(r[:-1], r[1:])] for r in recs])
-        return stage
+        kern = {k: (p.mean_ms() if p is not None else None) for k, p in probes.items()}
+        pairs = probes["blend"].per_step_count()
+        return stage, kern, pairs
+
+    def latency(path, frames):
+        """Per-frame device latency (estimate + project + sort + blend) over
+        `frames` frames, L2 flushed before each, cameras re-drawn."""
+        for i in range(3):
+            frame(cams[i], path)
+        out = []
+        for i in range(frames):
+            flush.fill_(i & 0xFF)
+            es = frame(cams[i], path)
+            out.append(es)
+            if (i + 1) % 64 == 0:   # bound the work in flight; the host stays frames ahead
+                torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        return np.array([e[0].elapsed_time(e[-1]) for e in out])
 
     clk = Clocks(local)
     clk.start()
     results = {p: timed(p) for p in paths}
     clocks = clk.stop()
-    st_ok, k = 0, rend.n_keys
-    from paper_2409_16504_gb300 import p2e_bins_check
-    st_ok, k = p2e_bins_check(rend.bins)
+    st_ok, n_keys = p2e_bins_check(rend.bins)
     if st_ok != 0:
-        raise RuntimeError(f"binning status {st_ok}: key capacity {rend.capacity} < {k}")
+        raise RuntimeError(f"binning status {st_ok}: key capacity {rend.capacity} < {n_keys}")
+    assert n_keys > n // 2, n_keys  # the key count of the last frame, not a loop index
 
     def summary(stage):
         fm = stage.sum(1)
@@ -295,15 +416,101 @@ def main():
                     p50=float(np.percentile(fm, 50)), p99=float(np.percentile(fm, 99)),
                     stage={nm: float(x) for nm, x in zip(["estimate", "project", "sort_bin", "blend"],
                                                          stage.mean(0))})
-    sums = {p: summary(results[p]) for p in paths}
+    sums = {p: summary(results[p][0]) for p in paths}
     head_path = paths[0]
     hs = sums[head_path]
+    kern, pairs = results[head_path][1], results[head_path][2]
+    lat = {p: latency(p, n_lat) for p in paths} if n_lat else {}
 
-    # end to end through the public API: every frame's cloud is uploaded
-    # from pinned host memory and its rgb/normal/depth images are read back
-    # to pinned host memory.  Uploads, compute (estimation + rendering) and
-    # read-backs run on three streams, double-buffered, so that frame i+1's
-    # upload and frame i-1's read-back overlap frame i's compute.
+    # ---- kernel rooflines (achieved work per launch / CUDA-event duration)
+    peaks, src_peak = measured_peaks()
+    hbm = peaks["hbm_gbs"]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12   # TFLOP/s (one op per lane per clock)
+    rooflines = {}
+    if kern["knn"]:
+        alg = KNN_BYTES_PER_QUERY * n
+        a = alg / (kern["knn"] / 1e3) / 1e9
+        rooflines["knn"] = {"kernel": "knn_pca_kernel", "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
+                            "frac": a / hbm, "traffic": ncu_traffic("knn"), "ms": kern["knn"],
+                            "algorithmic_bytes_per_launch": alg, "peak_source": src_peak}
+    if kern["mlp"]:
+        alg = MLP_FLOP_PER_POINT * n
+        a = alg / (kern["mlp"] / 1e3) / 1e12
+        pk = peaks["bf16_tflops"]
+        rooflines["mlp"] = {"kernel": "mlp_estimate_kernel", "bound": "tensor", "achieved": a, "peak": pk,
+                            "unit": "TFLOP/s", "frac": a / pk, "traffic": ncu_traffic("mlp"), "ms": kern["mlp"],
+                            "algorithmic_flop_per_launch": alg, "peak_source": src_peak + " (bf16 burst)"}
+    if kern["blend"]:
+        a = BLEND_FP32_PER_PAIR * pairs / (kern["blend"] / 1e3) / 1e12
+        hb = (BLEND_BYTES_PER_KEY * n_keys + BLEND_BYTES_PER_PIXEL * RES * RES) / (kern["blend"] / 1e3) / 1e9
+        rooflines["blend"] = {"kernel": f"blend_kernel<{args.tile}>", "bound": "alu", "achieved": a,
+                              "peak": fp32_peak, "unit": "TFLOP/s", "frac": a / fp32_peak,
+                              "traffic": ncu_traffic("blend"), "ms": kern["blend"],
+                              "pairs_per_launch": pairs, "fp32_ops_per_pair": BLEND_FP32_PER_PAIR,
+                              "peak_derivation": f"{sms} SMs x {FP32_LANES_PER_SM} fp32 lanes x {sm_mhz:.0f} MHz",
+                              "hbm": {"achieved_gbs": hb, "frac": hb / hbm,
+                                      "algorithmic_bytes_per_launch": BLEND_BYTES_PER_KEY * n_keys +
+                                      BLEND_BYTES_PER_PIXEL * RES * RES}}
+    dom = max(rooflines, key=lambda k: rooflines[k]["ms"])
+
+    line = {"metric": METRIC, "value": hs["value"], "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": hs["ms"], "p50_ms": hs["p50"], "p99_ms": hs["p99"],
+            "stage_ms": hs["stage"], "kernel_ms": kern, "path": head_path,
+            "paths": {p: {"Mpix_s": v["value"], "p50_ms": v["p50"], "p99_ms": v["p99"], "stage_ms": v["stage"],
+                          "kernel_ms": results[p][1]} for p, v in sums.items()},
+            "keys_per_frame": n_keys, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(head_path), "points": N_POINTS, "resolution": RES,
+                       "cameras": "uniform on a 2.5 m sphere, re-drawn per frame",
+                       "l2": "flushed (256 MiB write) before every timed frame", "tile": args.tile,
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "clocks": clocks, "roofline": rooflines[dom], "rooflines": rooflines}
+    if lat:
+        line["latency"] = {p: {"frames": len(v), "p50_ms": pct(v, 50), "p99_ms": pct(v, 99),
+                               "max_ms": float(v.max()), "under_10ms": float((v < 10.0).mean())}
+                           for p, v in lat.items()}
+
+    # launches of our kernels per frame: estimate (init, bbox, grid, count,
+    # scan, scatter, kNN-PCA, listed queries [+ MLP]); project; sort_bin
+    # (depth min, depth keys, 4 depth passes, scan + emit, digit histogram,
+    # tile passes, ranges, work list); render (fill, item table, blend)
+    tbits = int(np.ceil(np.log2(max(2, (RES // args.tile) ** 2))))
+    tile_passes = (32 + tbits + 7) // 8 - 4
+    sort_launches = 2 + 4 + 1 + 1 + tile_passes + 2
+    per_frame = {"render": 1 + sort_launches + 3, "pca": 8 + 1 + sort_launches + 3,
+                 "learned": 9 + 1 + sort_launches + 3}
+    line["gpu_launches"] = sum(per_frame[p] for p in paths) * args.steps
+
+    if not args.no_extras:
+        line["e2e"] = e2e_runs(torch, dev, head_path, est, rend, mlp_blob, cx, cc, g_static, gs, cams, args, world)
+        line["beyond_frame"] = beyond_frame(torch, dev, est, cx, cc, gs, img, cams, flush, ev, st, hbm)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(head_path)
+    if rank == 0 and world == 1 and not args.no_serving and not args.no_extras:
+        from paper_2409_16504_gb300 import serve
+        torch.cuda.synchronize()
+        line["serving"] = serve.run_load(seconds=3.0, rate=500.0, learned=mlp_blob is not None)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def e2e_runs(torch, dev, head_path, est, rend, mlp_blob, cx, cc, g_static, gs, cams, args, world):
+    """End to end through the public API.  Every frame uploads its cloud
+    from pinned host memory and reads its rgb/normal/depth images back to
+    pinned host memory.
+      * throughput: uploads, compute (estimation + rendering) and read-backs
+        on three streams, double-buffered, so that frame i+1's upload and
+        frame i-1's read-back overlap frame i's compute;
+      * latency: single frames, one at a time: host clock from issuing the
+        upload to observing the read-back complete."""
+    from paper_2409_16504_gb300 import Images
+    from paper_2409_16504_gb300.estimate import LEARNED, PCA
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    e_steps = max(3, min(args.steps, 50))
     hx, hc = cx.cpu().pin_memory(), cc.cpu().pin_memory()
     outs = [torch.empty((7 * RES * RES,), dtype=torch.float32).pin_memory() for _ in range(2)]
     dxs, dcs = [torch.empty_like(cx) for _ in range(2)], [torch.empty_like(cc) for _ in range(2)]
@@ -316,31 +523,31 @@ def main():
     comp_done = [torch.cuda.Event() for _ in range(2)]
     down_done = [torch.cuda.Event() for _ in range(2)]
     torch.cuda.synchronize()
-    for k in range(2):  # start from recorded events
-        comp_done[k].record(kst)
-        down_done[k].record(dns)
+    for j in range(2):  # start from recorded events
+        comp_done[j].record(kst)
+        down_done[j].record(dns)
 
     def e2e_frame(i, cam):
-        k = i & 1
+        j = i & 1
         with torch.cuda.stream(cps):
-            cps.wait_event(comp_done[k])            # frame i-2 done reading dxs[k]
-            dxs[k].copy_(hx, non_blocking=True)
-            dcs[k].copy_(hc, non_blocking=True)
-            up_done[k].record(cps)
+            cps.wait_event(comp_done[j])            # frame i-2 done reading dxs[j]
+            dxs[j].copy_(hx, non_blocking=True)
+            dcs[j].copy_(hc, non_blocking=True)
+            up_done[j].record(cps)
         with torch.cuda.stream(kst):
-            kst.wait_event(up_done[k])
-            kst.wait_event(down_done[k])            # frame i-2's images read back
-            src = (est(dxs[k], dcs[k], mode=mode, mlp_blob=mlp_blob, out=gs, stream=kst)
+            kst.wait_event(up_done[j])
+            kst.wait_event(down_done[j])            # frame i-2's images read back
+            src = (est(dxs[j], dcs[j], mode=mode, mlp_blob=mlp_blob, out=gs, stream=kst)
                    if head_path != "render" else g_static)
-            rend.render(src, [cam], out=imgs[k], check=False, stream=kst)
-            comp_done[k].record(kst)
+            rend.render(src, [cam], out=imgs[j], check=False, stream=kst)
+            comp_done[j].record(kst)
         with torch.cuda.stream(dns):
-            dns.wait_event(comp_done[k])
-            o = outs[k]
-            o[: 3 * RES * RES].copy_(imgs[k].rgb, non_blocking=True)
-            o[3 * RES * RES: 6 * RES * RES].copy_(imgs[k].normal, non_blocking=True)
-            o[6 * RES * RES:].copy_(imgs[k].depth, non_blocking=True)
-            down_done[k].record(dns)
+            dns.wait_event(comp_done[j])
+            o = outs[j]
+            o[: 3 * RES * RES].copy_(imgs[j].rgb, non_blocking=True)
+            o[3 * RES * RES: 6 * RES * RES].copy_(imgs[j].normal, non_blocking=True)
+            o[6 * RES * RES:].copy_(imgs[j].depth, non_blocking=True)
+            down_done[j].record(dns)
 
     for w in range(4):
         e2e_frame(w, cams[w])
@@ -354,10 +561,46 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = a.elapsed_time(b) / e_steps
 
-    # the rows beyond the frame: relighting of the 1024^2 view from its normal
-    # image (HBM bound: 28 B read + 12 B written per pixel) and the global
-    # isotropic estimator (kNN-PCA + mean spacing), each timed alone
-    from paper_2409_16504_gb300 import relight
+    # single frames, one at a time, on one stream
+    lat_host, lat_dev = [], []
+    s = kst
+    for i in range(3 + E2E_LATENCY_FRAMES):
+        cam = cams[i]
+        x0, x1 = ev(), ev()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s):
+            x0.record(s)
+            dxs[0].copy_(hx, non_blocking=True)
+            dcs[0].copy_(hc, non_blocking=True)
+            src = (est(dxs[0], dcs[0], mode=mode, mlp_blob=mlp_blob, out=gs, stream=s)
+                   if head_path != "render" else g_static)
+            rend.render(src, [cam], out=imgs[0], check=False, stream=s)
+            o = outs[0]
+            o[: 3 * RES * RES].copy_(imgs[0].rgb, non_blocking=True)
+            o[3 * RES * RES: 6 * RES * RES].copy_(imgs[0].normal, non_blocking=True)
+            o[6 * RES * RES:].copy_(imgs[0].depth, non_blocking=True)
+            x1.record(s)
+        x1.synchronize()
+        t1 = time.perf_counter()
+        if i >= 3:
+            lat_host.append(1e3 * (t1 - t0))
+            lat_dev.append(x0.elapsed_time(x1))
+    return {"value": world * RES * RES / (e2e_ms / 1e3) / 1e6, "unit": "Mpix/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+            "overlap": "uploads, compute and read-backs on three streams, double-buffered",
+            "frame_latency": {"frames": len(lat_host), "p50_ms": pct(lat_host, 50), "p99_ms": pct(lat_host, 99),
+                              "max_ms": float(max(lat_host)), "device_p50_ms": pct(lat_dev, 50),
+                              "device_p99_ms": pct(lat_dev, 99),
+                              "what": "one frame at a time: host clock from issuing the H2D upload of the "
+                                      "cloud to the D2H read-back of rgb/normal/depth observed complete"}}
+
+
+def beyond_frame(torch, dev, est, cx, cc, gs, img, cams, flush, ev, st, hbm):
+    """The rows beyond the frame, each timed alone: relighting of the
+    1024^2 view from its normal image (28 B read + 12 B written per pixel),
+    the global isotropic estimator, the point raster."""
+    from paper_2409_16504_gb300 import Images, point_raster, relight
     lights = [(0.3, 0.8, -0.5, 0.9), (-1.0, 0.2, 0.1, 0.3)]
     shaded = torch.empty_like(img.rgb)
 
@@ -377,72 +620,10 @@ def main():
     relight_ms = timed_op(lambda: relight(img, lights, ambient=0.15, out=shaded))
     relight_gbs = RES * RES * 40 / (relight_ms / 1e3) / 1e9
     glob_ms = timed_op(lambda: est.global_(cx, cc, 1.5, out=gs))
-    from paper_2409_16504_gb300 import point_raster
     raster_img = Images([cams[0]], dev)
     raster_ms = timed_op(lambda: point_raster(cx, cc, [cams[0]], out=raster_img))
-
-    # roofline of the dominant stage (one C-ABI call, timed by CUDA events on
-    # its stream): algorithmic DRAM bytes per call / its mean duration
-    peaks, src_peak = measured_peaks()
-    dom = max(hs["stage"], key=hs["stage"].get)
-    K, n = k, len(xyz)
-    if dom == "blend":
-        # per key: its index and the splat record gathered (xy_depth, conic,
-        # rect, rgb, normal); per pixel the nine output planes
-        alg = K * (4 + 16 + 16 + 8 + 16 + 16) + RES * RES * 36
-        what = "p2e_render (compositing)"
-    elif dom == "sort_bin":
-        # depth keys of the Gaussians and four passes over them, emission of
-        # the tile keys, two passes over those (12 B read + 12 B written each)
-        alg = n * (4 + 16 + 12) + 4 * n * 24 + n * 16 + K * 12 + 2 * K * 24
-        what = "p2e_sort_bin"
-    elif dom == "project":
-        alg = n * (48 + 44)
-        what = "p2e_project"
-    else:
-        # kNN-PCA: points in (xyz, rgb), neighbour indices and Gaussians out;
-        # the learned head then reads the indices, the neighbours' points and
-        # the PCA Gaussians once and rewrites the Gaussians
-        alg = n * (32 + 64 + 80)
-        if head_path == "learned":
-            alg += n * (64 + 32 + 80 + 64)
-        what = "p2e_estimate (kNN-PCA" + (" + learned MLP)" if head_path == "learned" else ")")
-    achieved = alg / (hs["stage"][dom] / 1e3) / 1e9
-    roof = {"kernel": what, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-            "peak_source": src_peak, "algorithmic_bytes_per_launch": alg}
-
-    # launches per frame: estimate (init, bbox, grid, count, scan, scatter,
-    # kNN-PCA [+ MLP]); project 1; sort_bin (scan+emit, histogram, radix
-    # passes, ranges, work list); render (fill, item table, blend)
-    passes = (32 + int(math.ceil(math.log2(max(2, (RES // args.tile) ** 2)))) + 7) // 8
-    launches_sort = 4 + passes
-    launches_per_frame = {"render": 1 + launches_sort + 3, "pca": 7 + 1 + launches_sort + 3,
-                          "learned": 8 + 1 + launches_sort + 3}
-    line = {"metric": METRIC, "value": hs["value"], "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": hs["ms"], "p50_ms": hs["p50"], "p99_ms": hs["p99"],
-            "stage_ms": hs["stage"], "path": head_path,
-            "paths": {p: {"Mpix_s": v["value"], "p50_ms": v["p50"], "p99_ms": v["p99"], "stage_ms": v["stage"]}
-                      for p, v in sums.items()},
-            "keys_per_frame": K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_name(head_path), "points": N_POINTS, "resolution": RES,
-                       "cameras": "uniform on a 2.5 m sphere, re-drawn per frame",
-                       "l2": "flushed (256 MiB write) before every timed frame", "tile": args.tile,
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
-            "clocks": clocks, "gpu_launches": sum(launches_per_frame[p] for p in paths) * args.steps,
-            "e2e": {"value": world * RES * RES / (e2e_ms / 1e3) / 1e6, "unit": "Mpix/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "roofline": roof,
-            "beyond_frame": {"relight_1024": {"ms": relight_ms, "achieved_gbs": relight_gbs,
-                                              "frac_hbm": relight_gbs / peaks["hbm_gbs"]},
-                             "global_estimate_800k_ms": glob_ms, "point_raster_800k_1024_ms": raster_ms}}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(head_path)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    return {"relight_1024": {"ms": relight_ms, "achieved_gbs": relight_gbs, "frac_hbm": relight_gbs / hbm},
+            "global_estimate_800k_ms": glob_ms, "point_raster_800k_1024_ms": raster_ms}
 
 
 def learned_weights(dev):

@@ -199,6 +199,9 @@ p2e_status p2e_sort_bin(const p2e_projected *proj, int64_t n, const p2e_camera *
  * p2e_sort_bin and still belongs to the caller.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture.
+ * The address is kept for the life of the process, so this entry point
+ * must not be used on a device after cudaDeviceReset of that device (the
+ * reloaded module may place the array elsewhere).
  * Limits: n * n_views <= P2E_NOALLOC_MAX_N and io->capacity <=
  * P2E_NOALLOC_MAX_CAPACITY, otherwise P2E_ERR_INVALID_ARG is returned and
  * nothing is enqueued.  All calls share the one array (the call clears what
@@ -243,9 +246,12 @@ p2e_status p2e_render(const p2e_gaussians *g, const p2e_projected *proj, const p
 /* p2e_render_backward -- exact gradient of p2e_render's outputs with
  * respect to the Gaussian parameters (the differentiable splatting used to
  * train the estimator, Sec. 1 and 3.3), with the discrete decisions (cull,
- * rectangle, 3-sigma test, floor, stop) held fixed.  Per tile the
- * transmittance is recomputed back to front from the stored alpha image and
- * `last`; no per-pixel lists are stored.
+ * rectangle, 3-sigma test, floor, stop) held fixed.  Per tile and pixel
+ * the transmittance is recomputed from the tile's sorted list and `last`:
+ * front to back for the final T, then back to front through the
+ * contributing splats; no per-pixel lists are stored.  `alpha` (the
+ * forward's alpha image) is not read and may be NULL: recovering T as
+ * 1 - alpha would lose ~2.5e-4 relative accuracy on saturated pixels.
  * Inputs: the forward's arguments and outputs plus the upstream gradients
  * d_rgb[3][H][W], d_normal[3][H][W], d_depth[H][W], d_alpha[H][W] (any may
  * be NULL = zero).  Outputs (device, written, not accumulated; n entries):
@@ -325,7 +331,6 @@ p2e_status p2e_mlp_backward(const float *xyz, const float *rgb, int64_t n, const
 p2e_status p2e_adam(float *params, float *grad, float *m, float *v, int64_t count, float lr,
                     float beta1, float beta2, float eps, int32_t step, void *blob, void *stream);
 
-/* Human-readable name of a status code (static storage). */
 /* ---- the global isotropic baseline and relighting ------------------- */
 
 /* p2e_estimate_global -- the comparison estimator of Sec. 4.1 ("surface
@@ -371,6 +376,56 @@ p2e_status p2e_point_raster(const float *xyz, const float *rgb, int64_t n, const
                             int32_t n_views, const float *bg, uint64_t *zbuf, float *out_rgb, float *out_depth,
                             void *stream);
 
+/* ---- measurement and diagnostics (no counterpart in the paper) -------- */
+
+/* p2e_set_kernel_probe -- attaches measurement to the launches of one
+ * kernel made by the calling host thread, until it is called again with
+ * probe = NULL.  This is the one piece of state the library keeps between
+ * calls (thread-local, host memory only); with no probe set nothing is
+ * recorded.
+ *   kernel   P2E_PROBE_KNN     the kNN-PCA kernel of p2e_estimate (its fast
+ *                              path; the few listed queries run after it)
+ *            P2E_PROBE_BLEND   the compositing kernel of p2e_render
+ *            P2E_PROBE_MLP     the learned head of p2e_estimate (mode 1)
+ *   probe    start_event / stop_event: cudaEvent_t (or NULL) recorded on
+ *            the launching stream immediately before / after the kernel;
+ *            count_dev: device uint64 (or NULL) the kernel adds its work
+ *            count to (blend: the (pixel, splat) pairs it evaluated, every
+ *            pass included; ignored by the other kernels).
+ * The probe struct is copied; the events and counter stay caller-owned. */
+enum { P2E_PROBE_KNN = 0, P2E_PROBE_BLEND = 1, P2E_PROBE_MLP = 2, P2E_PROBE_COUNT = 3 };
+typedef struct {
+    void *start_event;
+    void *stop_event;
+    uint64_t *count_dev;
+} p2e_kernel_probe;
+p2e_status p2e_set_kernel_probe(int32_t kernel, const p2e_kernel_probe *probe);
+
+/* p2e_estimate_check -- synchronises `stream` and returns P2E_ERR_TIMEOUT if
+ * a bounded device wait of the last p2e_estimate / p2e_estimate_global
+ * call on this scratch gave up (its outputs are then invalid), else P2E_OK.
+ * n and scratch as passed to that call. */
+p2e_status p2e_estimate_check(const void *scratch, int64_t scratch_bytes, int64_t n, void *stream);
+
+/* p2e_selftest_timeout -- drives one of the library's bounded device waits
+ * to its limit, so that tests can check that the wait gives up, the kernel
+ * returns and the timeout is reported, without faulting or hanging the GPU.
+ *   which 0  a radix-sort pass of p2e_sort_bin whose first tile is never
+ *            published: the next tile's decoupled look-back gives up;
+ *         1  the cell-count scan of p2e_estimate, likewise;
+ *         2  the learned head's mbarrier wait for an MMA completion that is
+ *            never issued.
+ *   spin_limit  wait rounds before giving up, 1 .. 2^22 (the library's
+ *            own default limit is 2^22 rounds, a few hundred ms).
+ *   scratch  device, >= P2E_SELFTEST_SCRATCH_BYTES, 256-byte aligned.
+ *   status_dev  device int32: P2E_ERR_TIMEOUT once the wait gave up.
+ * Asynchronous on `stream`; read status_dev after synchronising (for
+ * example through p2e_bins_check with a p2e_bins whose status_dev it is). */
+#define P2E_SELFTEST_SCRATCH_BYTES (1 << 20)
+p2e_status p2e_selftest_timeout(int32_t which, uint32_t spin_limit, void *scratch, int64_t scratch_bytes,
+                                int32_t *status_dev, void *stream);
+
+/* Human-readable name of a status code (static storage). */
 const char *p2e_status_string(p2e_status s);
 
 #ifdef __cplusplus

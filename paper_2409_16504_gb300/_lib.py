@@ -23,7 +23,10 @@ P2E_SCRATCH_SORT, P2E_SCRATCH_ESTIMATE, P2E_SCRATCH_BACKWARD = 0, 1, 2
 EXPORTS = ("p2e_default_config", "p2e_total_tiles", "p2e_scratch_bytes", "p2e_project",
            "p2e_sort_bin", "p2e_sort_bin_noalloc", "p2e_bins_check", "p2e_render",
            "p2e_render_backward", "p2e_estimate", "p2e_loss_eq5", "p2e_mlp_backward", "p2e_adam",
-           "p2e_estimate_global", "p2e_relight", "p2e_point_raster", "p2e_status_string")
+           "p2e_estimate_global", "p2e_relight", "p2e_point_raster", "p2e_set_kernel_probe",
+           "p2e_estimate_check", "p2e_selftest_timeout", "p2e_status_string")
+P2E_PROBE_KNN, P2E_PROBE_BLEND, P2E_PROBE_MLP = 0, 1, 2
+SELFTEST_SCRATCH_BYTES = 1 << 20
 P2E_MAX_LIGHTS = 8
 MLP_PARAMS = 15568
 NOALLOC_MAX_N = 1 << 22
@@ -56,6 +59,10 @@ class P2EBins(C.Structure):
     _fields_ = [("keys", C.c_void_p * 2), ("vals", C.c_void_p * 2), ("ranges", C.c_void_p),
                 ("tile_work", C.c_void_p), ("scratch", C.c_void_p), ("scratch_bytes", C.c_int64), ("capacity", C.c_int64),
                 ("n_keys_dev", C.c_void_p), ("status_dev", C.c_void_p), ("result", C.c_int32)]
+
+
+class P2EKernelProbe(C.Structure):
+    _fields_ = [("start_event", C.c_void_p), ("stop_event", C.c_void_p), ("count_dev", C.c_void_p)]
 
 
 class P2EError(RuntimeError):
@@ -124,6 +131,12 @@ def load(path: str | None = None):
         lib.p2e_point_raster.restype = C.c_int
         lib.p2e_point_raster.argtypes = [vp, vp, i64, C.POINTER(P2ECamera), i32, C.POINTER(C.c_float), vp, vp, vp,
                                          vp]
+        lib.p2e_set_kernel_probe.restype = C.c_int
+        lib.p2e_set_kernel_probe.argtypes = [i32, C.POINTER(P2EKernelProbe)]
+        lib.p2e_estimate_check.restype = C.c_int
+        lib.p2e_estimate_check.argtypes = [vp, i64, i64, vp]
+        lib.p2e_selftest_timeout.restype = C.c_int
+        lib.p2e_selftest_timeout.argtypes = [i32, C.c_uint32, vp, i64, vp, vp]
         _lib = lib
         return lib
 

@@ -3,11 +3,15 @@
 // decision of the forward pass held fixed (differentiable splatting, used
 // to train the estimator end to end, Sec. 1 and 3.3).
 //
-// K7 (per tile, persistent over the non-empty-tile list): each pixel walks
-// its tile list back to front from the forward's `last`, re-deciding
-// contribution with the forward's exact arithmetic (splat.cuh).  The
-// transmittance is recovered backwards, T_k = T_{k+1} / (1 - alpha_k), from
-// the final T = 1 - alpha; no per-pixel lists are stored.  With
+// K7 (per tile, persistent over the non-empty-tile list): each pixel first
+// recomputes its final transmittance front to back over its tile list up to
+// the forward's `last` (the product of (1 - alpha_k) over the contributing
+// splats, re-decided with the forward's exact arithmetic, splat.cuh), then
+// walks the list back to front, recovering T_k = T_{k+1} / (1 - alpha_k).
+// No per-pixel lists are stored.  The final T is not taken from the alpha
+// image: near saturation (T ~ 1e-4) the fp32 round trip alpha = 1 - T,
+// T = 1 - alpha loses ~3e-8 absolute, a relative error of ~2.5e-4 that the
+// division chain would carry to every splat of the pixel.  With
 // f_k = gC.c_k + gN.n_k + gD z_k and the running tail
 //   S_k = sum_{j>k} alpha_j T_j f_j + T_final (gC.bg - gA),
 // dL/dalpha_k = T_k f_k - S_k / (1 - alpha_k).  Per-splat screen-space
@@ -87,14 +91,40 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
                 for (int c = 0; c < 3; ++c) up[3 + c] = d_nrm[3 * V.pix_base + c * HW + pix];
             if (d_depth) up[6] = d_depth[V.pix_base + pix];
             if (d_alpha) up[7] = d_alpha[V.pix_base + pix];
-            T = 1.f - alpha_img[V.pix_base + pix];
             lastp = last_img[V.pix_base + pix];
             if (lastp > r.y) lastp = r.y;  // only reachable with mismatched inputs
             atomicMax(&s_end, lastp);
         }
-        float acc = T * (up[0] * P.bg[0] + up[1] * P.bg[1] + up[2] * P.bg[2] - up[7]);
         __syncthreads();
         const uint32_t end = s_end;
+        // final transmittance, front to back over [r.x, lastp)
+        for (uint32_t bstart = r.x; bstart < end; bstart += BATCH) {
+            const int cnt = (int)min((uint32_t)BATCH, end - bstart);
+            if (tid < cnt) {
+                uint32_t g = __ldg(vals + bstart + tid);
+                if (g >= (uint32_t)P.n) g = 0;
+                s_off[tid] = splat_offset(__ldg(xy_depth + gbase + g), x0, y0);
+                s_co[tid] = __ldg(conic_op + gbase + g);
+            }
+            __syncthreads();
+            if (inside) {
+                const int jend = (int)min((uint32_t)cnt, lastp > bstart ? lastp - bstart : 0u);
+                for (int j = 0; j < jend; ++j) {
+                    const float4 o = s_off[j], co = s_co[j];
+                    float dx, dy;
+                    splat_delta(o, lxf, lyf, dx, dy);
+                    const float power = splat_power_d(co, dx, dy);
+                    if (power < pw_min) continue;
+                    float e;
+                    bool fr;
+                    const float alpha = splat_alpha(co.w, power, amax, e, fr);
+                    if (alpha < afloor) continue;
+                    T *= 1.f - alpha;
+                }
+            }
+            __syncthreads();
+        }
+        float acc = T * (up[0] * P.bg[0] + up[1] * P.bg[1] + up[2] * P.bg[2] - up[7]);
         for (uint32_t bend = end; bend > r.x; bend = (bend - r.x > (uint32_t)BATCH) ? bend - BATCH : r.x) {
             const uint32_t bstart = (bend - r.x > (uint32_t)BATCH) ? bend - BATCH : r.x;
             const int cnt = (int)(bend - bstart);

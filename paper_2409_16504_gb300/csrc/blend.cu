@@ -220,27 +220,45 @@ __device__ __forceinline__ uint32_t rect_bits(int rx0, int rx1, int ry0, int ry1
     return row * spread;
 }
 
+// Shared-memory staging of every warp of a CTA (declared at namespace
+// scope so that the out-of-line segment walk addresses it directly).
+__shared__ StageRec g_stage[kWarps];
+
+// What every segment walk of one (tile, pixel block) item shares.
+struct SegArgs {
+    const uint32_t *vals;
+    const float4 *xy_depth, *conic_op;
+    const ushort4 *rect;
+    const float4 *rgb, *normal;
+    int64_t gbase;
+    int x0, y0;
+    float lxf, lyf;
+    uint32_t n;
+    float pw_min, amax, afloor, tmin;
+};
+
 // Composites the nh staged splats of one buffer for the lane's pixel, in
 // list order.  kStop: the stop rule of the sequential recurrence;
-// otherwise a pure product from the given state.
+// otherwise a pure product from the given state.  `pairs` counts the
+// (pixel, splat) pairs evaluated.
 template <bool kStop>
-__device__ __forceinline__ void composite_chunk(const StageBuf &sb, int nh, int x0, int y0, float lxf, float lyf,
-                                                const Views &P, PixState &st) {
+__device__ __forceinline__ void composite_chunk(const StageBuf &sb, int nh, const SegArgs &a, PixState &st,
+                                                uint32_t &pairs) {
     if (st.done) return;
-    const float pw_min = -0.5f * P.sigma_mult * P.sigma_mult;
-    const float amax = P.alpha_max, afloor = P.alpha_floor, tmin = P.t_min;
-    for (int j = 0; j < nh; ++j) {
+    int j = 0;
+    for (; j < nh; ++j) {
         const float4 xy = sb.xy[j], co = sb.co[j];
-        const float4 o = splat_offset(xy, x0, y0);
-        const float power = splat_power(o, co, lxf, lyf);
-        if (power < pw_min) continue;
+        const float4 o = splat_offset(xy, a.x0, a.y0);
+        const float power = splat_power(o, co, a.lxf, a.lyf);
+        if (power < a.pw_min) continue;
         float e;
         bool fr;
-        const float alpha = splat_alpha(co.w, power, amax, e, fr);
-        if (alpha < afloor) continue;
+        const float alpha = splat_alpha(co.w, power, a.amax, e, fr);
+        if (alpha < a.afloor) continue;
         const float Tn = st.T * (1.f - alpha);
-        if (kStop && Tn < tmin) {
+        if (kStop && Tn < a.tmin) {
             st.done = true;
+            ++j;  // the stopping splat was evaluated too
             break;
         }
         const float wgt = alpha * st.T;
@@ -255,26 +273,30 @@ __device__ __forceinline__ void composite_chunk(const StageBuf &sb, int nh, int 
         st.T = Tn;
         st.last = sb.pos[j] + 1u;
     }
+    pairs += (uint32_t)j;
 }
 
 // Streams list positions [s0, s1) for the warp's block.  Every lane
 // screens four splats per step of 128 (independent loads; the next step's
 // indices are fetched one step ahead); the hits of each chunk of 32 are
 // copied (cp.async) into one of two stage buffers in list order while the
-// previous chunk is composited from the other.  With a poll flag, returns
-// early (the position reached, a multiple of 128 splats past s0) as soon as
-// the flag is set; otherwise returns s1.
-template <bool kStop>
-__device__ __forceinline__ uint32_t composite_segment(uint32_t s0, uint32_t s1, int64_t gbase, int x0, int y0,
-                                                      float lxf, float lyf, const uint32_t *__restrict__ vals,
-                                                      const float4 *__restrict__ xy_depth,
-                                                      const float4 *__restrict__ conic_op,
-                                                      const ushort4 *__restrict__ rect,
-                                                      const float4 *__restrict__ rgb,
-                                                      const float4 *__restrict__ normal, const Views &P,
-                                                      StageRec &sg, int lane, PixState &st,
-                                                      const uint32_t *poll = nullptr) {
+// previous chunk is composited from the other.  `stop`: the stop rule of
+// the sequential recurrence, else the pure product (an aggregate).  With a
+// poll flag, returns early (the position reached, a multiple of 128 splats
+// past s0) as soon as the flag is set; otherwise returns s1.
+//
+// Out of line: the kernel walks segments from several places (the exact
+// first segment, aggregates, catch-ups and re-walks); one copy of this loop
+// keeps the kernel's code within the instruction caches.  The state is
+// copied in and out once per call; the loop runs on registers.
+__device__ __noinline__ uint32_t composite_segment(bool stop, uint32_t s0, uint32_t s1, const SegArgs &args,
+                                                   PixState &state, uint32_t &pair_count, const uint32_t *poll) {
     constexpr int kAhead = 4;  // chunks of 32 screened per step
+    const SegArgs a = args;
+    PixState st = state;
+    uint32_t pairs = 0;
+    const int lane = threadIdx.x & 31;
+    StageRec &sg = g_stage[threadIdx.x >> 5];
     const uint32_t lt = (1u << lane) - 1u;
     int cur = 0;               // buffer the next chunk is copied into
     int pend = 0;              // splats staged in buffer cur ^ 1, not yet composited
@@ -283,8 +305,12 @@ __device__ __forceinline__ uint32_t composite_segment(uint32_t s0, uint32_t s1, 
 #pragma unroll
         for (int k = 0; k < kAhead; ++k) {
             const uint32_t idx = b + 32u * k + (uint32_t)lane;
-            g[k] = idx < s1 ? __ldg(vals + idx) : 0xffffffffu;
+            g[k] = idx < s1 ? __ldg(a.vals + idx) : 0xffffffffu;
         }
+    };
+    auto composite = [&](const StageBuf &sb, int nh) {
+        if (stop) composite_chunk<true>(sb, nh, a, st, pairs);
+        else composite_chunk<false>(sb, nh, a, st, pairs);
     };
     fetch(s0, gk);
     uint32_t reached = s1;
@@ -304,10 +330,10 @@ __device__ __forceinline__ uint32_t composite_segment(uint32_t s0, uint32_t s1, 
         for (int k = 0; k < kAhead; ++k) {
             hk[k] = false;
             if (gk[k] != 0xffffffffu) {
-                if (gk[k] >= (uint32_t)P.n) gk[k] = 0;  // only reachable with corrupted bins
-                const ushort4 rc = __ldg(rect + gbase + gk[k]);
-                const int rx0 = max(0, (int)rc.x - x0), rx1 = min(kBW - 1, (int)rc.z - x0);
-                const int ry0 = max(0, (int)rc.y - y0), ry1 = min(kBH - 1, (int)rc.w - y0);
+                if (gk[k] >= a.n) gk[k] = 0;  // only reachable with corrupted bins
+                const ushort4 rc = __ldg(a.rect + a.gbase + gk[k]);
+                const int rx0 = max(0, (int)rc.x - a.x0), rx1 = min(kBW - 1, (int)rc.z - a.x0);
+                const int ry0 = max(0, (int)rc.y - a.y0), ry1 = min(kBH - 1, (int)rc.w - a.y0);
                 if (rx0 <= rx1 && ry0 <= ry1) hk[k] = (rect_bits(rx0, rx1, ry0, ry1) & live) != 0u;
             }
         }
@@ -323,17 +349,17 @@ __device__ __forceinline__ uint32_t composite_segment(uint32_t s0, uint32_t s1, 
             if (hk[k]) {
                 const int q = __popc(hits & lt);
                 const uint32_t g = gcur[k];
-                cp_async16(&sb.xy[q], xy_depth + gbase + g);
-                cp_async16(&sb.co[q], conic_op + gbase + g);
-                cp_async16(&sb.cc[q], rgb + g);
-                cp_async16(&sb.nr[q], normal + g);
+                cp_async16(&sb.xy[q], a.xy_depth + a.gbase + g);
+                cp_async16(&sb.co[q], a.conic_op + a.gbase + g);
+                cp_async16(&sb.cc[q], a.rgb + g);
+                cp_async16(&sb.nr[q], a.normal + g);
                 sb.pos[q] = base + 32u * k + (uint32_t)lane;
             }
             cp_async_commit();
             if (pend) {
                 cp_async_wait_all_but_one();
                 __syncwarp();
-                composite_chunk<kStop>(sg.b[cur ^ 1], pend, x0, y0, lxf, lyf, P, st);
+                composite(sg.b[cur ^ 1], pend);
                 __syncwarp();  // buffer cur ^ 1 is free again
             }
             pend = __popc(hits);
@@ -343,9 +369,11 @@ __device__ __forceinline__ uint32_t composite_segment(uint32_t s0, uint32_t s1, 
     if (pend) {
         cp_async_wait_all();
         __syncwarp();
-        composite_chunk<kStop>(sg.b[cur ^ 1], pend, x0, y0, lxf, lyf, P, st);
+        composite(sg.b[cur ^ 1], pend);
         __syncwarp();
     }
+    state = st;
+    pair_count += pairs;
     return reached;
 }
 
@@ -393,21 +421,16 @@ __device__ __forceinline__ uint32_t arrive(uint32_t *counter, int lane) {
 // re-walked from the true state with the stop rule.  An aggregate with
 // T = 0 marks a pixel whose stop is already known to fall inside.
 __device__ __forceinline__ void combine(PixState &cur, const PixState &ag, uint32_t s0, uint32_t s1,
-                                        int64_t gbase, int x0, int y0, float lxf, float lyf,
-                                        const uint32_t *__restrict__ vals, const float4 *__restrict__ xy_depth,
-                                        const float4 *__restrict__ conic_op, const ushort4 *__restrict__ rect,
-                                        const float4 *__restrict__ rgb, const float4 *__restrict__ normal,
-                                        const Views &P, StageRec &sg, int lane) {
+                                        const SegArgs &a, uint32_t &pairs) {
     bool rw = false;
     if (!cur.done) {
-        if (cur.T * ag.T >= P.t_min) cur = fold(cur, ag);
+        if (cur.T * ag.T >= a.tmin) cur = fold(cur, ag);
         else rw = true;
     }
     if (__any_sync(0xffffffffu, rw)) {
         PixState x = cur;
         x.done = !rw;  // only the re-walking pixels take part
-        composite_segment<true>(s0, s1, gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect, rgb, normal, P,
-                                sg, lane, x);
+        composite_segment(true, s0, s1, a, x, pairs, nullptr);
         if (rw) cur = x;
     }
 }
@@ -419,12 +442,10 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
     const float4 *__restrict__ xy_depth, const float4 *__restrict__ conic_op, const ushort4 *__restrict__ rect,
     const float4 *__restrict__ rgb, const float4 *__restrict__ normal, float *__restrict__ out_rgb,
     float *__restrict__ out_nrm, float *__restrict__ out_depth, float *__restrict__ out_alpha,
-    uint32_t *__restrict__ out_last, __grid_constant__ const Views P) {
+    uint32_t *__restrict__ out_last, unsigned long long *__restrict__ pair_count, __grid_constant__ const Views P) {
     constexpr int NBX = BT / kBW, NB = blocks_of(BT);
     constexpr int SW = kStateWords * 32;  // state floats of one (segment, block)
-    __shared__ StageRec stage[kWarps];
     const int lane = threadIdx.x & 31;
-    StageRec &sg = stage[threadIdx.x >> 5];
     const int lx = lane % kBW, ly = lane / kBW;
     const float lxf = (float)lx, lyf = (float)ly;
     const float tmin = P.t_min;
@@ -440,6 +461,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
     float *states = (float *)store;
     uint32_t *counters = chained ? (uint32_t *)(store + (size_t)total_segs * NB * kStateBytes) : nullptr;
     uint32_t *ready = chained ? counters + (size_t)total_segs * NB : nullptr;
+    uint32_t pairs = 0;  // (pixel, splat) pairs this lane evaluated
 
     for (;;) {
         uint32_t item = 0;
@@ -473,6 +495,23 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
         const uint2 r = ranges[tile];
         const int64_t gbase = (int64_t)vi * P.n;
         const uint32_t nseg = (r.y - r.x + S - 1) / S;
+        SegArgs sa;
+        sa.vals = vals;
+        sa.xy_depth = xy_depth;
+        sa.conic_op = conic_op;
+        sa.rect = rect;
+        sa.rgb = rgb;
+        sa.normal = normal;
+        sa.gbase = gbase;
+        sa.x0 = x0;
+        sa.y0 = y0;
+        sa.lxf = lxf;
+        sa.lyf = lyf;
+        sa.n = (uint32_t)P.n;
+        sa.pw_min = -0.5f * P.sigma_mult * P.sigma_mult;
+        sa.amax = P.alpha_max;
+        sa.afloor = P.alpha_floor;
+        sa.tmin = P.t_min;
         auto seg_lo = [&](uint32_t si) { return r.x + si * S; };
         auto seg_hi = [&](uint32_t si) { return min(r.y, r.x + (si + 1) * S); };
         // (segment, block) index of the chain's bookkeeping
@@ -484,21 +523,17 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
         if (!chained) {
             // the chain in one warp: segment 0 exact, every later one
             // speculated from T = 1 and combined, as the chained schedule does
-            composite_segment<true>(seg_lo(0), seg_hi(0), gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect,
-                                    rgb, normal, P, sg, lane, cur);
+            composite_segment(true, seg_lo(0), seg_hi(0), sa, cur, pairs, nullptr);
             for (m = 1; m < nseg; ++m) {
                 PixState ag;
                 fresh_state(ag, inside);
                 ag.done = ag.done || cur.done;
-                composite_segment<false>(seg_lo(m), seg_hi(m), gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op,
-                                         rect, rgb, normal, P, sg, lane, ag);
-                combine(cur, ag, seg_lo(m), seg_hi(m), gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect, rgb,
-                        normal, P, sg, lane);
+                composite_segment(false, seg_lo(m), seg_hi(m), sa, ag, pairs, nullptr);
+                combine(cur, ag, seg_lo(m), seg_hi(m), sa, pairs);
             }
             m = nseg - 1;
         } else if (seg == 0) {
-            composite_segment<true>(seg_lo(0), seg_hi(0), gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect,
-                                    rgb, normal, P, sg, lane, cur);
+            composite_segment(true, seg_lo(0), seg_hi(0), sa, cur, pairs, nullptr);
         } else {
             // speculate: the segment from T = 1 without stopping (its aggregate)
             const size_t pi = sidx(seg - 1);
@@ -514,16 +549,13 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
             fresh_state(ag, inside);
             if (known) ag.done = ag.done || pr.done;
             const uint32_t s0 = seg_lo(seg), s1 = seg_hi(seg);
-            const uint32_t reached = composite_segment<false>(s0, s1, gbase, x0, y0, lxf, lyf, vals, xy_depth,
-                                                              conic_op, rect, rgb, normal, P, sg, lane, ag,
-                                                              known ? nullptr : ready + pi);
+            const uint32_t reached = composite_segment(false, s0, s1, sa, ag, pairs, known ? nullptr : ready + pi);
             if (!known && reached < s1) {
                 (void)ld_acquire_u32(ready + pi);
                 load_state(states + pi * SW, lane, pr);
                 rewalk = !pr.done && !ag.done && pr.T * ag.T < tmin;
                 ag.done = ag.done || pr.done || rewalk;
-                composite_segment<false>(reached, s1, gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect, rgb,
-                                         normal, P, sg, lane, ag);
+                composite_segment(false, reached, s1, sa, ag, pairs, nullptr);
             }
             if (rewalk) ag.T = 0.f;
             const size_t si = sidx(seg);
@@ -532,8 +564,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
             // inclusive state) continues the chain
             if (arrive(counters + si, lane) == 0u) continue;
             load_state(states + pi * SW, lane, cur);  // the predecessor's inclusive state
-            combine(cur, ag, s0, s1, gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect, rgb, normal, P, sg,
-                    lane);
+            combine(cur, ag, s0, s1, sa, pairs);
         }
         // publish the chain forward: while the successor's aggregate is
         // already stored, combine it too
@@ -548,8 +579,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
             PixState ag;
             load_state(states + ni * SW, lane, ag);
             ++m;
-            combine(cur, ag, seg_lo(m), seg_hi(m), gbase, x0, y0, lxf, lyf, vals, xy_depth, conic_op, rect, rgb,
-                    normal, P, sg, lane);
+            combine(cur, ag, seg_lo(m), seg_hi(m), sa, pairs);
         }
         if (m + 1 == nseg && inside) {  // the last segment's inclusive state is the pixel
             const int64_t HW = (int64_t)V.H * V.W;
@@ -570,6 +600,12 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
             if (out_alpha) out_alpha[V.pix_base + p] = 1.f - cur.T;
             if (out_last) out_last[V.pix_base + p] = cur.last;
         }
+    }
+    if (pair_count) {  // one atomic per warp (every lane reaches here)
+        unsigned long long t = pairs;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0 && t) atomicAdd(pair_count, t);
     }
 }
 
@@ -646,10 +682,14 @@ static cudaError_t launch_blend(const p2e_gaussians *g, const p2e_projected *pro
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int64_t grid = (int64_t)sms * per_sm[slot];
+    const p2e_kernel_probe *pr = kernel_probe(P2E_PROBE_BLEND);
+    probe_start(pr, st);
     blend_kernel<BT><<<(unsigned)grid, kWarps * 32, 0, st>>>(
         (const uint2 *)bins->ranges, bins->vals[bins->result], bins->tile_work, bins->tile_work + 1, table, store,
         (const float4 *)proj->xy_depth, (const float4 *)proj->conic_op, (const ushort4 *)proj->rect,
-        (const float4 *)g->rgb, (const float4 *)g->normal, rgb, nrm, depth, alpha, last, P);
+        (const float4 *)g->rgb, (const float4 *)g->normal, rgb, nrm, depth, alpha, last,
+        pr ? (unsigned long long *)pr->count_dev : nullptr, P);
+    probe_stop(pr, st);
     return cudaGetLastError();
 }
 

@@ -29,6 +29,23 @@ cudaError_t launch_estimate(const float *xyz, const float *rgb, int64_t n, int32
                             const void *mlp, float pca_opacity, p2e_gaussians *out,
                             uint32_t *knn_idx, void *scratch, int num_sms, cudaStream_t st);
 
+cudaError_t estimate_status(const void *scratch, int64_t n, cudaStream_t st, int32_t *out);
+size_t selftest_sort_bytes();
+size_t selftest_scan_bytes();
+cudaError_t launch_selftest_sort(void *scratch, int32_t *status, uint32_t spin_limit, cudaStream_t st);
+cudaError_t launch_selftest_scan(void *scratch, int32_t *status, uint32_t spin_limit, cudaStream_t st);
+cudaError_t launch_selftest_mbar(int32_t *status, uint32_t spin_limit, cudaStream_t st);
+
+// Probes are per host thread: a thread measuring its launches does not
+// disturb launches from other threads.
+static thread_local p2e_kernel_probe t_probe[P2E_PROBE_COUNT];
+static thread_local bool t_probe_on[P2E_PROBE_COUNT];
+
+const p2e_kernel_probe *kernel_probe(int kernel) {
+    if (kernel < 0 || kernel >= P2E_PROBE_COUNT || !t_probe_on[kernel]) return nullptr;
+    return &t_probe[kernel];
+}
+
 int device_sms() {
     static int cache[64] = {0};
     int dev = 0;
@@ -168,10 +185,10 @@ p2e_status p2e_project(const p2e_gaussians *g, const p2e_camera *cams, int32_t n
 
 p2e_status p2e_sort_bin(const p2e_projected *proj, int64_t n, const p2e_camera *cams, int32_t n_views,
                         const p2e_config *cfg, p2e_bins *io, void *stream) {
+    if (n < 0 || n >= (int64_t(1) << 31) || !io) return P2E_ERR_INVALID_ARG;
     Views P;
     p2e_status s = fill_views(cams, n_views, cfg, n, P);
     if (s != P2E_OK) return s;
-    if (n < 0 || n >= (int64_t(1) << 31) || !io) return P2E_ERR_INVALID_ARG;
     if (n > 0 && (s = check_proj(proj)) != P2E_OK) return s;
     if (io->capacity < 0 || io->capacity >= (int64_t(1) << 30)) return P2E_ERR_INVALID_ARG;
     if (!io->ranges || !io->tile_work || !io->n_keys_dev || !io->status_dev || !io->scratch)
@@ -229,7 +246,7 @@ p2e_status p2e_render_backward(const p2e_gaussians *g, const p2e_projected *proj
     if ((s = fill_views(cams, n_views, cfg, g->n, P)) != P2E_OK) return s;
     if (g->n > 0 && (s = check_proj(proj)) != P2E_OK) return s;
     if (!bins || !bins->ranges || (bins->result != 0 && bins->result != 1)) return P2E_ERR_INVALID_ARG;
-    if (!alpha || !last) return P2E_ERR_INVALID_ARG;
+    if (!last) return P2E_ERR_INVALID_ARG;
     if (g->n > 0 && (!d_mean || !d_scale || !d_quat || !d_opacity || !d_rgb_g || !d_normal_g))
         return P2E_ERR_INVALID_ARG;
     if (scratch_bytes < (int64_t)backward_scratch_bytes(g->n * n_views) ||
@@ -285,6 +302,40 @@ p2e_status p2e_estimate_global(const float *xyz, const float *rgb, int64_t n, fl
     return e == cudaSuccess ? P2E_OK : P2E_ERR_CUDA;
 }
 
+p2e_status p2e_set_kernel_probe(int32_t kernel, const p2e_kernel_probe *probe) {
+    if (kernel < 0 || kernel >= P2E_PROBE_COUNT) return P2E_ERR_INVALID_ARG;
+    if (probe) {
+        t_probe[kernel] = *probe;
+        t_probe_on[kernel] = true;
+    } else {
+        t_probe_on[kernel] = false;
+    }
+    return P2E_OK;
+}
+
+p2e_status p2e_estimate_check(const void *scratch, int64_t scratch_bytes, int64_t n, void *stream) {
+    if (n < 17 || n >= (int64_t(1) << 31) || !scratch || ((uintptr_t)scratch & 255u) ||
+        scratch_bytes < (int64_t)estimate_scratch_bytes(n))
+        return P2E_ERR_INVALID_ARG;
+    int32_t st = 0;
+    if (estimate_status(scratch, n, (cudaStream_t)stream, &st) != cudaSuccess) return P2E_ERR_CUDA;
+    return st != 0 ? (p2e_status)st : P2E_OK;
+}
+
+p2e_status p2e_selftest_timeout(int32_t which, uint32_t spin_limit, void *scratch, int64_t scratch_bytes,
+                                int32_t *status_dev, void *stream) {
+    if (which < 0 || which > 2 || spin_limit < 1 || spin_limit > kSpinLimit || !status_dev || !scratch ||
+        ((uintptr_t)scratch & 255u) || ((uintptr_t)status_dev & 3u) || scratch_bytes < P2E_SELFTEST_SCRATCH_BYTES)
+        return P2E_ERR_INVALID_ARG;
+    if (selftest_sort_bytes() > P2E_SELFTEST_SCRATCH_BYTES || selftest_scan_bytes() > P2E_SELFTEST_SCRATCH_BYTES)
+        return P2E_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = which == 0   ? launch_selftest_sort(scratch, status_dev, spin_limit, st)
+                    : which == 1 ? launch_selftest_scan(scratch, status_dev, spin_limit, st)
+                                 : launch_selftest_mbar(status_dev, spin_limit, st);
+    return e == cudaSuccess ? P2E_OK : P2E_ERR_CUDA;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
@@ -302,7 +353,8 @@ static void *g_noalloc_addr[64];  // device address of the array, per device, 0 
 extern "C" p2e_status p2e_sort_bin_noalloc(const p2e_projected *proj, int64_t n, const p2e_camera *cams,
                                            int32_t n_views, const p2e_config *cfg, p2e_bins *io,
                                            void *stream) {
-    if (!io || n < 0 || n_views < 1 || n_views > P2E_MAX_VIEWS) return P2E_ERR_INVALID_ARG;
+    // n is bounded before it is multiplied by the view count
+    if (!io || n < 0 || n > P2E_NOALLOC_MAX_N || n_views < 1 || n_views > P2E_MAX_VIEWS) return P2E_ERR_INVALID_ARG;
     if (n * n_views > P2E_NOALLOC_MAX_N || io->capacity > P2E_NOALLOC_MAX_CAPACITY || io->capacity < 0)
         return P2E_ERR_INVALID_ARG;
     if (sort_scratch_bytes(n * n_views, io->capacity) > kNoallocScratchBytes) return P2E_ERR_INVALID_ARG;

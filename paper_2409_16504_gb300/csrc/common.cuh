@@ -64,6 +64,18 @@ __device__ __forceinline__ int view_of_tile(const Views &P, int64_t tile) {
     return v;
 }
 
+// Measurement probe of one kernel (p2e_set_kernel_probe), or nullptr when
+// the calling host thread has none set for it.
+const p2e_kernel_probe *kernel_probe(int kernel);
+
+// Events of a probe around one launch, recorded on the launching stream.
+inline void probe_start(const p2e_kernel_probe *pr, cudaStream_t st) {
+    if (pr && pr->start_event) cudaEventRecord((cudaEvent_t)pr->start_event, st);
+}
+inline void probe_stop(const p2e_kernel_probe *pr, cudaStream_t st) {
+    if (pr && pr->stop_event) cudaEventRecord((cudaEvent_t)pr->stop_event, st);
+}
+
 }  // namespace p2e
 
 #define P2E_CUDA_CHECK_LAUNCH()                                  \

@@ -21,6 +21,8 @@
 //             (normal = smallest axis turned away from the centroid, first
 //             axis with its largest component positive, e2 = e3 x e1) ->
 //             quaternion (Shepperd).
+#include <string.h>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -49,14 +51,12 @@ struct EstScratch {
     float4 *spts;         // n points in cell order, .w = bits of the original index
     float4 *pk;           // 2n: point i's position and colour in one 32-byte record (learned path)
     uint32_t *knn;        // n * 16 (when the caller passes none)
-    void *mlp_scratch;    // see mlp.cu
     int64_t ncell_max, scan_tiles;
 };
 
 __host__ __device__ inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 static int64_t ncell_cap(int64_t n) { return std::max<int64_t>(2 * n, 1 << 16); }
 constexpr int kScanT = 4096;
-size_t mlp_scratch_bytes(int64_t n);
 
 static size_t est_layout(int64_t n, void *base, EstScratch *S) {
     const int64_t nc = ncell_cap(n);
@@ -80,7 +80,6 @@ static size_t est_layout(int64_t n, void *base, EstScratch *S) {
     s.spts = (float4 *)take((size_t)n * 16);
     s.knn = (uint32_t *)take((size_t)n * kK * 4);
     s.pk = (float4 *)take((size_t)n * 32);
-    s.mlp_scratch = take(mlp_scratch_bytes(n));
     s.ncell_max = nc;
     s.scan_tiles = st;
     if (S) *S = s;
@@ -214,7 +213,7 @@ __device__ __forceinline__ void st_rel64(uint64_t *p, uint64_t v) {
 // thread), the look-back by one warp over 32 predecessors at a time.
 __global__ void __launch_bounds__(256) scan_counts_kernel(const uint32_t *__restrict__ counts, int64_t len,
                                                           uint32_t *__restrict__ start, EstScratch S,
-                                                          int32_t *status) {
+                                                          int32_t *status, uint32_t spin_limit) {
     __shared__ uint32_t s_tile;
     __shared__ uint32_t s_w[8];
     __shared__ uint64_t s_prefix;
@@ -268,7 +267,7 @@ __global__ void __launch_bounds__(256) scan_counts_kernel(const uint32_t *__rest
                 const int first = pre ? __ffs(pre) - 1 : 32;  // nearest inclusive prefix
                 const unsigned need = first >= 31 ? 0xffffffffu : ((2u << first) - 1u);
                 if (notready & need) {
-                    if (++spins > kSpinLimit) {
+                    if (++spins > spin_limit) {
                         if (lane == 0) atomicExch(status, (int32_t)P2E_ERR_TIMEOUT);
                         break;
                     }
@@ -456,17 +455,22 @@ __device__ __forceinline__ void pca_out(const GridParams &g, const float4 &p, ui
                                         float4 *__restrict__ mean_op, float4 *__restrict__ scale,
                                         float4 *__restrict__ quat, float4 *__restrict__ rgb_out,
                                         float4 *__restrict__ normal) {
+    // The covariance is shift invariant; it is accumulated on the offsets
+    // p_j - p_i, which are exact (or nearly: the coordinates of near
+    // neighbours agree in sign and exponent), so that the centroid's rounding
+    // is relative to the neighbourhood's size, not to the coordinates'
+    // magnitude (a 1 mm neighbourhood at 1 m would lose ~4 digits).
     float m[3] = {0, 0, 0};
     for (int k = 0; k < kK; ++k) {
         const float4 qk = nb(k);
         if (knn_out) knn_out[(int64_t)i * kK + k] = __float_as_uint(qk.w);
-        m[0] += qk.x; m[1] += qk.y; m[2] += qk.z;
+        m[0] += qk.x - p.x; m[1] += qk.y - p.y; m[2] += qk.z - p.z;
     }
     for (int k = 0; k < 3; ++k) m[k] *= (1.f / kK);
     float C[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     for (int k = 0; k < kK; ++k) {
         const float4 qk = nb(k);  // second pass, from L1
-        const float d[3] = {qk.x - m[0], qk.y - m[1], qk.z - m[2]};
+        const float d[3] = {(qk.x - p.x) - m[0], (qk.y - p.y) - m[1], (qk.z - p.z) - m[2]};
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -808,7 +812,7 @@ __global__ void est_init_kernel(EstScratch S) {
 }
 
 cudaError_t launch_mlp_estimate(const float4 *pk, int64_t n, const void *mlp,
-                                const uint32_t *knn, p2e_gaussians *out, void *scratch, int num_sms,
+                                const uint32_t *knn, p2e_gaussians *out, int32_t *status, int num_sms,
                                 cudaStream_t st);
 
 cudaError_t launch_estimate(const float *xyz, const float *rgb, int64_t n, int32_t mode,
@@ -822,25 +826,74 @@ cudaError_t launch_estimate(const float *xyz, const float *rgb, int64_t n, int32
     if ((e = cudaMemsetAsync(S.counts, 0, (size_t)S.ncell_max * 4, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(S.scan_state, 0, (size_t)(S.scan_tiles + 1) * 8, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(S.ticket, 0, 64, st)) != cudaSuccess) return e;
+    // status words (zeroed with the tickets): [8] the cell-count scan's
+    // look-back, [9] the learned head's mbarrier waits
     int32_t *status = (int32_t *)(S.ticket + 8);
     const int g1 = num_sms * 4;
     bbox_kernel<<<num_sms * 2, 256, 0, st>>>((const float4 *)xyz, n, S);
     grid_setup_kernel<<<1, 1, 0, st>>>(n, S);
     cell_count_kernel<<<g1, 256, 0, st>>>((const float4 *)xyz, mode == 1 ? (const float4 *)rgb : nullptr, n, S);
-    scan_counts_kernel<<<(unsigned)S.scan_tiles, 256, 0, st>>>(S.counts, S.ncell_max, S.start, S, status);
+    scan_counts_kernel<<<(unsigned)S.scan_tiles, 256, 0, st>>>(S.counts, S.ncell_max, S.start, S, status,
+                                                               kSpinLimit);
     scatter_kernel<<<g1, 256, 0, st>>>((const float4 *)xyz, n, S);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     uint32_t *knn = knn_idx ? knn_idx : S.knn;
+    const p2e_kernel_probe *pr = kernel_probe(P2E_PROBE_KNN);
+    probe_start(pr, st);
     knn_pca_kernel<<<(unsigned)((n + kKnnThreads - 1) / kKnnThreads), kKnnThreads, 0, st>>>(
         (const float4 *)xyz, (const float4 *)rgb, n, pca_opacity, S, knn, (float4 *)out->mean_op,
         (float4 *)out->scale, (float4 *)out->quat, (float4 *)out->rgb, (float4 *)out->normal);
+    probe_stop(pr, st);
     // the listed queries, one warp each (their number is on the device)
     knn_pca_slow_kernel<<<num_sms * 8, kSlowWarps * 32, 0, st>>>(
         (const float4 *)xyz, (const float4 *)rgb, pca_opacity, S, knn, (float4 *)out->mean_op,
         (float4 *)out->scale, (float4 *)out->quat, (float4 *)out->rgb, (float4 *)out->normal);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (mode == 1) return launch_mlp_estimate(S.pk, n, mlp, knn, out, S.mlp_scratch, num_sms, st);
+    if (mode == 1) return launch_mlp_estimate(S.pk, n, mlp, knn, out, (int32_t *)(S.ticket + 9), num_sms, st);
     return cudaSuccess;
+}
+
+// Status of the last p2e_estimate (or p2e_estimate_global) call on this
+// scratch: P2E_ERR_TIMEOUT if one of its bounded device waits gave up.
+// Synchronises the stream.
+cudaError_t estimate_status(const void *scratch, int64_t n, cudaStream_t st, int32_t *out) {
+    EstScratch S;
+    est_layout(n, const_cast<void *>(scratch), &S);
+    int32_t w[2] = {0, 0};
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemcpy(w, S.ticket + 8, sizeof w, cudaMemcpyDeviceToHost)) != cudaSuccess) return e;
+    *out = w[0] != 0 ? w[0] : w[1];
+    return cudaSuccess;
+}
+
+// Timeout self-test of the cell-count scan: two tiles of counts whose work
+// tickets start at 1, so the only CTA takes tile 1 and waits on tile 0's
+// look-back word, which nothing publishes; the wait gives up after
+// `spin_limit` tries and records P2E_ERR_TIMEOUT.
+__global__ void selftest_scan_init_kernel(uint32_t *ticket) {
+    if (threadIdx.x == 0) *ticket = 1u;
+}
+
+size_t selftest_scan_bytes() { return al256(2 * kScanT * 4) + al256((2 * kScanT + 1) * 4) + al256(64) + al256(64); }
+
+cudaError_t launch_selftest_scan(void *scratch, int32_t *status, uint32_t spin_limit, cudaStream_t st) {
+    char *p = (char *)scratch;
+    EstScratch S;
+    memset(&S, 0, sizeof S);
+    uint32_t *counts = (uint32_t *)p;
+    p += al256(2 * kScanT * 4);
+    uint32_t *start = (uint32_t *)p;
+    p += al256((2 * kScanT + 1) * 4);
+    S.ticket = (uint32_t *)p;
+    p += al256(64);
+    S.scan_state = (uint64_t *)p;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, selftest_scan_bytes(), st);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(status, 0, sizeof(int32_t), st)) != cudaSuccess) return e;
+    selftest_scan_init_kernel<<<1, 32, 0, st>>>(S.ticket);
+    scan_counts_kernel<<<1, 256, 0, st>>>(counts, 2 * kScanT, start, S, status, spin_limit);
+    return cudaGetLastError();
 }
 
 // The global isotropic baseline: the mean nearest-neighbour distance over

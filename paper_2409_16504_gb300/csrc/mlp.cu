@@ -34,8 +34,6 @@ constexpr int kBlobBytes = kBlobB + (3 * kHid + kOutPad) * 4;
 static_assert(kBlobBytes == P2E_MLP_BLOB_BYTES, "weight blob layout of p2e.h");
 constexpr uint32_t kTmemCols = 64;
 
-size_t mlp_scratch_bytes(int64_t) { return 256; }
-
 // H (the hidden activations) aliases the front of A: layer 1 has finished
 // reading A when its epilogue writes H, and each later layer has finished
 // reading H when its epilogue overwrites it.  55 KB per CTA: four CTAs per SM.
@@ -89,15 +87,21 @@ __device__ __forceinline__ void umma_commit(uint64_t *mbar) {
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+// Bounded wait for the mbarrier phase `parity` to complete: at most
+// `limit` try_wait rounds, each suspending the thread for at most ~1 us
+// (the suspend-time hint) unless the phase completes first, then false:
+// about a second at the default limit.
+constexpr uint32_t kMbarTries = 1u << 20;
+constexpr uint32_t kMbarSuspendNs = 1000;
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint32_t limit = kMbarTries) {
     const uint32_t a = smem_u32(mbar);
-    for (uint32_t it = 0; it < (1u << 20); ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}\n"
             : "=r"(ok)
-            : "r"(a), "r"(parity)
+            : "r"(a), "r"(parity), "r"(kMbarSuspendNs)
             : "memory");
         if (ok) return true;
     }
@@ -376,9 +380,8 @@ __global__ void __launch_bounds__(kTM, 3) mlp_estimate_kernel(const float4 *__re
 }
 
 cudaError_t launch_mlp_estimate(const float4 *pk, int64_t n, const void *mlp,
-                                const uint32_t *knn, p2e_gaussians *out, void *scratch, int num_sms,
+                                const uint32_t *knn, p2e_gaussians *out, int32_t *status, int num_sms,
                                 cudaStream_t st) {
-    int32_t *status = (int32_t *)scratch;
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     const size_t smem = sizeof(MlpSmem) + 1024;
@@ -408,10 +411,34 @@ cudaError_t launch_mlp_estimate(const float4 *pk, int64_t n, const void *mlp,
     }
     const int64_t ntiles = (n + kTM - 1) / kTM;
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms * per_sm[slot]);
+    const p2e_kernel_probe *pr = kernel_probe(P2E_PROBE_MLP);
+    probe_start(pr, st);
     mlp_estimate_kernel<<<grid, kTM, smem, st>>>(pk, n,
                                                  (const unsigned char *)mlp, knn, (float4 *)out->mean_op,
                                                  (float4 *)out->scale, (float4 *)out->quat, (float4 *)out->normal,
                                                  status);
+    probe_stop(pr, st);
+    return cudaGetLastError();
+}
+
+// Timeout self-test of the bounded mbarrier wait: one CTA initialises an
+// mbarrier that expects one arrival, which never comes (no MMA is issued,
+// no TMEM is allocated), and waits on it with the head's wait routine.
+__global__ void selftest_mbar_kernel(int32_t *status, uint32_t limit) {
+    __shared__ uint64_t mbar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&mbar, 0u, limit)) atomicExch(status, (int32_t)P2E_ERR_TIMEOUT);
+    __syncthreads();
+}
+
+cudaError_t launch_selftest_mbar(int32_t *status, uint32_t spin_limit, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    selftest_mbar_kernel<<<1, 32, 0, st>>>(status, spin_limit);
     return cudaGetLastError();
 }
 

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_emit_kernel(
     const float4 *__restrict__ xy_depth, const uint32_t *__restrict__ order, int64_t n_total,
     uint64_t *__restrict__ keys,
     uint32_t *__restrict__ vals, int64_t capacity, SortScratch S, int64_t *n_keys_dev,
-    int32_t *status, __grid_constant__ const Views P) {
+    int32_t *status, uint32_t spin_limit, __grid_constant__ const Views P) {
     __shared__ uint64_t sm[kScanThreads / 32];
     __shared__ uint32_t s_tile;
     __shared__ uint64_t s_prefix;
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_emit_kernel(
                 const int first = pre ? __ffs(pre) - 1 : 32;
                 const unsigned need = first >= 31 ? 0xffffffffu : ((2u << first) - 1u);
                 if (notready & need) {
-                    if (++spins > kSpinLimit) {
+                    if (++spins > spin_limit) {
                         if (lane == 0) atomicExch(status, (int32_t)P2E_ERR_TIMEOUT);
                         break;
                     }
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
     const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const int64_t *n_keys_dev,
     int64_t capacity, int shift, const uint32_t *__restrict__ hist, uint32_t *sort_state,
-    uint32_t *ticket, int32_t *status) {
+    uint32_t *ticket, int32_t *status, uint32_t spin_limit) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem &sm = *reinterpret_cast<SortSmem *>(smem_raw);
     const int64_t K = sort_count(n_keys_dev, capacity);
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
         while (p >= 0) {
             const uint32_t w = ld_acquire_u32(sort_state + (size_t)p * kRadix + d);
             if ((w >> 30) == 0) {
-                if (++spins > kSpinLimit) { atomicExch(status, (int32_t)P2E_ERR_TIMEOUT); break; }
+                if (++spins > spin_limit) { atomicExch(status, (int32_t)P2E_ERR_TIMEOUT); break; }
                 backoff_lb(spins);
                 continue;
             }
@@ -483,6 +483,20 @@ __global__ void __launch_bounds__(1024) tile_work_kernel(const uint2 *__restrict
     }
 }
 
+// The radix pass takes more than the default 48 KB of dynamic shared
+// memory; the attribute is per device, so it is set once on each.
+static cudaError_t configure_radix_pass() {
+    static int configured[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (configured[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(radix_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SortSmem));
+    if (e == cudaSuccess) configured[dev] = 1;
+    return e;
+}
+
 int sort_passes(int64_t total_tiles) {
     int tb = 0;
     while ((int64_t(1) << tb) < total_tiles) ++tb;
@@ -503,17 +517,13 @@ cudaError_t launch_sort_bin(const p2e_projected *proj, const Views &P, p2e_bins 
     e = cudaMemsetAsync(io->n_keys_dev, 0, sizeof(int64_t), st);
     if (e != cudaSuccess) return e;
     const size_t smem = sizeof(SortSmem);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(radix_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_set = true;
-    }
+    if ((e = configure_radix_pass()) != cudaSuccess) return e;
     const unsigned sort_grid = (unsigned)(S.sort_tiles > 0 ? S.sort_tiles : 1);
     auto pass = [&](int slot, int src, int shift, const int64_t *count, unsigned grid) {
         radix_pass_kernel<<<grid, kSortThreads, smem, st>>>(
             io->keys[src], io->vals[src], io->keys[src ^ 1], io->vals[src ^ 1], count, io->capacity, shift,
             S.hist + slot * kRadix, S.sort_state + (size_t)slot * (S.sort_tiles + 1) * kRadix,
-            S.tickets + 1 + slot, io->status_dev);
+            S.tickets + 1 + slot, io->status_dev, kSpinLimit);
         return cudaGetLastError();
     };
     const unsigned scan_grid = (unsigned)S.scan_tiles;
@@ -533,7 +543,7 @@ cudaError_t launch_sort_bin(const p2e_projected *proj, const Views &P, p2e_bins 
         scan_emit_kernel<<<scan_grid, kScanThreads, 0, st>>>(proj->ntiles, (const ushort4 *)proj->rect,
                                                              (const float4 *)proj->xy_depth, io->vals[1], n_total,
                                                              io->keys[0], io->vals[0], io->capacity, S,
-                                                             io->n_keys_dev, io->status_dev, P);
+                                                             io->n_keys_dev, io->status_dev, kSpinLimit, P);
         digit_hist_kernel<<<num_sms * 4, 256, 0, st>>>(io->keys[0], io->n_keys_dev, io->capacity, 32, tpasses,
                                                        S.hist + 4 * kRadix);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -546,7 +556,7 @@ cudaError_t launch_sort_bin(const p2e_projected *proj, const Views &P, p2e_bins 
             scan_emit_kernel<<<scan_grid, kScanThreads, 0, st>>>(proj->ntiles, (const ushort4 *)proj->rect,
                                                                  (const float4 *)proj->xy_depth, nullptr, n_total,
                                                                  io->keys[0], io->vals[0], io->capacity, S,
-                                                                 io->n_keys_dev, io->status_dev, P);
+                                                                 io->n_keys_dev, io->status_dev, kSpinLimit, P);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         digit_hist_kernel<<<num_sms * 4, 256, 0, st>>>(io->keys[0], io->n_keys_dev, io->capacity, 0, passes,
@@ -561,6 +571,50 @@ cudaError_t launch_sort_bin(const p2e_projected *proj, const Views &P, p2e_bins 
                                                     P.total_tiles, (uint2 *)io->ranges);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     tile_work_kernel<<<1, 1024, 0, st>>>((const uint2 *)io->ranges, P.total_tiles, io->tile_work);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Timeout self-test: one radix pass over two tiles of keys whose work
+// tickets start at 1, so the only CTA takes tile 1 and its look-back waits
+// on tile 0's state, which no CTA ever publishes.  The wait gives up after
+// `spin_limit` tries, records P2E_ERR_TIMEOUT and the pass finishes (its
+// writes stay inside the buffers).
+// ---------------------------------------------------------------------------
+__global__ void selftest_sort_init_kernel(uint32_t *ticket, int64_t *n_keys, int64_t k) {
+    if (threadIdx.x == 0) {
+        *ticket = 1u;
+        *n_keys = k;
+    }
+}
+
+size_t selftest_sort_bytes() {
+    const size_t k = 2 * kSortTile;
+    return align256(2 * k * 8) + align256(2 * k * 4) + align256(kRadix * 4) + align256(3 * kRadix * 4) +
+           align256(16) + align256(16);
+}
+
+cudaError_t launch_selftest_sort(void *scratch, int32_t *status, uint32_t spin_limit, cudaStream_t st) {
+    const int64_t k = 2 * kSortTile;
+    char *p = (char *)scratch;
+    uint64_t *keys = (uint64_t *)p;
+    p += align256(2 * k * 8);
+    uint32_t *vals = (uint32_t *)p;
+    p += align256(2 * k * 4);
+    uint32_t *hist = (uint32_t *)p;  // all zero: no digit holds every key, so the pass ranks
+    p += align256(kRadix * 4);
+    uint32_t *state = (uint32_t *)p;
+    p += align256(3 * kRadix * 4);
+    uint32_t *ticket = (uint32_t *)p;
+    p += align256(16);
+    int64_t *n_keys = (int64_t *)p;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, selftest_sort_bytes(), st);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(status, 0, sizeof(int32_t), st)) != cudaSuccess) return e;
+    if ((e = configure_radix_pass()) != cudaSuccess) return e;
+    selftest_sort_init_kernel<<<1, 32, 0, st>>>(ticket, n_keys, k);
+    radix_pass_kernel<<<1, kSortThreads, sizeof(SortSmem), st>>>(keys, vals, keys + k, vals + k, n_keys, k, 0, hist,
+                                                                 state, ticket, status, spin_limit);
     return cudaGetLastError();
 }
 

@@ -47,6 +47,13 @@ class Estimator:
         return out
 
 
+    def check(self, n: int, stream=None) -> None:
+        """Synchronises ``stream`` and raises if a bounded device wait of the
+        last estimate on this scratch (``n`` points) gave up."""
+        sp = (self.scratch.data_ptr() + 255) & ~255
+        check("p2e_estimate", _lib.load().p2e_estimate_check(C.c_void_p(sp), self.scratch_bytes, n,
+                                                             _stream(stream)))
+
     def global_(self, xyz: torch.Tensor, rgb: torch.Tensor, sigma_rel: float, opacity: float = 0.9,
                 out: GaussianSet | None = None, knn: torch.Tensor | None = None, stream=None) -> GaussianSet:
         """The global isotropic baseline: scale sigma_rel x the cloud's mean

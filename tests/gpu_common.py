@@ -67,19 +67,46 @@ def gpu_proj_view(r, v, n):
     return dict(uv=uv, zkey=xy[:, 2].copy(), conic=co[:, :3], prect=rect[:, [0, 2, 1, 3]], ntiles=nt)
 
 
+# Knife-edge pixels (the oracle's flags: a splat's power within 1e-4 of the
+# 3-sigma boundary, alpha within 1e-6 of the floor or T within 1e-7 of the
+# cutoff) are excluded from the tolerance check because fp32 and fp64 may
+# take the discrete decision differently there.  Their number is bounded:
+# on the seeded test scenes it is 0-0.06 % of the pixels.
+MAX_FLAG_FRAC = 1e-3
+
+
 def compare_images(gpu: dict, orc: dict, tol=TOL, check_last=True, vals=None, ranges=None,
-                   tile=16, tile_base=0, tiles_x=None):
-    """Element-wise comparison on unflagged pixels; returns the max error."""
-    ok = ~orc["flag"]
+                   tile=16, tile_base=0, tiles_x=None, max_flag_frac=MAX_FLAG_FRAC,
+                   max_flag_mismatch=None):
+    """Element-wise comparison on unflagged pixels.  Returns the max error
+    per plane, the number of flagged pixels and how many of those differ by
+    more than ``tol`` (the decisions fp32 actually took differently);
+    asserts the flagged fraction is at most ``max_flag_frac`` and, if given,
+    the mismatching flagged pixels at most ``max_flag_mismatch``."""
+    flag = orc["flag"]
+    ok = ~flag
     errs = {}
+    bad = np.zeros(flag.shape, bool)
     for key in ("rgb", "normal"):
-        d = np.abs(gpu[key].cpu().numpy().astype(np.float64) - orc[key])[:, ok]
+        d = np.abs(gpu[key].cpu().numpy().astype(np.float64) - orc[key])
+        bad |= (d > tol).any(0)
+        d = d[:, ok]
         errs[key] = float(d.max()) if d.size else 0.0
     for key in ("depth", "alpha"):
-        d = np.abs(gpu[key].cpu().numpy().astype(np.float64) - orc[key])[ok]
+        d = np.abs(gpu[key].cpu().numpy().astype(np.float64) - orc[key])
+        bad |= d > tol
+        d = d[ok]
         errs[key] = float(d.max()) if d.size else 0.0
     for key, e in errs.items():
         assert e <= tol, f"{key}: max abs error {e:.3g} > {tol}"
+    nflag = int(flag.sum())
+    nmis = int((bad & flag).sum())
+    print(f"flagged pixels {nflag} of {flag.size} ({nflag / flag.size:.2e}); of them beyond {tol}: {nmis}")
+    assert nflag <= max_flag_frac * flag.size, f"{nflag} flagged pixels of {flag.size}"
+    if max_flag_mismatch is not None:
+        assert nmis <= max_flag_mismatch, f"{nmis} flagged pixels beyond the tolerance"
+    errs["flagged"] = nflag
+    errs["flagged_mismatch"] = nmis
     if check_last and vals is not None:
         last = gpu["last"].cpu().numpy().astype(np.int64)
         H, W = last.shape

@@ -44,3 +44,4 @@ def test_struct_layouts_match_header():
     assert C.sizeof(_lib.P2EConfig) == 4 + 5 * 4 + 3 * 4
     assert C.sizeof(_lib.P2EGaussians) == 5 * 8 + 8
     assert C.sizeof(_lib.P2EBins) == 2 * 8 + 2 * 8 + 8 + 8 + 8 + 8 + 8 + 8 + 8 + 8
+    assert C.sizeof(_lib.P2EKernelProbe) == 3 * 8

@@ -3,9 +3,12 @@
 kNN: the neighbour sets must be equal, except where fp32 and fp64 order
 two candidates differently; the accepted mismatch is one whose neighbours'
 FP64 distances agree with the oracle's sorted distances to 1e-6 relative.
-PCA: Sigma = R diag(s^2) R^T within 1e-4 of max|Sigma| per point (Sigma, not
-(s, q): eigenvectors are ill-conditioned near equal eigenvalues), unit
-normals parallel, with the orientation checked where (p - c) . n is clear.
+PCA: Sigma = R diag(s^2) R^T within 1e-4 of max|Sigma| per point, for every
+point (Sigma, not (s, q): eigenvectors are ill-conditioned near equal
+eigenvalues), unit normals parallel, with the orientation checked where
+(p - c) . n is clear.  The kernel accumulates the covariance on the
+offsets p_j - p_i (exact for near neighbours), so its fp32 rounding is
+relative to the neighbourhood's size: ~1e-6 of max|Sigma|.
 """
 import numpy as np
 import pytest
@@ -43,12 +46,12 @@ def _check(xyz, rgb):
     ok = same
     S_ref = oracle.sigma_of(e["scale"][ok], e["quat"][ok])
     S_got = oracle.sigma_of(got["scale"][ok, :3], got["quat"][ok])
-    # (a point whose 16 neighbours coincide has Sigma = 0 in FP64 and an fp32
-    # residue of the centroid's rounding, a few ulps of |x| ~ 1 m squared,
-    # ~1e-13 m^2: Sigma is compared to at least 1e-8 m^2, (0.1 mm)^2, far
-    # below the ~1e-6 m^2 of the test clouds' point spacing)
+    # (a point whose 16 neighbours coincide has Sigma = 0: the error is
+    # taken relative to at least 1e-8 m^2, (0.1 mm)^2, far below the
+    # ~1e-6 m^2 of the test clouds' point spacing)
     err = np.abs(S_got - S_ref).max((1, 2)) / np.maximum(np.abs(S_ref).max((1, 2)), 1e-8)
-    assert np.percentile(err, 99.9) < 1e-4 and err.max() < 1e-3, err.max()
+    print(f"Sigma: max rel error {err.max():.2e}, 99.9th percentile {np.percentile(err, 99.9):.2e}")
+    assert err.max() < 1e-4, err.max()
     cos = np.abs((got["normal"][ok, :3] * e["normal"][ok]).sum(1))
     # the normal is ill-defined only when the two smallest eigenvalues tie
     with np.errstate(divide="ignore", invalid="ignore"):  # lam0 = 0 where Sigma = 0

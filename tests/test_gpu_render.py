@@ -43,7 +43,7 @@ def _check_bins(r, g, cams, cfg=None):
     return keys, vals, ranges
 
 
-def _check_images(r, out, g, cams, cfg=None, tol=TOL):
+def _check_images(r, out, g, cams, cfg=None, tol=TOL, max_flag_mismatch=None):
     cfg = {**oracle.DEFAULT_CFG, **(cfg or {})}
     keys, vals, ranges = _check_bins(r, g, cams, cfg)
     base = 0
@@ -52,16 +52,20 @@ def _check_images(r, out, g, cams, cfg=None, tol=TOL):
         orc = oracle.render(g, cam, cfg)
         tx, ty = oracle.tiles_of(cam, cfg["tile"])
         errs.append(compare_images(out.view(v), orc, tol, vals=vals, ranges=ranges,
-                                   tile=cfg["tile"], tile_base=base, tiles_x=tx))
+                                   tile=cfg["tile"], tile_base=base, tiles_x=tx,
+                                   max_flag_mismatch=max_flag_mismatch))
         base += tx * ty
     return errs
 
 
 def test_cfg1_sphere_128():
+    """The 4096-point sphere: every pixel within 1e-4, knife-edge pixels
+    included (the oracle flags ~8 of 16384; fp32 takes the same decisions
+    there, so none is excluded in effect)."""
     g, cam = cfg1_scene()
     r, out = gpu_render(g, [cam])
     _check_projection(r, g, [cam])
-    errs = _check_images(r, out, g, [cam])
+    errs = _check_images(r, out, g, [cam], max_flag_mismatch=0)
     assert np.count_nonzero(out.view(0)["alpha"].cpu().numpy()) > 1000
     print("cfg1 max errors", errs)
 
@@ -155,11 +159,12 @@ def test_invalid_arguments_rejected_before_launch():
 
 def test_full_size_humanoid_800k_1024():
     """800K points, 1024^2: bit-exact keys/ranges, images within 1e-4 on
-    every unflagged pixel (the oracle renders the whole frame)."""
+    every pixel (the oracle renders the whole frame; it flags ~190 knife-edge
+    pixels, on which fp32 takes the same decisions)."""
     g, cam = humanoid_scene(800_000, 1024, 1024)
     r, out = gpu_render(g, [cam], capacity=1 << 21)
     _check_projection(r, g, [cam])
-    errs = _check_images(r, out, g, [cam])
+    errs = _check_images(r, out, g, [cam], max_flag_mismatch=0)
     print("800K max errors", errs)
 
 
