@@ -473,7 +473,7 @@ def main():
                            for p, v in lat.items()}
 
     # launches of our kernels per frame: estimate (init, bbox, grid, count,
-    # scan, scatter, kNN-PCA, listed queries [+ MLP]); project; sort_bin
+    # scan, scatter, kNN-PCA, listed queries [+ MLP head]); project; sort_bin
     # (depth min, depth keys, 4 depth passes, scan + emit, digit histogram,
     # tile passes, ranges, work list); render (fill, item table, blend)
     tbits = int(np.ceil(np.log2(max(2, (RES // args.tile) ** 2))))
@@ -486,6 +486,9 @@ def main():
     if not args.no_extras:
         line["e2e"] = e2e_runs(torch, dev, head_path, est, rend, mlp_blob, cx, cc, g_static, gs, cams, args, world)
         line["beyond_frame"] = beyond_frame(torch, dev, est, cx, cc, gs, img, cams, flush, ev, st, hbm)
+        # differentiation at scale: 200K points, 8 views at 512^2, Eq. 5 + SSIM
+        from paper_2409_16504_gb300.train import time_differentiation
+        line["differentiation"] = time_differentiation(points=200_000, views=8, res=512, ssim_weight=0.2, reps=5)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(head_path)
     if rank == 0 and world == 1 and not args.no_serving and not args.no_extras:

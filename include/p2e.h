@@ -307,6 +307,23 @@ p2e_status p2e_loss_eq5(const float *rgb, const float *normal, const float *gt_r
                         float w1, float w2, float w3, float *loss_dev, float *d_rgb,
                         float *d_normal, void *stream);
 
+/* p2e_loss_ssim -- the structural term of an "L1 + SSIM" image loss on the
+ * rendered colour (the training objective of the differentiable splatting
+ * this renderer follows; the paper's Eq. 5 is the L1 + normal loss above):
+ *   D = 1 - mean over pixels and channels of SSIM(I^, I)
+ * with, per channel and pixel, local statistics over an 11 x 11 Gaussian
+ * window (sigma 1.5, normalised; pixels outside the image count as zero):
+ *   SSIM = (2 mx my + C1)(2 cxy + C2) / ((mx^2 + my^2 + C1)(vx + vy + C2)),
+ *   C1 = 0.01^2, C2 = 0.03^2 (images in [0, 1]).
+ * ACCUMULATES: *loss_dev += weight D and d_rgb += weight dD/dI^ (so that it
+ * adds to p2e_loss_eq5's outputs).  rgb, gt_rgb, d_rgb: device planar
+ * [3][H][W] per view, views concatenated; view_hw (host): H, W of each of
+ * n_views views.  scratch: device, >= 96 bytes per pixel of all views,
+ * 256-byte aligned. */
+p2e_status p2e_loss_ssim(const float *rgb, const float *gt_rgb, const int32_t *view_hw, int32_t n_views,
+                         float weight, float *loss_dev, float *d_rgb, void *scratch, int64_t scratch_bytes,
+                         void *stream);
+
 /* p2e_mlp_backward -- gradient of a loss with respect to the estimator's
  * parameters, given its gradient with respect to the estimated Gaussians
  * (d_scale[3n], d_quat[4n] w.r.t. the output quaternion, d_opacity[n],
@@ -317,7 +334,11 @@ p2e_status p2e_loss_eq5(const float *rgb, const float *normal, const float *gt_r
  * mlp_weights: the blob the forward used.  The network is re-evaluated
  * with the forward's bf16 roundings.  grad: device float[P2E_MLP_PARAMS]
  * in blob order (W1, W2, W3, W4 16x64, b1, b2, b3, b4 16), ACCUMULATED
- * into.  Synchronises the stream once (reads the PCA opacity). */
+ * into.  The products run on the tensor cores with bf16 operands (the
+ * gradients flowing back are rounded to bf16 before each product) and fp32
+ * accumulation.  Synchronises the stream twice (reads the PCA opacity
+ * before the launch, and the kernel's status after it): returns
+ * P2E_ERR_TIMEOUT if a bounded device wait gave up (grad is then invalid). */
 #define P2E_MLP_PARAMS 15568
 p2e_status p2e_mlp_backward(const float *xyz, const float *rgb, int64_t n, const uint32_t *knn_idx,
                             const p2e_gaussians *pca, const void *mlp_weights, const float *d_scale,
@@ -383,10 +404,10 @@ p2e_status p2e_point_raster(const float *xyz, const float *rgb, int64_t n, const
  * probe = NULL.  This is the one piece of state the library keeps between
  * calls (thread-local, host memory only); with no probe set nothing is
  * recorded.
- *   kernel   P2E_PROBE_KNN     the kNN-PCA kernel of p2e_estimate (its fast
- *                              path; the few listed queries run after it)
- *            P2E_PROBE_BLEND   the compositing kernel of p2e_render
- *            P2E_PROBE_MLP     the learned head of p2e_estimate (mode 1)
+ *   kernel   P2E_PROBE_KNN       the kNN-PCA kernel of p2e_estimate (its
+ *                                fast path; the few listed queries run after it)
+ *            P2E_PROBE_BLEND     the compositing kernel of p2e_render
+ *            P2E_PROBE_MLP       the learned head of p2e_estimate (mode 1)
  *   probe    start_event / stop_event: cudaEvent_t (or NULL) recorded on
  *            the launching stream immediately before / after the kernel;
  *            count_dev: device uint64 (or NULL) the kernel adds its work

@@ -66,6 +66,7 @@ struct StageBuf {          // one chunk of staged splats (raw records)
     float4 co[32];         // (A, B, C, o)
     float4 cc[32];         // rgb
     float4 nr[32];         // (nx, ny, nz, -)
+    float4 off[32];        // block-relative offset of the centre (splat_offset), per splat
     uint32_t pos[32];      // list position
 };
 struct StageRec {          // per warp: two buffers, filled by cp.async in turn
@@ -241,14 +242,15 @@ struct SegArgs {
 // list order.  kStop: the stop rule of the sequential recurrence;
 // otherwise a pure product from the given state.  `pairs` counts the
 // (pixel, splat) pairs evaluated.
+// The splat's block-relative offset (the same for every pixel of the
+// block) was formed once per splat when the chunk was staged.
 template <bool kStop>
 __device__ __forceinline__ void composite_chunk(const StageBuf &sb, int nh, const SegArgs &a, PixState &st,
                                                 uint32_t &pairs) {
     if (st.done) return;
     int j = 0;
     for (; j < nh; ++j) {
-        const float4 xy = sb.xy[j], co = sb.co[j];
-        const float4 o = splat_offset(xy, a.x0, a.y0);
+        const float4 o = sb.off[j], co = sb.co[j];
         const float power = splat_power(o, co, a.lxf, a.lyf);
         if (power < a.pw_min) continue;
         float e;
@@ -269,7 +271,7 @@ __device__ __forceinline__ void composite_chunk(const StageBuf &sb, int nh, cons
         st.n0 = fmaf(wgt, nr.x, st.n0);
         st.n1 = fmaf(wgt, nr.y, st.n1);
         st.n2 = fmaf(wgt, nr.z, st.n2);
-        st.D = fmaf(wgt, xy.z, st.D);
+        st.D = fmaf(wgt, sb.xy[j].z, st.D);
         st.T = Tn;
         st.last = sb.pos[j] + 1u;
     }
@@ -308,7 +310,10 @@ __device__ __noinline__ uint32_t composite_segment(bool stop, uint32_t s0, uint3
             g[k] = idx < s1 ? __ldg(a.vals + idx) : 0xffffffffu;
         }
     };
-    auto composite = [&](const StageBuf &sb, int nh) {
+    auto composite = [&](StageBuf &sb, int nh) {
+        // one lane per staged splat: its offset from the block's origin
+        if (lane < nh) sb.off[lane] = splat_offset(sb.xy[lane], a.x0, a.y0);
+        __syncwarp();
         if (stop) composite_chunk<true>(sb, nh, a, st, pairs);
         else composite_chunk<false>(sb, nh, a, st, pairs);
     };

@@ -7,25 +7,27 @@
 // K13 loss_eq5:  L = w1 mean|I - I^| + w2 mean(|n x n^| + w3 min(|n - n^|, |n + n^|))
 //                (mean over pixels, the L1 also over the 3 channels); writes
 //                dL/dI^ and dL/dn^.
-// K12 mlp_bwd:   per tile of 32 points: recompute the features and the
-//                forward pass (bf16-rounded operands and activations, fp32
-//                sums, as the tensor-core kernel), back-propagate the output
-//                mapping (scale exp, quaternion increment, opacity logit
-//                shift, normal = third axis of R(q)) and the four layers
-//                with register-tiled shared-memory products; weight
-//                gradients accumulate in shared memory per CTA and are added
-//                to the global fp32 gradient once per CTA.
+// K12 mlp_bwd:   per tile of 128 points: recompute the features and the
+//                forward pass on tcgen05 (the inference head's bf16
+//                roundings), back-propagate the output mapping (scale exp,
+//                quaternion increment, opacity logit shift, normal = third
+//                axis of R(q)) per thread, then the four layers on tcgen05
+//                (bf16 operands, fp32 accumulation); weight and bias
+//                gradients accumulate in TMEM per CTA and are added to the
+//                global fp32 gradient once per CTA.
 // K12 adam:      fp32 master weights, first/second moments, bias
 //                correction; also writes the bf16 blob the forward reads.
 #include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
 
-#include "common.cuh"
+#include <algorithm>
+
+#include "tcgen05.cuh"
 
 namespace p2e {
 
 constexpr int kIn = 96, kHid = 64, kOut = 8, kOutPad = 16, kNb = 16;
-constexpr int kP = 32;  // points per tile
-constexpr int kNT = 256;
 // fp32 parameter vector layout (same order as the blob): W1, W2, W3, W4 (16x64), b1, b2, b3, b4 (16)
 constexpr int oW1 = 0, oW2 = oW1 + kHid * kIn, oW3 = oW2 + kHid * kHid, oW4 = oW3 + kHid * kHid,
               oB1 = oW4 + kOutPad * kHid, oB2 = oB1 + kHid, oB3 = oB2 + kHid, oB4 = oB3 + kHid,
@@ -92,139 +94,417 @@ __global__ void __launch_bounds__(256) loss_eq5_kernel(const float *__restrict__
     }
 }
 
-// ------------------------------------------------------------ MLP backward
-__device__ __forceinline__ float bfr(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+// ------------------------------------------------------------ SSIM term
+// D = 1 - mean SSIM(I^, I) over every pixel and channel of the views, the
+// structural term of an "L1 + SSIM" image loss, with its exact gradient
+// with respect to the rendered image I^ (x; the target is y).  Per channel
+// and pixel p, with an 11 x 11 Gaussian window w (sigma 1.5, normalised,
+// zero outside the image):
+//   mx = w * x, my = w * y, Exx = w * x^2, Eyy = w * y^2, Exy = w * xy,
+//   vx = Exx - mx^2, vy = Eyy - my^2, cxy = Exy - mx my,
+//   S = (2 mx my + C1)(2 cxy + C2) / ((mx^2 + my^2 + C1)(vx + vy + C2)),
+//   C1 = 0.01^2, C2 = 0.03^2 (images in [0, 1]).
+// dS_p/dx_q = w(p - q) (A_p + 2 x_q B_p + y_q C_p), A = dS/dmx, B = dS/dExx,
+// C = dS/dExy, so dD/dx = -(w * A + 2 x (w * B) + y (w * C)) / N
+// (w symmetric).  The blurs are separable: a horizontal then a vertical
+// 11-tap pass, each its own kernel, over planes in scratch.
+constexpr int kSsimR = 5;  // window radius
 
-// C[m][n] (+)= sum_k A[m*asm + k*ask] B[k*bsk + n*bsn], each thread a TM x TN block
-template <int M, int N, int K, int TM, int TN>
-__device__ __forceinline__ void sgemm(const float *A, int asm_, int ask, const float *B, int bsk, int bsn,
-                                      float *C, int ldc, bool acc) {
-    constexpr int BM = M / TM, BN = N / TN;
-    for (int blk = threadIdx.x; blk < BM * BN; blk += kNT) {
-        const int m0 = (blk / BN) * TM, n0 = (blk % BN) * TN;
-        float c[TM][TN];
-#pragma unroll
-        for (int i = 0; i < TM; ++i)
-#pragma unroll
-            for (int j = 0; j < TN; ++j) c[i][j] = acc ? C[(m0 + i) * ldc + n0 + j] : 0.f;
-        for (int k = 0; k < K; ++k) {
-            float a[TM], b[TN];
-#pragma unroll
-            for (int i = 0; i < TM; ++i) a[i] = A[(m0 + i) * asm_ + k * ask];
-#pragma unroll
-            for (int j = 0; j < TN; ++j) b[j] = B[k * bsk + (n0 + j) * bsn];
-#pragma unroll
-            for (int i = 0; i < TM; ++i)
-#pragma unroll
-                for (int j = 0; j < TN; ++j) c[i][j] = fmaf(a[i], b[j], c[i][j]);
+struct SsimViews {
+    int32_t n_views;
+    int32_t W[P2E_MAX_VIEWS], H[P2E_MAX_VIEWS];
+    int64_t base[P2E_MAX_VIEWS];  // first pixel of the view
+    int64_t npix;
+    float w[2 * kSsimR + 1];
+};
+
+// (view, local pixel) of element e of a [3][H][W]-per-view plane set
+__device__ __forceinline__ int ssim_view(const SsimViews &V, int64_t q) {
+    int v = 0;
+    while (v + 1 < V.n_views && V.base[v + 1] <= q) ++v;
+    return v;
+}
+
+// pass 1 (horizontal) of the five products, one thread per (pixel, channel)
+__global__ void __launch_bounds__(256) ssim_h5_kernel(const float *__restrict__ x, const float *__restrict__ y,
+                                                      float *__restrict__ h5, __grid_constant__ const SsimViews V) {
+    const int64_t total = 3 * V.npix;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = e / 3;
+        const int c = (int)(e - 3 * q);
+        const int v = ssim_view(V, q);
+        const int64_t p = q - V.base[v];
+        const int W = V.W[v];
+        const int64_t HW = (int64_t)W * V.H[v];
+        const int64_t plane = 3 * V.base[v] + c * HW;
+        const int row = (int)(p / W), col = (int)(p - (int64_t)row * W);
+        float s[5] = {0, 0, 0, 0, 0};
+        for (int k = -kSsimR; k <= kSsimR; ++k) {
+            const int cc = col + k;
+            if (cc < 0 || cc >= W) continue;
+            const float a = x[plane + (int64_t)row * W + cc], b = y[plane + (int64_t)row * W + cc];
+            const float wk = V.w[k + kSsimR];
+            s[0] = fmaf(wk, a, s[0]);
+            s[1] = fmaf(wk, b, s[1]);
+            s[2] = fmaf(wk, a * a, s[2]);
+            s[3] = fmaf(wk, b * b, s[3]);
+            s[4] = fmaf(wk, a * b, s[4]);
         }
+        const int64_t o = plane + p;
 #pragma unroll
-        for (int i = 0; i < TM; ++i)
-#pragma unroll
-            for (int j = 0; j < TN; ++j) C[(m0 + i) * ldc + n0 + j] = c[i][j];
+        for (int k = 0; k < 5; ++k) h5[k * 3 * V.npix + o] = s[k];
     }
 }
 
-struct BwdSmem {
-    float W1[kHid * kIn], W2[kHid * kHid], W3[kHid * kHid], W4[kOut * kHid];
-    float b[3 * kHid + kOut];
-    float X[kP * kIn];
-    float H1[kP * kHid], H2[kP * kHid], H3[kP * kHid];
-    float G1[kP * kHid], G2[kP * kHid];
-    float Y[kP * kOutPad], dY[kP * kOutPad];
-    float dW1[kHid * kIn], dW2[kHid * kHid], dW3[kHid * kHid], dW4[kOut * kHid];
-    float db[3 * kHid + kOut];
+// pass 2 (vertical): the local statistics, S, and the derivative maps
+// A, B, C; adds -weight * S / N to the loss (one atomic per block)
+__global__ void __launch_bounds__(256) ssim_v5_kernel(const float *__restrict__ h5, float *__restrict__ abc,
+                                                      float weight, float *loss, __grid_constant__ const SsimViews V) {
+    constexpr float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+    const int64_t total = 3 * V.npix;
+    float acc = 0.f;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = e / 3;
+        const int c = (int)(e - 3 * q);
+        const int v = ssim_view(V, q);
+        const int64_t p = q - V.base[v];
+        const int W = V.W[v], H = V.H[v];
+        const int64_t HW = (int64_t)W * H;
+        const int64_t plane = 3 * V.base[v] + c * HW;
+        const int row = (int)(p / W), col = (int)(p - (int64_t)row * W);
+        float m[5] = {0, 0, 0, 0, 0};
+        for (int k = -kSsimR; k <= kSsimR; ++k) {
+            const int rr = row + k;
+            if (rr < 0 || rr >= H) continue;
+            const float wk = V.w[k + kSsimR];
+            const int64_t o = plane + (int64_t)rr * W + col;
+#pragma unroll
+            for (int j = 0; j < 5; ++j) m[j] = fmaf(wk, h5[j * 3 * V.npix + o], m[j]);
+        }
+        const float mx = m[0], my = m[1];
+        const float vx = m[2] - mx * mx, vy = m[3] - my * my, cxy = m[4] - mx * my;
+        const float n1 = 2.f * mx * my + C1, n2 = 2.f * cxy + C2;
+        const float d1 = mx * mx + my * my + C1, d2 = vx + vy + C2;
+        const float S = (n1 * n2) / (d1 * d2);
+        acc += S;
+        const int64_t o = plane + p;
+        abc[o] = S * (2.f * my / n1 - 2.f * my / n2 - 2.f * mx / d1 + 2.f * mx / d2);
+        abc[3 * V.npix + o] = -S / d2;
+        abc[6 * V.npix + o] = 2.f * S / n2;
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    __shared__ float sw[8];
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sw[k];
+        atomicAdd(loss, -weight * t / (float)total);
+    }
+}
+
+// pass 3 (horizontal) of A, B, C
+__global__ void __launch_bounds__(256) ssim_h3_kernel(const float *__restrict__ abc, float *__restrict__ h3,
+                                                      __grid_constant__ const SsimViews V) {
+    const int64_t total = 3 * V.npix;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = e / 3;
+        const int c = (int)(e - 3 * q);
+        const int v = ssim_view(V, q);
+        const int64_t p = q - V.base[v];
+        const int W = V.W[v];
+        const int64_t HW = (int64_t)W * V.H[v];
+        const int64_t plane = 3 * V.base[v] + c * HW;
+        const int row = (int)(p / W), col = (int)(p - (int64_t)row * W);
+        float s[3] = {0, 0, 0};
+        for (int k = -kSsimR; k <= kSsimR; ++k) {
+            const int cc = col + k;
+            if (cc < 0 || cc >= W) continue;
+            const float wk = V.w[k + kSsimR];
+            const int64_t o = plane + (int64_t)row * W + cc;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) s[j] = fmaf(wk, abc[j * 3 * V.npix + o], s[j]);
+        }
+        const int64_t o = plane + p;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) h3[j * 3 * V.npix + o] = s[j];
+    }
+}
+
+// pass 4 (vertical): d_rgb += weight dD/dx
+__global__ void __launch_bounds__(256) ssim_grad_kernel(const float *__restrict__ x, const float *__restrict__ y,
+                                                        const float *__restrict__ h3, float weight,
+                                                        float *__restrict__ d_rgb, __grid_constant__ const SsimViews V) {
+    const int64_t total = 3 * V.npix;
+    const float scale = -weight / (float)total;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = e / 3;
+        const int c = (int)(e - 3 * q);
+        const int v = ssim_view(V, q);
+        const int64_t p = q - V.base[v];
+        const int W = V.W[v], H = V.H[v];
+        const int64_t HW = (int64_t)W * H;
+        const int64_t plane = 3 * V.base[v] + c * HW;
+        const int row = (int)(p / W), col = (int)(p - (int64_t)row * W);
+        float s[3] = {0, 0, 0};
+        for (int k = -kSsimR; k <= kSsimR; ++k) {
+            const int rr = row + k;
+            if (rr < 0 || rr >= H) continue;
+            const float wk = V.w[k + kSsimR];
+            const int64_t o = plane + (int64_t)rr * W + col;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) s[j] = fmaf(wk, h3[j * 3 * V.npix + o], s[j]);
+        }
+        const int64_t o = plane + p;
+        d_rgb[o] += scale * (s[0] + 2.f * x[o] * s[1] + y[o] * s[2]);
+    }
+}
+
+size_t ssim_scratch_bytes(int64_t npix) { return (size_t)8 * 3 * (size_t)npix * sizeof(float); }
+
+__global__ void ssim_add_kernel(float *loss, float v) {
+    if (threadIdx.x == 0) atomicAdd(loss, v);
+}
+
+// ------------------------------------------------------------ MLP backward
+// One 128-point tile per step (the UMMA M dimension), persistent CTAs of
+// 128 threads (thread = point row), one CTA per SM (the weight gradients
+// hold 416 TMEM columns).  All contractions run on tcgen05 (bf16 operands,
+// fp32 accumulation in TMEM):
+//   forward   H_l = bf16(relu(H_{l-1} W_l^T + b_l)), y = H_3 W_4^T + b_4, as
+//             the inference head (same roundings)
+//   output    dY = dL/dy through the output mapping (per thread, fp32),
+//             rounded to bf16 for the products
+//   backward  dH_{l-1} = dA_l W_l          (M = 128 points, K = out_l)
+//             dA_{l-1} = dH_{l-1} (H_{l-1} > 0), bf16
+//             [dW_l | db_l] += dA_l^T [H_{l-1} | 1]
+//                                         (M = out_l padded to 128, K = 128
+//                                          points, N = in_l + 16: a row of
+//                                          ones gives the bias gradient)
+// The [dW | db] accumulators stay in TMEM across the CTA's tiles and are
+// added to the global fp32 gradient once per CTA.  Operands whose
+// contraction runs over the points are written transposed (point-major ->
+// unit-major) by the epilogues; an A operand with fewer than 128 real rows
+// reads its padding rows from the next buffer (their products land in TMEM
+// lanes that are never read).
+// status of the last training backward on this device (P2E_OK, or
+// P2E_ERR_TIMEOUT when a bounded wait gave up)
+static __device__ int32_t g_train_status;
+
+constexpr int kBT = 128;
+constexpr int kInB = kIn + 16, kHidB = kHid + 16;   // B operands with the ones row (and zero padding)
+constexpr uint32_t kBwdCols = 512;
+constexpr uint32_t kColAcc = 0, kColW1 = 64, kColW2 = 192, kColW3 = 288, kColW4 = 384;
+
+struct __align__(128) TrainSmem {
+    __nv_bfloat16 W1[kHid * kIn], W2[kHid * kHid], W3[kHid * kHid], W4[kOutPad * kHid];   // forward B
+    __nv_bfloat16 W2T[kHid * kHid], W3T[kHid * kHid], W4T[kHid * kOutPad];                 // backward B
+    __nv_bfloat16 R[kBT * kIn];          // X, then H1..H3, then dA3, dA2 (point-major)
+    __nv_bfloat16 dY[kBT * kOutPad];     // point-major
+    __nv_bfloat16 dYT[kOutPad * kBT];    // unit-major; as a 128-row A operand it reads on into dAT, XT
+    __nv_bfloat16 dAT[kHid * kBT];       // unit-major; its padding rows read on into XT
+    __nv_bfloat16 XT[kInB * kBT];        // rows 96: ones, 97..111: zero
+    __nv_bfloat16 HT[3][kHidB * kBT];    // rows 64: ones, 65..79: zero
+    float b[3 * kHid + kOutPad];
+    uint64_t bar;
+    uint32_t tmem;
+    int err;
 };
+static_assert(sizeof(TrainSmem) + 1024 <= 227 * 1024, "shared memory of the training backward");
 
 __device__ __forceinline__ float4 qmul4(float4 a, float4 b) {
     return make_float4(a.x * b.x - a.y * b.y - a.z * b.z - a.w * b.w, a.x * b.y + a.y * b.x + a.z * b.w - a.w * b.z,
                        a.x * b.z - a.y * b.w + a.z * b.x + a.w * b.y, a.x * b.w + a.y * b.z - a.z * b.y + a.w * b.x);
 }
 
-__global__ void __launch_bounds__(kNT) mlp_bwd_kernel(
+// value v of (unit c, point r) into a unit-major [rows][128] operand
+__device__ __forceinline__ void put_t(__nv_bfloat16 *T, int c, int r, __nv_bfloat16 v) {
+    T[core_off(c, r, kBT)] = v;
+}
+
+__global__ void __launch_bounds__(kBT, 1) mlp_bwd_kernel(
     const float4 *__restrict__ xyz, const float4 *__restrict__ rgb, int64_t n, const uint32_t *__restrict__ knn,
     const float4 *__restrict__ pca_scale, const float4 *__restrict__ pca_quat, float opacity0,
     const unsigned char *__restrict__ blob, const float *__restrict__ d_scale, const float *__restrict__ d_quat,
-    const float *__restrict__ d_opacity, const float *__restrict__ d_normal, float *__restrict__ grad) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    BwdSmem &sm = *reinterpret_cast<BwdSmem *>(smem_raw);
-    const int tid = threadIdx.x;
-    // bf16 weights -> fp32 shared memory; zero the accumulators
+    const float *__restrict__ d_opacity, const float *__restrict__ d_normal, float *__restrict__ grad,
+    int32_t *status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    TrainSmem &sm = *reinterpret_cast<TrainSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t ntiles = (n + kBT - 1) / kBT;
+
+    // ---- weights: forward B operands W_l [out][in] and backward B
+    // operands W_l^T [in][out], core-matrix layout, from the bf16 blob
     {
         const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(blob);
-        for (int t = tid; t < kHid * kIn; t += kNT) sm.W1[t] = __bfloat162float(wb[oW1 + t]);
-        for (int t = tid; t < kHid * kHid; t += kNT) {
-            sm.W2[t] = __bfloat162float(wb[oW2 + t]);
-            sm.W3[t] = __bfloat162float(wb[oW3 + t]);
+        for (int t = tid; t < kHid * kIn; t += kBT) {
+            const int o = t / kIn, i = t % kIn;
+            sm.W1[core_off(o, i, kIn)] = wb[oW1 + t];
         }
-        for (int t = tid; t < kOut * kHid; t += kNT) sm.W4[t] = __bfloat162float(wb[oW4 + t]);
+        for (int t = tid; t < kHid * kHid; t += kBT) {
+            const int o = t / kHid, i = t % kHid;
+            sm.W2[core_off(o, i, kHid)] = wb[oW2 + t];
+            sm.W3[core_off(o, i, kHid)] = wb[oW3 + t];
+            sm.W2T[core_off(i, o, kHid)] = wb[oW2 + t];
+            sm.W3T[core_off(i, o, kHid)] = wb[oW3 + t];
+        }
+        for (int t = tid; t < kOutPad * kHid; t += kBT) {
+            const int o = t / kHid, i = t % kHid;
+            sm.W4[core_off(o, i, kHid)] = wb[oW4 + t];
+            sm.W4T[core_off(i, o, kOutPad)] = wb[oW4 + t];
+        }
         const float *bb = reinterpret_cast<const float *>(blob + 2 * oB1);
-        for (int t = tid; t < 3 * kHid; t += kNT) sm.b[t] = bb[t];
-        for (int t = tid; t < kOut; t += kNT) sm.b[3 * kHid + t] = bb[3 * kHid + t];
-        for (int t = tid; t < kHid * kIn; t += kNT) sm.dW1[t] = 0.f;
-        for (int t = tid; t < kHid * kHid; t += kNT) { sm.dW2[t] = 0.f; sm.dW3[t] = 0.f; }
-        for (int t = tid; t < kOut * kHid; t += kNT) sm.dW4[t] = 0.f;
-        for (int t = tid; t < 3 * kHid + kOut; t += kNT) sm.db[t] = 0.f;
+        for (int t = tid; t < 3 * kHid + kOutPad; t += kBT) sm.b[t] = bb[t];
+        // the ones rows of the [H | 1] operands (rows in_l .. in_l + 15:
+        // one row of ones, fifteen of zeros), written once
+        const __nv_bfloat16 one = __float2bfloat16_rn(1.f), zero = __float2bfloat16_rn(0.f);
+        for (int t = tid; t < 16 * kBT; t += kBT) {
+            const int c = t / kBT, r = t % kBT;
+            const __nv_bfloat16 v = c == 0 ? one : zero;
+            put_t(sm.XT, kIn + c, r, v);
+            for (int l = 0; l < 3; ++l) put_t(sm.HT[l], kHid + c, r, v);
+        }
+        // the dY operand's padding columns 8..15 stay zero
+        for (int t = tid; t < kBT * kOutPad; t += kBT) sm.dY[t] = zero;
+        for (int t = tid; t < kOutPad * kBT; t += kBT) sm.dYT[t] = zero;
     }
+    if (tid == 0) {
+        sm.err = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sm.bar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem)),
+                     "r"(kBwdCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    proxy_fence();
+    tc_fence_before();
     __syncthreads();
-    const int64_t ntiles = (n + kP - 1) / kP;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        // ---- features: 8 threads per point, 2 neighbours each
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    uint32_t phase = 0;
+    bool ok = true;
+    // issue (thread 0), commit, wait (everyone), uniform verdict
+    auto run = [&](auto &&issue) {
+        if (!ok) return;  // after a wait gave up nothing more is issued
+        if (tid == 0) {
+            tc_fence_after();
+            issue();
+            umma_commit(&sm.bar);
+        }
+        const bool w = mbar_wait(&sm.bar, phase);
+        phase ^= 1u;
+        tc_fence_after();
+        ok = ok && !__syncthreads_or(!w);
+    };
+    // generic stores into operands -> visible to the tensor cores
+    auto publish = [&]() {
+        proxy_fence();
+        tc_fence_before();
+        __syncthreads();
+    };
+
+    bool first = true;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int64_t i = tile * kBT + tid;
+        const bool live = i < n;
+        // ---- features of point i (bf16-rounded as the forward rounds them)
+        float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), q0 = make_float4(1.f, 0.f, 0.f, 0.f);
         {
-            const int pt = tid >> 3, part = tid & 7;
-            const int64_t i = tile * kP + pt;
-            float *xr = sm.X + pt * kIn;
-            if (i < n) {
-                const float4 p = __ldg(xyz + i), c = __ldg(rgb + i), q = __ldg(pca_quat + i);
-                const float w = q.x, x = q.y, y = q.z, z = q.w;
+            float f[kIn];
+#pragma unroll
+            for (int k = 0; k < kIn; ++k) f[k] = 0.f;
+            if (live) {
+                const float4 p = __ldg(xyz + i), c = __ldg(rgb + i);
+                q0 = __ldg(pca_quat + i);
+                s0 = __ldg(pca_scale + i);
+                const uint4 *kp = reinterpret_cast<const uint4 *>(knn + i * kNb);
+                uint32_t nb[kNb];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint4 u = __ldg(kp + k);
+                    nb[4 * k] = u.x; nb[4 * k + 1] = u.y; nb[4 * k + 2] = u.z; nb[4 * k + 3] = u.w;
+                }
+                float4 pn[kNb], cn[kNb];
+#pragma unroll
+                for (int u = 0; u < kNb; ++u) {
+                    pn[u] = __ldg(xyz + nb[u]);
+                    cn[u] = __ldg(rgb + nb[u]);
+                }
+                const float w = q0.x, x = q0.y, y = q0.z, z = q0.w;
                 const float R00 = 1.f - 2.f * (y * y + z * z), R01 = 2.f * (x * y - w * z), R02 = 2.f * (x * z + w * y);
                 const float R10 = 2.f * (x * y + w * z), R11 = 1.f - 2.f * (x * x + z * z), R12 = 2.f * (y * z - w * x);
                 const float R20 = 2.f * (x * z - w * y), R21 = 2.f * (y * z + w * x), R22 = 1.f - 2.f * (x * x + y * y);
-                const float4 pl = __ldg(xyz + knn[i * kNb + kNb - 1]);
-                const float lx = pl.x - p.x, ly = pl.y - p.y, lz = pl.z - p.z;
+                const float lx = pn[kNb - 1].x - p.x, ly = pn[kNb - 1].y - p.y, lz = pn[kNb - 1].z - p.z;
                 const float inv_r = 1.f / fmaxf(sqrtf(lx * lx + ly * ly + lz * lz), 1e-12f);
-                for (int u = 0; u < 2; ++u) {
-                    const int k = part * 2 + u;
-                    const uint32_t j = knn[i * kNb + k];
-                    const float4 pj = __ldg(xyz + j), cj = __ldg(rgb + j);
-                    const float dx = pj.x - p.x, dy = pj.y - p.y, dz = pj.z - p.z;
-                    xr[6 * k + 0] = bfr((R00 * dx + R10 * dy + R20 * dz) * inv_r);
-                    xr[6 * k + 1] = bfr((R01 * dx + R11 * dy + R21 * dz) * inv_r);
-                    xr[6 * k + 2] = bfr((R02 * dx + R12 * dy + R22 * dz) * inv_r);
-                    xr[6 * k + 3] = bfr(cj.x - c.x);
-                    xr[6 * k + 4] = bfr(cj.y - c.y);
-                    xr[6 * k + 5] = bfr(cj.z - c.z);
+#pragma unroll
+                for (int u = 0; u < kNb; ++u) {
+                    const float dx = pn[u].x - p.x, dy = pn[u].y - p.y, dz = pn[u].z - p.z;
+                    f[6 * u + 0] = (R00 * dx + R10 * dy + R20 * dz) * inv_r;
+                    f[6 * u + 1] = (R01 * dx + R11 * dy + R21 * dz) * inv_r;
+                    f[6 * u + 2] = (R02 * dx + R12 * dy + R22 * dz) * inv_r;
+                    f[6 * u + 3] = cn[u].x - c.x;
+                    f[6 * u + 4] = cn[u].y - c.y;
+                    f[6 * u + 5] = cn[u].z - c.z;
                 }
-            } else {
-                for (int k = part * 12; k < part * 12 + 12; ++k) xr[k] = 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < kIn; k += 8) {
+                uint32_t wv[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[k + 2 * e], f[k + 2 * e + 1]);
+                    wv[e] = *reinterpret_cast<const uint32_t *>(&b2);
+                    put_t(sm.XT, k + 2 * e, tid, b2.x);
+                    put_t(sm.XT, k + 2 * e + 1, tid, b2.y);
+                }
+                *reinterpret_cast<uint4 *>(sm.R + core_off(tid, k, kIn)) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
             }
         }
-        __syncthreads();
-        // ---- forward (fp32 sums of bf16-rounded operands)
-        sgemm<kP, kHid, kIn, 2, 4>(sm.X, kIn, 1, sm.W1, 1, kIn, sm.H1, kHid, false);
-        __syncthreads();
-        for (int t = tid; t < kP * kHid; t += kNT) sm.H1[t] = bfr(fmaxf(sm.H1[t] + sm.b[t % kHid], 0.f));
-        __syncthreads();
-        sgemm<kP, kHid, kHid, 2, 4>(sm.H1, kHid, 1, sm.W2, 1, kHid, sm.H2, kHid, false);
-        __syncthreads();
-        for (int t = tid; t < kP * kHid; t += kNT) sm.H2[t] = bfr(fmaxf(sm.H2[t] + sm.b[kHid + t % kHid], 0.f));
-        __syncthreads();
-        sgemm<kP, kHid, kHid, 2, 4>(sm.H2, kHid, 1, sm.W3, 1, kHid, sm.H3, kHid, false);
-        __syncthreads();
-        for (int t = tid; t < kP * kHid; t += kNT) sm.H3[t] = bfr(fmaxf(sm.H3[t] + sm.b[2 * kHid + t % kHid], 0.f));
-        __syncthreads();
-        sgemm<kP, kOut, kHid, 1, 1>(sm.H3, kHid, 1, sm.W4, 1, kHid, sm.Y, kOutPad, false);
-        __syncthreads();
-        // ---- output mapping backward -> dY (one thread per point)
-        if (tid < kP) {
-            const int64_t i = tile * kP + tid;
-            float *dy = sm.dY + tid * kOutPad;
-            for (int e = 0; e < kOutPad; ++e) dy[e] = 0.f;
-            if (i < n) {
+        publish();
+        // ---- forward: three hidden layers, ReLU masks kept per thread
+        uint32_t mask[3][2];
+        const __nv_bfloat16 *Wf[3] = {sm.W1, sm.W2, sm.W3};
+        for (int L = 0; L < 3; ++L) {
+            run([&] { umma_chain(tmem + kColAcc, sm.R, Wf[L], kBT, L == 0 ? kIn : kHid, kHid, false); });
+            float v[kHid];
+            tmem_ld64(tmem + lane_base + kColAcc, v);
+            mask[L][0] = mask[L][1] = 0u;
+#pragma unroll
+            for (int c = 0; c < kHid; c += 8) {
+                uint32_t wv[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int k = c + 2 * e;
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(fmaxf(v[k] + sm.b[L * kHid + k], 0.f),
+                                                                    fmaxf(v[k + 1] + sm.b[L * kHid + k + 1], 0.f));
+                    wv[e] = *reinterpret_cast<const uint32_t *>(&b2);
+                    put_t(sm.HT[L], k, tid, b2.x);
+                    put_t(sm.HT[L], k + 1, tid, b2.y);
+                    if (__bfloat162float(b2.x) > 0.f) mask[L][k >> 5] |= 1u << (k & 31);
+                    if (__bfloat162float(b2.y) > 0.f) mask[L][(k + 1) >> 5] |= 1u << ((k + 1) & 31);
+                }
+                *reinterpret_cast<uint4 *>(sm.R + core_off(tid, c, kHid)) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            }
+            publish();
+        }
+        run([&] { umma_chain(tmem + kColAcc, sm.R, sm.W4, kBT, kHid, kOutPad, false); });
+        // ---- output mapping backward -> dY (fp32, then bf16 operands)
+        {
+            float yv[16];
+            tmem_ld16(tmem + lane_base + kColAcc, yv);
+            float dy[kOut];
+#pragma unroll
+            for (int e = 0; e < kOut; ++e) dy[e] = 0.f;
+            if (live) {
                 float y[kOut];
-                for (int e = 0; e < kOut; ++e) y[e] = sm.Y[tid * kOutPad + e] + sm.b[3 * kHid + e];
-                const float4 s0 = __ldg(pca_scale + i), q0 = __ldg(pca_quat + i);
+#pragma unroll
+                for (int e = 0; e < kOut; ++e) y[e] = yv[e] + sm.b[3 * kHid + e];
                 const float s0v[3] = {s0.x, s0.y, s0.z};
+#pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const float yc = fminf(fmaxf(y[k], -4.f), 4.f);
                     dy[k] = (y[k] > -4.f && y[k] < 4.f) ? d_scale[3 * i + k] * s0v[k] * __expf(yc) : 0.f;
@@ -249,64 +529,95 @@ __global__ void __launch_bounds__(kNT) mlp_bwd_kernel(
                                      -a3 * g[0] + a2 * g[1] - a1 * g[2] + a0 * g[3]};
                 const float hv[4] = {dh.x, dh.y, dh.z, dh.w};
                 const float dot = hv[0] * gh[0] + hv[1] * gh[1] + hv[2] * gh[2] + hv[3] * gh[3];
+#pragma unroll
                 for (int k = 0; k < 4; ++k) dy[3 + k] = (gh[k] - hv[k] * dot) / dnorm;
                 const float o0 = fminf(fmaxf(opacity0, 1e-6f), 1.f - 1e-6f);
                 const float o = 1.f / (1.f + __expf(-(__logf(o0 / (1.f - o0)) + y[7])));
                 dy[7] = d_opacity[i] * o * (1.f - o);
             }
+            uint32_t wv[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const __nv_bfloat162 b2 = __floats2bfloat162_rn(dy[2 * e], dy[2 * e + 1]);
+                wv[e] = *reinterpret_cast<const uint32_t *>(&b2);
+                put_t(sm.dYT, 2 * e, tid, b2.x);
+                put_t(sm.dYT, 2 * e + 1, tid, b2.y);
+            }
+            *reinterpret_cast<uint4 *>(sm.dY + core_off(tid, 0, kOutPad)) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
-        __syncthreads();
-        // ---- layer 4
-        sgemm<kOut, kHid, kP, 1, 2>(sm.dY, 1, kOutPad, sm.H3, kHid, 1, sm.dW4, kHid, true);
-        if (tid < kOut) {
-            float s = 0.f;
-            for (int p = 0; p < kP; ++p) s += sm.dY[p * kOutPad + tid];
-            sm.db[3 * kHid + tid] += s;
+        publish();
+        // ---- layer 4: dH3 = dY W4 ; [dW4 | db4] += dY^T [H3 | 1]
+        run([&] {
+            umma_chain(tmem + kColAcc, sm.dY, sm.W4T, kBT, kOutPad, kHid, false);
+            umma_chain(tmem + kColW4, sm.dYT, sm.HT[2], kBT, kBT, kHidB, !first);
+        });
+        // ---- layers 3, 2: dA_l = dH_l (H_l > 0); dH_{l-1} = dA_l W_l ;
+        // [dW_l | db_l] += dA_l^T [H_{l-1} | 1]
+        const __nv_bfloat16 *WT[3] = {nullptr, sm.W2T, sm.W3T};
+        const uint32_t colW[3] = {kColW1, kColW2, kColW3};
+        for (int L = 2; L >= 0; --L) {
+            float v[kHid];
+            tmem_ld64(tmem + lane_base + kColAcc, v);
+#pragma unroll
+            for (int c = 0; c < kHid; c += 8) {
+                uint32_t wv[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int k = c + 2 * e;
+                    const float g0 = (mask[L][k >> 5] >> (k & 31)) & 1u ? v[k] : 0.f;
+                    const float g1 = (mask[L][(k + 1) >> 5] >> ((k + 1) & 31)) & 1u ? v[k + 1] : 0.f;
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(g0, g1);
+                    wv[e] = *reinterpret_cast<const uint32_t *>(&b2);
+                    put_t(sm.dAT, k, tid, b2.x);
+                    put_t(sm.dAT, k + 1, tid, b2.y);
+                }
+                if (L > 0)
+                    *reinterpret_cast<uint4 *>(sm.R + core_off(tid, c, kHid)) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            }
+            publish();
+            run([&] {
+                if (L > 0) umma_chain(tmem + kColAcc, sm.R, WT[L], kBT, kHid, kHid, false);
+                umma_chain(tmem + colW[L], sm.dAT, L > 0 ? sm.HT[L - 1] : sm.XT, kBT, kBT, L > 0 ? kHidB : kInB,
+                           !first);
+            });
         }
-        sgemm<kP, kHid, kOut, 2, 4>(sm.dY, kOutPad, 1, sm.W4, kHid, 1, sm.G1, kHid, false);
-        __syncthreads();
-        for (int t = tid; t < kP * kHid; t += kNT) sm.G1[t] = sm.H3[t] > 0.f ? sm.G1[t] : 0.f;
-        __syncthreads();
-        // ---- layer 3
-        sgemm<kHid, kHid, kP, 4, 4>(sm.G1, 1, kHid, sm.H2, kHid, 1, sm.dW3, kHid, true);
-        if (tid < kHid) {
-            float s = 0.f;
-            for (int p = 0; p < kP; ++p) s += sm.G1[p * kHid + tid];
-            sm.db[2 * kHid + tid] += s;
-        }
-        sgemm<kP, kHid, kHid, 2, 4>(sm.G1, kHid, 1, sm.W3, kHid, 1, sm.G2, kHid, false);
-        __syncthreads();
-        for (int t = tid; t < kP * kHid; t += kNT) sm.G2[t] = sm.H2[t] > 0.f ? sm.G2[t] : 0.f;
-        __syncthreads();
-        // ---- layer 2
-        sgemm<kHid, kHid, kP, 4, 4>(sm.G2, 1, kHid, sm.H1, kHid, 1, sm.dW2, kHid, true);
-        if (tid < kHid) {
-            float s = 0.f;
-            for (int p = 0; p < kP; ++p) s += sm.G2[p * kHid + tid];
-            sm.db[kHid + tid] += s;
-        }
-        sgemm<kP, kHid, kHid, 2, 4>(sm.G2, kHid, 1, sm.W2, kHid, 1, sm.G1, kHid, false);
-        __syncthreads();
-        for (int t = tid; t < kP * kHid; t += kNT) sm.G1[t] = sm.H1[t] > 0.f ? sm.G1[t] : 0.f;
-        __syncthreads();
-        // ---- layer 1
-        sgemm<kHid, kIn, kP, 4, 6>(sm.G1, 1, kHid, sm.X, kIn, 1, sm.dW1, kIn, true);
-        if (tid < kHid) {
-            float s = 0.f;
-            for (int p = 0; p < kP; ++p) s += sm.G1[p * kHid + tid];
-            sm.db[tid] += s;
-        }
-        __syncthreads();
+        first = false;
     }
-    // ---- once per CTA: add the accumulated gradients
-    for (int t = tid; t < kHid * kIn; t += kNT) atomicAdd(&grad[oW1 + t], sm.dW1[t]);
-    for (int t = tid; t < kHid * kHid; t += kNT) {
-        atomicAdd(&grad[oW2 + t], sm.dW2[t]);
-        atomicAdd(&grad[oW3 + t], sm.dW3[t]);
+    // ---- once per CTA: [dW | db] rows 0..63 (TMEM lanes of warps 0, 1)
+    if (ok && warp < 2 && !first) {
+        const int row = tid;  // output unit
+        float v[64], u[32], w16[16];
+        // layer 1: 96 weight columns, then the bias column
+        tmem_ld64(tmem + lane_base + kColW1, v);
+        tmem_ld32(tmem + lane_base + kColW1 + 64, u);
+        tmem_ld16(tmem + lane_base + kColW1 + 96, w16);
+        for (int c = 0; c < 64; ++c) atomicAdd(&grad[oW1 + row * kIn + c], v[c]);
+        for (int c = 0; c < 32; ++c) atomicAdd(&grad[oW1 + row * kIn + 64 + c], u[c]);
+        atomicAdd(&grad[oB1 + row], w16[0]);
+        const uint32_t cols[2] = {kColW2, kColW3};
+        const int offs[2] = {oW2, oW3}, boffs[2] = {oB2, oB3};
+        for (int l = 0; l < 2; ++l) {
+            tmem_ld64(tmem + lane_base + cols[l], v);
+            tmem_ld16(tmem + lane_base + cols[l] + 64, w16);
+            for (int c = 0; c < 64; ++c) atomicAdd(&grad[offs[l] + row * kHid + c], v[c]);
+            atomicAdd(&grad[boffs[l] + row], w16[0]);
+        }
+        tmem_ld64(tmem + lane_base + kColW4, v);
+        tmem_ld16(tmem + lane_base + kColW4 + 64, w16);
+        if (row < kOut) {
+            for (int c = 0; c < 64; ++c) atomicAdd(&grad[oW4 + row * kHid + c], v[c]);
+            atomicAdd(&grad[oB4 + row], w16[0]);
+        }
+    } else if (!ok && tid == 0) {
+        atomicExch(status, (int32_t)P2E_ERR_TIMEOUT);
+        mbar_wait(&sm.bar, phase ^ 1u);  // let an overdue MMA finish (bounded)
     }
-    for (int t = tid; t < kOut * kHid; t += kNT) atomicAdd(&grad[oW4 + t], sm.dW4[t]);
-    for (int t = tid; t < 3 * kHid; t += kNT) atomicAdd(&grad[oB1 + t], sm.db[t]);
-    for (int t = tid; t < kOut; t += kNT) atomicAdd(&grad[oB4 + t], sm.db[3 * kHid + t]);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBwdCols) : "memory");
+    }
 }
 
 // ------------------------------------------------------------------ Adam
@@ -366,37 +677,87 @@ p2e_status p2e_loss_eq5(const float *rgb, const float *normal, const float *gt_r
     return cudaGetLastError() == cudaSuccess ? P2E_OK : P2E_ERR_CUDA;
 }
 
+p2e_status p2e_loss_ssim(const float *rgb, const float *gt_rgb, const int32_t *view_hw, int32_t n_views,
+                         float weight, float *loss_dev, float *d_rgb, void *scratch, int64_t scratch_bytes,
+                         void *stream) {
+    if (!rgb || !gt_rgb || !view_hw || !loss_dev || !d_rgb || !scratch) return P2E_ERR_INVALID_ARG;
+    if (n_views < 1 || n_views > P2E_MAX_VIEWS || !(weight == weight)) return P2E_ERR_INVALID_ARG;
+    if (((uintptr_t)scratch & 255u)) return P2E_ERR_INVALID_ARG;
+    SsimViews V;
+    memset(&V, 0, sizeof V);
+    V.n_views = n_views;
+    int64_t tot = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const int32_t h = view_hw[2 * v], w = view_hw[2 * v + 1];
+        if (h < 1 || w < 1 || h > 8192 || w > 8192) return P2E_ERR_INVALID_ARG;
+        V.H[v] = h;
+        V.W[v] = w;
+        V.base[v] = tot;
+        tot += (int64_t)h * w;
+    }
+    V.npix = tot;
+    if (scratch_bytes < (int64_t)ssim_scratch_bytes(tot)) return P2E_ERR_INVALID_ARG;
+    double ws = 0.0;
+    for (int k = -kSsimR; k <= kSsimR; ++k) ws += exp(-(double)(k * k) / (2.0 * 1.5 * 1.5));
+    for (int k = -kSsimR; k <= kSsimR; ++k) V.w[k + kSsimR] = (float)(exp(-(double)(k * k) / (2.0 * 1.5 * 1.5)) / ws);
+    float *h5 = (float *)scratch;                 // 5 planes x 3 channels
+    float *abc = h5 + (size_t)5 * 3 * tot;        // 3 planes x 3 channels
+    float *h3 = h5;                               // reused once the statistics are taken
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned grid = (unsigned)std::min<int64_t>((3 * tot + 255) / 256, (int64_t)device_sms() * 8);
+    // the constant part of D: + weight (D = 1 - mean S)
+    ssim_add_kernel<<<1, 1, 0, st>>>(loss_dev, weight);
+    ssim_h5_kernel<<<grid, 256, 0, st>>>(rgb, gt_rgb, h5, V);
+    ssim_v5_kernel<<<grid, 256, 0, st>>>(h5, abc, weight, loss_dev, V);
+    ssim_h3_kernel<<<grid, 256, 0, st>>>(abc, h3, V);
+    ssim_grad_kernel<<<grid, 256, 0, st>>>(rgb, gt_rgb, h3, weight, d_rgb, V);
+    return cudaGetLastError() == cudaSuccess ? P2E_OK : P2E_ERR_CUDA;
+}
+
 p2e_status p2e_mlp_backward(const float *xyz, const float *rgb, int64_t n, const uint32_t *knn_idx,
                             const p2e_gaussians *pca, const void *mlp_weights, const float *d_scale,
                             const float *d_quat, const float *d_opacity, const float *d_normal, float *grad,
                             void *stream) {
-    if (n < 1 || !xyz || !rgb || !knn_idx || !pca || !pca->scale || !pca->quat || !mlp_weights || !d_scale ||
-        !d_quat || !d_opacity || !d_normal || !grad)
+    if (n < 1 || n >= (int64_t(1) << 31) || !xyz || !rgb || !knn_idx || !pca || !pca->scale || !pca->quat ||
+        !pca->mean_op || !mlp_weights || !d_scale || !d_quat || !d_opacity || !d_normal || !grad)
         return P2E_ERR_INVALID_ARG;
-    const size_t smem = sizeof(BwdSmem);
+    if (((uintptr_t)knn_idx & 15u) || ((uintptr_t)mlp_weights & 15u)) return P2E_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t smem = sizeof(TrainSmem) + 1024;
     static int configured[64] = {0};
+    static int32_t *status_addr[64] = {nullptr};
     int dev = 0;
-    cudaGetDevice(&dev);
-    const int slot = (dev >= 0 && dev < 64) ? dev : 0;
-    if (!configured[slot]) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return P2E_ERR_CUDA;
+    if (!configured[dev]) {
         if (cudaFuncSetAttribute(mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return P2E_ERR_CUDA;
-        configured[slot] = 1;
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_train_status) != cudaSuccess || !ptr) return P2E_ERR_CUDA;
+        status_addr[dev] = (int32_t *)ptr;
+        configured[dev] = 1;
     }
-    const int64_t ntiles = (n + kP - 1) / kP;
+    int32_t *status = status_addr[dev];
+    const int64_t ntiles = (n + kBT - 1) / kBT;
+    // one CTA per SM: its weight-gradient accumulators take 416 of the 512
+    // TMEM columns
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)device_sms());
     // opacity of the PCA estimate is the same for every point (mean_op.w)
     float o0 = 0.9f;
-    if (cudaMemcpyAsync(&o0, pca->mean_op ? pca->mean_op + 3 : nullptr, sizeof(float), cudaMemcpyDeviceToHost,
-                        (cudaStream_t)stream) != cudaSuccess ||
-        cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+    if (cudaMemcpyAsync(&o0, pca->mean_op + 3, sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
         return P2E_ERR_CUDA;
-    mlp_bwd_kernel<<<grid, kNT, smem, (cudaStream_t)stream>>>(
-        (const float4 *)xyz, (const float4 *)rgb, n, knn_idx, (const float4 *)pca->scale,
-        (const float4 *)pca->quat, o0, (const unsigned char *)mlp_weights, d_scale, d_quat, d_opacity, d_normal,
-        grad);
-    return cudaGetLastError() == cudaSuccess ? P2E_OK : P2E_ERR_CUDA;
+    if (cudaMemsetAsync(status, 0, sizeof(int32_t), st) != cudaSuccess) return P2E_ERR_CUDA;
+    mlp_bwd_kernel<<<grid, kBT, smem, st>>>((const float4 *)xyz, (const float4 *)rgb, n, knn_idx,
+                                           (const float4 *)pca->scale, (const float4 *)pca->quat, o0,
+                                           (const unsigned char *)mlp_weights, d_scale, d_quat, d_opacity, d_normal,
+                                           grad, status);
+    if (cudaGetLastError() != cudaSuccess) return P2E_ERR_CUDA;
+    int32_t hs = 0;
+    if (cudaMemcpyAsync(&hs, status, sizeof hs, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return P2E_ERR_CUDA;
+    return hs != 0 ? (p2e_status)hs : P2E_OK;
 }
 
 p2e_status p2e_adam(float *params, float *grad, float *m, float *v, int64_t count, float lr, float beta1,

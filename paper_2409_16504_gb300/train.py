@@ -47,37 +47,47 @@ def unflatten(theta: torch.Tensor) -> dict:
     return out
 
 
+def scene_parts(seed: int, n_points: int, n_views: int, res: int, jitter: float = 0.15, degrade=None):
+    """Host-side parts of a scene: (prims, xyz, rgb, cameras).  ``degrade``:
+    None, ("quant", alpha) for a 10-bit voxelised input coarsened by alpha,
+    or ("sub", beta) for a random beta-subset (the input augmentations of
+    Sec. 3.3); the ground truth stays exact."""
+    import scenes
+    prims = scenes.humanoid_primitives(seed, jitter=jitter)
+    xyz, rgb, _, _ = scenes.humanoid_cloud(n_points, seed=seed, prims=prims)
+    if degrade is not None:
+        kind, amount = degrade
+        if kind == "quant":
+            xyz, rgb = scenes.quantize_cloud(xyz, rgb, alpha=amount)
+        elif kind == "sub":
+            xyz, rgb = scenes.subsample_cloud(xyz, rgb, amount, seed + 11)
+        else:
+            raise ValueError(f"unknown degradation {kind}")
+    rng = np.random.default_rng(seed + 7)
+    center = xyz.mean(0)
+    cams = [scenes.sphere_camera(center, 2.5, rng, res, res) for _ in range(n_views)]
+    return prims, xyz, rgb, cams
+
+
 class Scene:
     """A training / evaluation scene: cloud on the device, cameras, and the
     ground-truth RGB and normal images in the renderer's planar layout."""
 
     def __init__(self, seed: int, n_points: int, n_views: int, res: int, jitter: float = 0.15,
-                 device="cuda", degrade=None):
-        """``degrade``: None, ("quant", alpha) for a 10-bit voxelised input
-        coarsened by alpha, or ("sub", beta) for a random beta-subset (the
-        input augmentations of Sec. 3.3); the ground truth stays exact."""
+                 device="cuda", degrade=None, parts=None, gt=None):
+        """``parts`` / ``gt``: precomputed scene_parts(...) and ground-truth
+        views (e.g. ray cast in a process pool), else computed here."""
         import scenes
-        prims = scenes.humanoid_primitives(seed, jitter=jitter)
-        xyz, rgb, _, _ = scenes.humanoid_cloud(n_points, seed=seed, prims=prims)
-        if degrade is not None:
-            kind, amount = degrade
-            if kind == "quant":
-                xyz, rgb = scenes.quantize_cloud(xyz, rgb, alpha=amount)
-            elif kind == "sub":
-                xyz, rgb = scenes.subsample_cloud(xyz, rgb, amount, seed + 11)
-            else:
-                raise ValueError(f"unknown degradation {kind}")
-            n_points = len(xyz)
-        rng = np.random.default_rng(seed + 7)
-        center = xyz.mean(0)
-        self.cams = [scenes.sphere_camera(center, 2.5, rng, res, res) for _ in range(n_views)]
-        gt = scenes.gt_views(prims, self.cams)
+        prims, xyz, rgb, cams = parts or scene_parts(seed, n_points, n_views, res, jitter, degrade)
+        self.cams = cams
+        if gt is None:
+            gt = scenes.gt_views(prims, cams)
         self.xyz, self.rgb = cloud_tensors(xyz, rgb, device)
-        self.n = n_points
+        self.n = len(xyz)
         self.gt_rgb = torch.from_numpy(np.concatenate([g["rgb"].reshape(-1) for g in gt]).astype(np.float32)).to(device)
         self.gt_normal = torch.from_numpy(
             np.concatenate([g["normal"].reshape(-1) for g in gt]).astype(np.float32)).to(device)
-        self.view_pixels = (C.c_int64 * n_views)(*[res * res] * n_views)
+        self.view_pixels = (C.c_int64 * len(cams))(*[int(c["width"]) * int(c["height"]) for c in cams])
 
 
     def degraded(self, degrade, seed: int = 0, device="cuda") -> "Scene":
@@ -101,9 +111,28 @@ class Scene:
         return out
 
 
+def loss_ssim(rgb: torch.Tensor, gt_rgb: torch.Tensor, sizes: list, weight: float, loss_dev: torch.Tensor,
+              d_rgb: torch.Tensor, scratch: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Adds weight x (1 - mean SSIM) of the rendered colour to ``loss_dev`` and
+    its gradient to ``d_rgb`` (p2e_loss_ssim); ``sizes`` = [(H, W)] per view.
+    Returns the scratch buffer (grown if needed) for reuse."""
+    npix = sum(h * w for h, w in sizes)
+    need = 96 * npix + 256
+    if scratch is None or scratch.numel() < need:
+        scratch = torch.empty(need, dtype=torch.uint8, device=rgb.device)
+    hw = (C.c_int32 * (2 * len(sizes)))(*[v for h, w in sizes for v in (h, w)])
+    sp = (scratch.data_ptr() + 255) & ~255
+    check("p2e_loss_ssim", _lib.load().p2e_loss_ssim(_ptr(rgb), _ptr(gt_rgb), hw, len(sizes), C.c_float(weight),
+                                                     _ptr(loss_dev), _ptr(d_rgb), C.c_void_p(sp), need - 256,
+                                                     _stream(stream)))
+    return scratch
+
+
 class Trainer:
     def __init__(self, n_max: int, seed: int = 0, lr: float = 1e-3, cfg: dict | None = None, device="cuda",
-                 params: dict | None = None):
+                 params: dict | None = None, ssim_weight: float = 0.0):
+        """``ssim_weight`` > 0 adds that weight times the SSIM term
+        (p2e_loss_ssim) of the colour to the Eq. 5 loss."""
         self.device = device
         self.cfg = {**DEFAULT_CONFIG, **(cfg or {})}
         self.theta = flatten(params if params is not None else mlp.init_params(seed, device)).to(device)
@@ -116,15 +145,29 @@ class Trainer:
         self.t = 0
         self.est = Estimator(n_max, device)
         self.loss_dev = torch.zeros(1, dtype=torch.float32, device=device)
+        # buffers reused across steps (the renderer grows its key buffers
+        # when a scene needs more)
+        self.rend = Renderer(self.cfg, capacity=1 << 20, device=device)
+        self.knn = torch.empty((n_max, 16), dtype=torch.int32, device=device)
+        self.g_pca = GaussianSet.empty(n_max, device)
+        self.g_net = GaussianSet.empty(n_max, device)
+        self.ssim_weight = float(ssim_weight)
+        self.ssim_scratch = None
 
     def params(self) -> dict:
         return unflatten(self.theta)
 
     def _forward(self, sc: Scene, learned: bool = True):
-        knn = torch.empty((sc.n, 16), dtype=torch.int32, device=self.device)
-        g_pca = self.est(sc.xyz, sc.rgb, mode=PCA, knn=knn)
-        g = self.est(sc.xyz, sc.rgb, mode=LEARNED, mlp_blob=self.blob) if learned else g_pca
-        r = Renderer(self.cfg, capacity=max(1 << 18, 6 * sc.n * len(sc.cams)), device=self.device)
+        if sc.n > self.knn.shape[0]:
+            self.knn = torch.empty((sc.n, 16), dtype=torch.int32, device=self.device)
+            self.g_pca = GaussianSet.empty(sc.n, self.device)
+            self.g_net = GaussianSet.empty(sc.n, self.device)
+        n = sc.n
+        knn = self.knn[:n]
+        view = lambda g: GaussianSet(g.mean_op[:n], g.scale[:n], g.quat[:n], g.rgb[:n], g.normal[:n])  # noqa: E731
+        g_pca = self.est(sc.xyz, sc.rgb, mode=PCA, knn=knn, out=view(self.g_pca))
+        g = self.est(sc.xyz, sc.rgb, mode=LEARNED, mlp_blob=self.blob, out=view(self.g_net)) if learned else g_pca
+        r = self.rend
         img = r.render(g, sc.cams)
         return knn, g_pca, g, r, img
 
@@ -134,6 +177,10 @@ class Trainer:
         check("p2e_loss_eq5", _lib.load().p2e_loss_eq5(
             _ptr(img.rgb), _ptr(img.normal), _ptr(sc.gt_rgb), _ptr(sc.gt_normal), sc.view_pixels,
             len(sc.cams), *LOSS_W, _ptr(self.loss_dev), _ptr(d_rgb), _ptr(d_nrm), _stream()))
+        if self.ssim_weight > 0:
+            sizes = [(int(c["height"]), int(c["width"])) for c in sc.cams]
+            self.ssim_scratch = loss_ssim(img.rgb, sc.gt_rgb, sizes, self.ssim_weight, self.loss_dev, d_rgb,
+                                          self.ssim_scratch)
         return d_rgb, d_nrm
 
     def step(self, sc: Scene) -> float:
@@ -161,16 +208,51 @@ class Trainer:
         return dict(loss=float(self.loss_dev.item()), psnr=10.0 * math.log10(1.0 / max(mse, 1e-12)))
 
 
+def time_differentiation(points: int = 200_000, views: int = 8, res: int = 512, ssim_weight: float = 0.2,
+                         reps: int = 5, seed: int = 3, device="cuda") -> dict:
+    """Forward and backward of the splatting at the differentiation scale:
+    a ``points``-point humanoid (kNN-PCA Gaussians), ``views`` views at
+    res x res, loss = Eq. 5 + ssim_weight x the SSIM term against the exact
+    ray-cast views, gradients with respect to every Gaussian parameter.
+    Median CUDA-event milliseconds of each phase over ``reps`` runs."""
+    sc = Scene(seed, points, views, res, device=device)
+    tr = Trainer(points, ssim_weight=ssim_weight, device=device)
+    knn, g_pca, g, r, img = tr._forward(sc, learned=False)
+    st = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    rows = []
+    for it in range(reps + 2):
+        e = [ev() for _ in range(4)]
+        e[0].record(st)
+        img = r.render(g, sc.cams, out=img, check=False)
+        e[1].record(st)
+        d_rgb, d_nrm = tr._loss(sc, img)
+        e[2].record(st)
+        d = p2e_render_backward(g, r.proj, r.bins, sc.cams, r.cfg, img.alpha, img.last, d_rgb=d_rgb,
+                                d_normal=d_nrm)
+        e[3].record(st)
+        torch.cuda.synchronize()
+        if it >= 2:
+            rows.append([e[k].elapsed_time(e[k + 1]) for k in range(3)])
+    med = np.median(np.array(rows), 0)
+    finite = all(bool(torch.isfinite(v).all()) for v in d.values())
+    return dict(points=points, views=views, res=res, ssim_weight=ssim_weight, keys=r.n_keys,
+                render_ms=float(med[0]), loss_ms=float(med[1]), backward_ms=float(med[2]),
+                total_ms=float(med.sum()), loss=float(tr.loss_dev.item()), gradients_finite=finite)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description="train the learned per-point estimator")
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--scenes", type=int, default=32)
-    ap.add_argument("--points", type=int, default=150_000)
+    ap.add_argument("--points", type=int, nargs="+", default=[100_000, 1_000_000],
+                    help="points per training scene: one value, or a range drawn log-uniformly per scene")
     ap.add_argument("--views", type=int, default=4)
-    ap.add_argument("--res", type=int, default=256)
+    ap.add_argument("--res", type=int, default=512)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--eval-scenes", type=int, default=4)
     ap.add_argument("--out", default=mlp.TRAINED)
+    ap.add_argument("--ssim", type=float, default=0.0, help="weight of the SSIM term added to the Eq. 5 loss")
     ap.add_argument("--augment", type=float, default=0.0,
                     help="fraction of training scenes with degraded inputs (10-bit voxels coarsened by "
                          "alpha in [0.25, 1], or a beta in [0.125, 1] random subset)")
@@ -186,10 +268,18 @@ def main(argv=None):
             return None
         return ("quant", float(rng.uniform(0.25, 1.0))) if rng.random() < 0.5 else \
             ("sub", float(rng.uniform(0.125, 1.0)))
-    pool = [Scene(1000 + s, a.points, a.views, a.res, degrade=degrade_of(s)) for s in range(a.scenes)]
-    held = [Scene(2000 + s, a.points, 12, a.res) for s in range(a.eval_scenes)]
-    print(f"scenes ready in {time.time() - t0:.1f} s", flush=True)
-    tr = Trainer(a.points, lr=a.lr)
+    lo, hi = (a.points[0], a.points[-1])
+    npts = [int(round(math.exp(rng.uniform(math.log(lo), math.log(hi))))) if hi > lo else lo
+            for _ in range(a.scenes)]
+    parts = [scene_parts(1000 + s, npts[s], a.views, a.res, degrade=degrade_of(s)) for s in range(a.scenes)]
+    held_parts = [scene_parts(2000 + s, int(math.sqrt(lo * hi)), 12, a.res) for s in range(a.eval_scenes)]
+    # ground truth ray cast in a process pool before the first GPU call
+    from .evaluate import ground_truth
+    gts = ground_truth([(p[0], p[3]) for p in parts + held_parts])
+    pool = [Scene(0, 0, 0, 0, parts=p, gt=g) for p, g in zip(parts, gts[:len(parts)])]
+    held = [Scene(0, 0, 0, 0, parts=p, gt=g) for p, g in zip(held_parts, gts[len(parts):])]
+    print(f"scenes ready in {time.time() - t0:.1f} s (points {min(npts)}..{max(npts)})", flush=True)
+    tr = Trainer(max(npts + [len(p[1]) for p in held_parts]), lr=a.lr, ssim_weight=a.ssim)
     before = [tr.evaluate(h, learned=False) for h in held]
     t1 = time.time()
     for it in range(a.steps):

@@ -2,16 +2,20 @@
 
 * p2e_loss_eq5 against Eq. 5 written out in numpy (FP64): loss and its
   gradient within 1e-5 (fp32 sums over ~10^4 pixels).
-* p2e_mlp_backward against the oracle's FP64 gradient with the forward's
-  bf16 roundings held fixed: per parameter tensor |gpu - oracle|_F <=
-  2e-2 |oracle|_F.  The GPU sums in fp32 and takes its features from its
-  own fp32 PCA frame (~1e-6 from the FP64 one); about 5e-4 of the features
-  then round to the neighbouring bf16 value (2^-8 apart), which moves the
-  hidden activations and, through cancelling sums, the early layers'
-  gradients by up to ~1% (measured: on identical inputs the kernel agrees
-  with the FP64 gradient to 4e-5 of the largest entry).  Points whose PCA frame is
-  ill-conditioned (near-equal eigenvalues) or whose canonical sign
-  decisions are knife edges get zero upstream gradient on both sides.
+* p2e_mlp_backward (tcgen05: bf16 operands, fp32 accumulation) against the
+  oracle's FP64 gradient with the forward's bf16 roundings held fixed, per
+  parameter tensor: |gpu - oracle|_F <= 2e-2 |oracle|_F and, element by
+  element, max |gpu - oracle| <= 3e-2 max |oracle|.  The GPU rounds the
+  gradients flowing back to bf16 before each tensor-core product (2^-9
+  relative per operand, averaging out over the 128-point sums), sums in
+  fp32, and takes its features from its own fp32 PCA frame (~1e-6 from the
+  FP64 one): about 5e-4 of the features then round to the neighbouring
+  bf16 value (2^-8 apart), which moves the hidden activations and, through
+  cancelling sums, the early layers' gradients by up to ~1%.  Points whose
+  PCA frame is ill-conditioned (near-equal eigenvalues) or whose canonical
+  sign decisions are knife edges get zero upstream gradient on both sides.
+  The 50K-point case runs several 128-point tiles per CTA (the TMEM
+  gradient accumulators carried across tiles).
 * p2e_adam against numpy.
 * A short end-to-end run (estimate -> render -> loss -> backward -> Adam)
   lowers the loss.
@@ -86,11 +90,12 @@ def test_loss_eq5_matches_numpy():
     np.testing.assert_allclose(got_n, g_n, rtol=1e-4, atol=1e-9)
 
 
-def test_mlp_backward_matches_oracle():
+@pytest.mark.parametrize("npts", [4096, 50_000])
+def test_mlp_backward_matches_oracle(npts):
     from paper_2409_16504_gb300 import _lib, mlp
     from paper_2409_16504_gb300.estimate import PCA, Estimator, cloud_tensors
     from paper_2409_16504_gb300.render import _ptr, _stream
-    xyz, rgb, _, _ = scenes.humanoid_cloud(4096, seed=9)
+    xyz, rgb, _, _ = scenes.humanoid_cloud(npts, seed=9)
     n = len(xyz)
     g = torch.Generator().manual_seed(4)
     p = mlp.init_params(2, device="cpu")
@@ -132,9 +137,15 @@ def test_mlp_backward_matches_oracle():
     got = {k: v.cpu().numpy().astype(np.float64) for k, v in unflatten(grad).items()}
     for k in ("W1", "W2", "W3", "W4", "b1", "b2", "b3", "b4"):
         r = ref[k]
-        err = np.linalg.norm(got[k] - r) / np.linalg.norm(r)
+        g_ = got[k]
+        if k in ("W4", "b4"):   # rows 8..15 are padding: exactly zero on both sides
+            assert (g_[8:] == 0).all()
+        err = np.linalg.norm(g_ - r) / np.linalg.norm(r)
+        emax = np.abs(g_ - r).max() / np.abs(r).max()
+        print(f"{k}: Frobenius {err:.2e}, element max {emax:.2e} of max |ref|")
         assert np.abs(r).max() > 0
         assert err <= 2e-2, (k, err)
+        assert emax <= 3e-2, (k, emax)
 
 
 def test_adam_matches_numpy():
