@@ -15,8 +15,9 @@
 // f_k = gC.c_k + gN.n_k + gD z_k and the running tail
 //   S_k = sum_{j>k} alpha_j T_j f_j + T_final (gC.bg - gA),
 // dL/dalpha_k = T_k f_k - S_k / (1 - alpha_k).  Per-splat screen-space
-// gradients (u, v, A, B, C, o, z, rgb, normal) are reduced over the warp,
-// then over the CTA in shared memory, then added to global memory.
+// gradients (u, v, A, B, C, o, z, rgb, normal) are reduced over the warp
+// (a transposing butterfly: 16 shuffles for the 13 channels), then over the
+// CTA in shared memory, then added to global memory.
 //
 // K8 (per Gaussian): chain rule through conic = Sigma_s^-1,
 // Sigma_s = M M^T + lowpass I, M = J T R S, R(q / |q|), and the centre
@@ -32,6 +33,31 @@ size_t backward_scratch_bytes(int64_t n_total) {
     return ((size_t)n_total * kG2D * sizeof(float) + 255) & ~size_t(255);
 }
 
+// Sum over the warp of 16 per-lane values (q[QN..15] taken as zero),
+// returned transposed: lane l gets the sum of value (l >> 1) & 15.
+__device__ __forceinline__ float warp_transpose_sum(const float (&q)[QN], int lane) {
+    float a[8], b[4], c[2];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {  // offset 16: keep half i + 8 * bit4
+        const float lo = i < QN ? q[i] : 0.f, hi = i + 8 < QN ? q[i + 8] : 0.f;
+        const bool up = (lane & 16) != 0;
+        a[i] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {  // offset 8
+        const bool up = (lane & 8) != 0;
+        b[i] = (up ? a[i + 4] : a[i]) + __shfl_xor_sync(0xffffffffu, up ? a[i] : a[i + 4], 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {  // offset 4
+        const bool up = (lane & 4) != 0;
+        c[i] = (up ? b[i + 2] : b[i]) + __shfl_xor_sync(0xffffffffu, up ? b[i] : b[i + 2], 4);
+    }
+    const bool up = (lane & 2) != 0;  // offset 2
+    float d = (up ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, up ? c[0] : c[1], 2);
+    return d + __shfl_xor_sync(0xffffffffu, d, 1);
+}
+
 template <int B>
 struct BwdShape {
     static constexpr int NT = B * B;
@@ -42,19 +68,23 @@ template <int B>
 __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
     const uint32_t *__restrict__ work, uint32_t *__restrict__ work_counter,
-    const float4 *__restrict__ xy_depth, const float4 *__restrict__ conic_op,
+    const float4 *__restrict__ xy_depth, const float4 *__restrict__ conic_op, const ushort4 *__restrict__ rect,
     const float4 *__restrict__ rgb, const float4 *__restrict__ normal,
     const float *__restrict__ alpha_img, const uint32_t *__restrict__ last_img,
     const float *__restrict__ d_rgb, const float *__restrict__ d_nrm, const float *__restrict__ d_depth,
     const float *__restrict__ d_alpha, float *__restrict__ g2d, __grid_constant__ const Views P) {
     constexpr int NT = BwdShape<B>::NT, BATCH = BwdShape<B>::BATCH;
     __shared__ float4 s_off[BATCH], s_co[BATCH], s_cz[BATCH], s_nr[BATCH];
+    __shared__ ushort4 s_rc[BATCH];
     __shared__ uint32_t s_g[BATCH];
     __shared__ float s_acc[BATCH][QN];
     __shared__ uint32_t s_item, s_end;
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int lx = tid % B, ly = tid / B;
+    // the tile rows of this warp's pixels (a splat whose pixel rectangle
+    // misses them cannot touch them: the warp skips it as a whole)
+    const int wy0 = (tid & ~31) / B, wy1 = ((tid & ~31) + 31) / B;
     const float lxf = (float)lx, lyf = (float)ly;
     const float pw_min = -0.5f * P.sigma_mult * P.sigma_mult;
     const float amax = P.alpha_max, afloor = P.alpha_floor;
@@ -105,11 +135,14 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
                 if (g >= (uint32_t)P.n) g = 0;
                 s_off[tid] = splat_offset(__ldg(xy_depth + gbase + g), x0, y0);
                 s_co[tid] = __ldg(conic_op + gbase + g);
+                s_rc[tid] = __ldg(rect + gbase + g);
             }
             __syncthreads();
             if (inside) {
                 const int jend = (int)min((uint32_t)cnt, lastp > bstart ? lastp - bstart : 0u);
                 for (int j = 0; j < jend; ++j) {
+                    const ushort4 rc = s_rc[j];
+                    if ((int)rc.w < y0 + wy0 || (int)rc.y > y0 + wy1) continue;  // uniform over the warp
                     const float4 o = s_off[j], co = s_co[j];
                     float dx, dy;
                     splat_delta(o, lxf, lyf, dx, dy);
@@ -136,12 +169,15 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
                 const float4 cc = __ldg(rgb + g);
                 s_off[tid] = splat_offset(xy, x0, y0);
                 s_co[tid] = __ldg(conic_op + gbase + g);
+                s_rc[tid] = __ldg(rect + gbase + g);
                 s_cz[tid] = make_float4(cc.x, cc.y, cc.z, xy.z);
                 s_nr[tid] = __ldg(normal + g);
                 s_g[tid] = g;
             }
             __syncthreads();
             for (int j = cnt - 1; j >= 0; --j) {
+                const ushort4 rc = s_rc[j];
+                if ((int)rc.w < y0 + wy0 || (int)rc.y > y0 + wy1) continue;  // uniform over the warp
                 float q[QN];
 #pragma unroll
                 for (int c = 0; c < QN; ++c) q[c] = 0.f;
@@ -186,17 +222,13 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                    for (int c = 0; c < QN; ++c) {
-                        float v = q[c];
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                        q[c] = v;
-                    }
-                    if (lane == 0)
-#pragma unroll
-                        for (int c = 0; c < QN; ++c)
-                            if (q[c] != 0.f) atomicAdd(&s_acc[j][c], q[c]);
+                    // transposing butterfly: each step hands half of the
+                    // channels a lane still holds to its partner, so 16
+                    // channels take 8 + 4 + 2 + 1 + 1 shuffles; lane l ends
+                    // with the warp's sum of channel (l >> 1) & 15
+                    const float v = warp_transpose_sum(q, lane);
+                    const int c = (lane >> 1) & 15;
+                    if (!(lane & 1) && c < QN && v != 0.f) atomicAdd(&s_acc[j][c], v);
                 }
             }
             __syncthreads();
@@ -337,7 +369,8 @@ static cudaError_t launch_bwd(const p2e_gaussians *g, const p2e_projected *proj,
     const int grid = device_sms() * (B == 8 ? 8 : (B == 16 ? 2 : 1));
     blend_bwd_kernel<B><<<grid, BwdShape<B>::NT, 0, st>>>(
         (const uint2 *)bins->ranges, bins->vals[bins->result], bins->tile_work, bins->tile_work + 1,
-        (const float4 *)proj->xy_depth, (const float4 *)proj->conic_op, (const float4 *)g->rgb,
+        (const float4 *)proj->xy_depth, (const float4 *)proj->conic_op, (const ushort4 *)proj->rect,
+        (const float4 *)g->rgb,
         (const float4 *)g->normal, alpha, last, d_rgb, d_normal, d_depth, d_alpha, g2d, P);
     return cudaGetLastError();
 }

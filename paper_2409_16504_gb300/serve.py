@@ -206,6 +206,9 @@ class GpuExecutor:
 
     def _promote(self) -> None:
         if self.pending is not None and self.ready[self.pending].query():
+            # the estimate finished: raises if one of its bounded device
+            # waits gave up (its Gaussians would be invalid)
+            self.est.check(self.n[self.pending], self.est_stream)
             self.front, self.pending = self.pending, None
 
     def publish(self, xyz, rgb, version: int = 0) -> None:
@@ -233,6 +236,7 @@ class GpuExecutor:
         self.n[back], self.ready[back], self.version[back] = n, ev, version
         if self.front is None:
             ev.synchronize()
+            self.est.check(n, self.est_stream)
             self.front = back
         else:
             self.pending = back

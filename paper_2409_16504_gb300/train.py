@@ -243,8 +243,8 @@ def time_differentiation(points: int = 200_000, views: int = 8, res: int = 512, 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description="train the learned per-point estimator")
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--scenes", type=int, default=32)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--scenes", type=int, default=48)
     ap.add_argument("--points", type=int, nargs="+", default=[100_000, 1_000_000],
                     help="points per training scene: one value, or a range drawn log-uniformly per scene")
     ap.add_argument("--views", type=int, default=4)
