@@ -64,26 +64,31 @@ BLEND_BYTES_PER_PIXEL = 9 * 4
 FP32_LANES_PER_SM = 128
 
 # DRAM bytes per launch from one ncu capture of the kernel (dram__bytes_read
-# + dram__bytes_write, profiles/), valid while the kernel's source file is
-# unchanged (its SHA-256 prefix below); otherwise the line reports null.
+# + dram__bytes_write, profiles/), valid while the kernel's sources are
+# unchanged (the SHA-256 prefix of their concatenation below); otherwise the
+# line reports null.
+_CSRC = "paper_2409_16504_gb300/csrc/"
 NCU_TRAFFIC = {
-    "knn": {"kernel": "knn_pca_kernel", "source": "paper_2409_16504_gb300/csrc/estimate.cu",
+    "knn": {"kernel": "knn_pca_kernel", "sources": [_CSRC + "estimate.cu"],
             "sha256_16": None, "bytes": None},
-    "blend": {"kernel": "blend_kernel<16>", "source": "paper_2409_16504_gb300/csrc/blend.cu",
+    "blend": {"kernel": "blend_kernel<16>", "sources": [_CSRC + "blend.cu", _CSRC + "splat.cuh"],
               "sha256_16": None, "bytes": None},
-    "mlp": {"kernel": "mlp_estimate_kernel", "source": "paper_2409_16504_gb300/csrc/mlp.cu",
-            "sha256_16": None, "bytes": None},
+    "mlp": {"kernel": "mlp_estimate_kernel", "sources": [_CSRC + "mlp.cu", _CSRC + "tcgen05.cuh"],
+            "sha256_16": "7d49e064b1b85464", "bytes": 135_280_000},
 }
 
 
-def source_digest(rel: str) -> str:
-    with open(os.path.join(ROOT, rel), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def source_digest(rels: list) -> str:
+    h = hashlib.sha256()
+    for rel in rels:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(which: str):
     e = NCU_TRAFFIC[which]
-    if e["bytes"] is None or e["sha256_16"] != source_digest(e["source"]):
+    if e["bytes"] is None or e["sha256_16"] != source_digest(e["sources"]):
         return None
     return e["bytes"]
 
@@ -331,7 +336,7 @@ def main():
     rend = Renderer({"tile": args.tile}, capacity=1 << 21, device=dev)
     est(cx, cc, out=gs)
     rend.render(gs, [cams[0]])
-    rend.capacity = int(rend.n_keys * 1.6) + 4096   # headroom for other viewpoints
+    rend.capacity = int(rend.n_keys * 2.0) + 4096   # headroom for other viewpoints and the compositing states
     rend.render(gs, [cams[0]])
     img = Images([cams[0]], dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)

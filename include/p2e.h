@@ -71,11 +71,21 @@ typedef struct {
  *   t_min       compositing stops before T would drop below    (1e-4)
  *   lowpass     px^2 added to the screen covariance diagonal   (0.3)
  *   sigma_mult  splat boundary in standard deviations (Sec. 3.1: 3)
- *   bg          background colour composited with the final T  (0,0,0) */
+ *   bg          background colour composited with the final T  (0,0,0)
+ *   schedule    compositing work schedule (no effect on the images, which
+ *               are bit-identical either way): P2E_SCHEDULE_AUTO (0) chains
+ *               the segments of long tile lists across warps, longest
+ *               tiles first, while their states fit in the free half of
+ *               the key buffers (8 bytes per key of a chained segment), and
+ *               has one warp per (tile, pixel block) take the rest;
+ *               P2E_SCHEDULE_PER_BLOCK (1) has one warp composite all
+ *               segments of every (tile, pixel block) in turn. */
+enum { P2E_SCHEDULE_AUTO = 0, P2E_SCHEDULE_PER_BLOCK = 1 };
 typedef struct {
     int32_t tile;
     float alpha_floor, alpha_max, t_min, lowpass, sigma_mult;
     float bg[3];
+    int32_t schedule;
 } p2e_config;
 
 /* Gaussian set, device memory, n entries each (Sec. 3.1, 11 parameters plus
@@ -234,8 +244,9 @@ p2e_status p2e_bins_check(const p2e_bins *io, int64_t *n_keys_host, void *stream
  *   Any output pointer may be NULL except `last` when a backward pass
  *   will follow.
  * Scratch: the free half of the key double buffer, keys[1 - result] and
- * vals[1 - result], is overwritten (per-segment compositing states and
- * the work-item table); the sorted keys/vals[result] are left intact.
+ * vals[1 - result], is overwritten (the work-item table, per-segment
+ * compositing states, arrival counters and flags); the sorted
+ * keys/vals[result] are left intact.
  * Device waits are bounded; one that gives up sets *bins->status_dev to
  * P2E_ERR_TIMEOUT (reported by p2e_bins_check). */
 p2e_status p2e_render(const p2e_gaussians *g, const p2e_projected *proj, const p2e_bins *bins,

@@ -17,6 +17,7 @@ _lib = None
 
 P2E_OK, P2E_ERR_INVALID_ARG, P2E_ERR_CAPACITY, P2E_ERR_CUDA, P2E_ERR_TIMEOUT, P2E_ERR_UNSUPPORTED = range(6)
 P2E_MAX_VIEWS = 64
+P2E_SCHEDULE_AUTO, P2E_SCHEDULE_PER_BLOCK = 0, 1
 P2E_SCRATCH_SORT, P2E_SCRATCH_ESTIMATE, P2E_SCRATCH_BACKWARD = 0, 1, 2
 
 # every symbol include/p2e.h declares
@@ -42,7 +43,7 @@ class P2ECamera(C.Structure):
 class P2EConfig(C.Structure):
     _fields_ = [("tile", C.c_int32), ("alpha_floor", C.c_float), ("alpha_max", C.c_float),
                 ("t_min", C.c_float), ("lowpass", C.c_float), ("sigma_mult", C.c_float),
-                ("bg", C.c_float * 3)]
+                ("bg", C.c_float * 3), ("schedule", C.c_int32)]
 
 
 class P2EGaussians(C.Structure):

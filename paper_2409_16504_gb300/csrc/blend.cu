@@ -34,8 +34,10 @@
 // last segment's state is the pixel.  While it speculates, a warp polls the
 // predecessor's state: pixels it shows done, or whose stop it shows to lie
 // in the part already walked, drop out (their aggregate is not used; the
-// latter publish T = 0).  Without room for the states (small capacities)
-// one warp runs the same segments of a (tile, block) in turn.  Which rule
+// latter publish T = 0).  The states take 8 bytes per key of the segments
+// they cover; the longest tiles take them first, and where the free buffers
+// run out (small capacities) one warp runs the same segments of a (tile,
+// block) in turn, tile by tile.  Which rule
 // gives a pixel's result depends only on its tile's list: results are
 // bit-identical across schedules, batches and runs.
 //
@@ -51,7 +53,7 @@ namespace p2e {
 
 constexpr int kBW = 8, kBH = 4;    // pixel block of one warp
 constexpr int kWarps = 8;          // warps per CTA
-constexpr int kStateWords = 9;     // T, C0..2, N0..2, D, last | done << 31
+constexpr int kStateFloats = 8;    // T, C0..2, N0..2, D (and a word last | done << 31 apart)
 constexpr uint32_t kDoneBit = 1u << 31;
 constexpr uint32_t kIncl = 2u;  // segment flag: inclusive state published
 
@@ -59,6 +61,9 @@ __host__ __device__ constexpr int blocks_of(int tile) { return (tile / kBW) * (t
 // Segment length: 128 splats per pixel block of the tile (1024 for 16-px
 // tiles).  It is fixed, so a pixel's arithmetic depends only on its tile's
 // list, never on the capacity, the other views of the call, or timing.
+// (Longer segments leave too few items: with 2048 nearly every segment of
+// a frame starts at once and is speculated in full before its predecessor
+// publishes; measured 2.7x the evaluated pairs.)
 __host__ __device__ constexpr uint32_t seg_len(int tile) { return 128u * (uint32_t)blocks_of(tile); }
 
 struct StageBuf {          // one chunk of staged splats (raw records)
@@ -96,47 +101,61 @@ __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Layout of the free half of the key double buffer while p2e_render runs:
-//   vals[1 - result] (uint32): [0] 1 when segments are chained across warps,
-//                    [1, n_work + 1] item_base, [n_work + 2, 2 n_work + 2] seg_base
-//   keys[1 - result] (bytes):  segment states (seg-major, kStateWords x 32
-//                    words per block), then one arrival counter and one
-//                    ready flag per (segment, block)
-// item_base[w] / seg_base[w]: first item / first segment of work entry w.
-constexpr int kStateBytes = kStateWords * 32 * 4;
+// Layout of the free half of the key double buffer while p2e_render runs
+// (n_work work entries, NB pixel blocks per tile, one state slot per
+// segment of a chained tile):
+//   vals[1 - result] (uint32 words):
+//     [0]                          1 when the chained schedule is in use
+//     [1, n_work + 1]              item_base: first item of work entry w, then the total
+//     [n_work + 2, 2 n_work + 2]   slot_base: first state slot of entry w (kNoSlot for a
+//                                  tile whose blocks each run in one warp), then the
+//                                  slots in use
+//     [2 n_work + 3]               multi-segment tiles run without chaining
+//     [2 n_work + 4]               max_slots: the slots the two buffers hold
+//     from tbl_words(n_work)       per (slot, block) 32 words 'last | done << 31',
+//                                  then max_slots x NB arrival counters, then as
+//                                  many ready flags
+//   keys[1 - result] (floats):     per (slot, block) kStateFloats x 32 state floats
+//                                  (word-major)
+// A slot costs NB x 1 KB of the key buffer, i.e. 8 bytes per key of its
+// segment: the key buffer holds the states of every key it can hold.
+constexpr uint32_t kNoSlot = 0xffffffffu;
+__host__ __device__ inline int64_t tbl_words(uint32_t n_work) { return (2 * (int64_t)n_work + 5 + 31) & ~int64_t(31); }
 
-// Item table (one CTA): exclusive scans of blocks x segments and of
-// segments over the work list, the chain decision, and zeroed counters and
-// flags for the segments in use.  Chaining needs the key count within the
-// capacity and the tables and states within the free buffers; otherwise
-// every (tile, block) is one item and nothing else is written.
+// Item table (one CTA).  Over the work list (longest tiles first), the
+// multi-segment tiles take state slots while they fit (a prefix of the
+// list): each of their segments is an item per block, chained across
+// warps.  A multi-segment tile past the prefix is one item per block whose
+// warp runs the same segments in turn (same arithmetic, same result); a
+// one-segment tile is one item per block in either case.  Chaining needs
+// the key count within the capacity and the table within the value buffer;
+// otherwise every (tile, block) is one item and nothing else is written.
 __global__ void __launch_bounds__(1024) render_items_kernel(const uint2 *__restrict__ ranges,
                                                             const uint32_t *__restrict__ work,
                                                             const int64_t *__restrict__ n_keys_dev,
                                                             int64_t capacity, int allow_chain, int tile,
-                                                            uint32_t *__restrict__ table, char *__restrict__ store) {
+                                                            uint32_t *__restrict__ table) {
     __shared__ uint32_t s_sum[32], s_off[32];
-    __shared__ uint32_t s_carry, s_tot;
+    __shared__ uint32_t s_carry, s_carry2, s_tot, s_used, s_alone;
     const uint32_t n_work = work[0];
     const uint32_t nb = (uint32_t)blocks_of(tile), S = seg_len(tile);
-    const bool fits = allow_chain && *n_keys_dev <= capacity && 2 * (int64_t)n_work + 3 <= capacity;
+    const int64_t tbl = tbl_words(n_work);
+    const bool fits = allow_chain && *n_keys_dev <= capacity && tbl <= capacity;
     if (!fits) {
         if (threadIdx.x == 0 && capacity > 0) table[0] = 0u;
         return;
     }
-    uint32_t *item_base = table + 1, *seg_base = table + 2 + n_work;
-    if (threadIdx.x == 0) s_carry = 0;
+    const int64_t ms = min(capacity * 8 / ((int64_t)nb * 32 * kStateFloats * 4),  // key buffer (bytes)
+                           (capacity - tbl) / ((int64_t)nb * 34));                // value buffer (words)
+    const uint32_t max_slots = (uint32_t)min(ms, (int64_t)0x7fffffff);
+    uint32_t *item_base = table + 1, *slot_base = table + 2 + n_work;
+    if (threadIdx.x == 0) s_carry = s_carry2 = s_used = s_alone = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = (int)(blockDim.x >> 5);
-    for (uint32_t b0 = 0; b0 < n_work; b0 += blockDim.x) {
-        const uint32_t w = b0 + threadIdx.x;
-        uint32_t v = 0;
-        if (w < n_work) {
-            const uint2 r = ranges[work[2 + w]];
-            v = (r.y - r.x + S - 1) / S;  // segments of the tile
-        }
-        uint32_t x = v;  // inclusive scan within the warp
+    // exclusive block scan of one value per thread (and the block's total)
+    auto block_scan = [&](uint32_t v, uint32_t &excl, uint32_t &tot) {
+        uint32_t x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -156,26 +175,51 @@ __global__ void __launch_bounds__(1024) render_items_kernel(const uint2 *__restr
             if (lane == 31) s_tot = t;
         }
         __syncthreads();
+        excl = s_off[wid] + x - v;
+        tot = s_tot;
+        __syncthreads();
+    };
+    for (uint32_t b0 = 0; b0 < n_work; b0 += blockDim.x) {
+        const uint32_t w = b0 + threadIdx.x;
+        uint32_t v = 0;
+        if (w < n_work) {
+            const uint2 r = ranges[work[2 + w]];
+            v = (r.y - r.x + S - 1) / S;  // segments of the tile
+        }
+        const uint32_t vs = v > 1 ? v : 0u;  // slots a chained tile takes
+        uint32_t e1, t1, e0, t0;
+        block_scan(vs, e1, t1);
+        const uint64_t first = (uint64_t)s_carry2 + e1;
+        const bool chain = vs > 0 && first + vs <= max_slots;
+        const uint32_t vi = (vs > 0 && !chain) ? 1u : v;  // items per block
+        block_scan(vi, e0, t0);
         const uint32_t carry = s_carry;
         if (w < n_work) {
-            const uint32_t e = carry + s_off[wid] + x - v;
-            seg_base[w] = e;
-            item_base[w] = e * nb;
+            item_base[w] = (carry + e0) * nb;
+            slot_base[w] = chain ? (uint32_t)first : (vs > 0 ? kNoSlot : 0u);
+            if (chain) atomicMax(&s_used, (uint32_t)(first + vs));
+            if (vs > 0 && !chain) atomicAdd(&s_alone, 1u);
         }
         __syncthreads();
-        if (threadIdx.x == 0) s_carry = carry + s_tot;
+        if (threadIdx.x == 0) {
+            s_carry = carry + t0;
+            s_carry2 = s_carry2 + t1;
+        }
         __syncthreads();
     }
-    const uint32_t total_segs = s_carry;
-    const bool ok = (int64_t)total_segs * nb * (kStateBytes + 8) <= capacity * 8;
+    const uint32_t used = s_used;
     if (threadIdx.x == 0) {
-        seg_base[n_work] = total_segs;
-        item_base[n_work] = total_segs * nb;
-        table[0] = ok ? 1u : 0u;
+        item_base[n_work] = s_carry * nb;
+        slot_base[n_work] = used;
+        table[2 * n_work + 3] = s_alone;
+        table[2 * n_work + 4] = max_slots;
+        table[0] = 1u;
     }
-    if (ok) {  // arrival counters and ready flags of every (segment, block)
-        uint32_t *words = (uint32_t *)(store + (size_t)total_segs * nb * kStateBytes);
-        for (uint32_t t = threadIdx.x; t < 2 * total_segs * nb; t += blockDim.x) words[t] = 0u;
+    // arrival counters and ready flags of the slots in use
+    uint32_t *counters = table + tbl + (size_t)max_slots * nb * 32, *ready = counters + (size_t)max_slots * nb;
+    for (uint32_t t = threadIdx.x; t < used * nb; t += blockDim.x) {
+        counters[t] = 0u;
+        ready[t] = 0u;
     }
 }
 
@@ -186,30 +230,31 @@ __device__ __forceinline__ void fresh_state(PixState &s, bool inside) {
     s.done = !inside;
 }
 
-// per-lane state words, word-major ([word][lane]: coalesced), through L2
-__device__ __forceinline__ void load_state(const float *src, int lane, PixState &s) {
-    s.T = __ldcg(src + 0 * 32 + lane);
-    s.c0 = __ldcg(src + 1 * 32 + lane);
-    s.c1 = __ldcg(src + 2 * 32 + lane);
-    s.c2 = __ldcg(src + 3 * 32 + lane);
-    s.n0 = __ldcg(src + 4 * 32 + lane);
-    s.n1 = __ldcg(src + 5 * 32 + lane);
-    s.n2 = __ldcg(src + 6 * 32 + lane);
-    s.D = __ldcg(src + 7 * 32 + lane);
-    const uint32_t w = __float_as_uint(__ldcg(src + 8 * 32 + lane));
+// per-lane state words, word-major ([word][lane]: coalesced), through L2:
+// the floats in fs, the word 'last | done << 31' in ls
+__device__ __forceinline__ void load_state(const float *fs, const uint32_t *ls, int lane, PixState &s) {
+    s.T = __ldcg(fs + 0 * 32 + lane);
+    s.c0 = __ldcg(fs + 1 * 32 + lane);
+    s.c1 = __ldcg(fs + 2 * 32 + lane);
+    s.c2 = __ldcg(fs + 3 * 32 + lane);
+    s.n0 = __ldcg(fs + 4 * 32 + lane);
+    s.n1 = __ldcg(fs + 5 * 32 + lane);
+    s.n2 = __ldcg(fs + 6 * 32 + lane);
+    s.D = __ldcg(fs + 7 * 32 + lane);
+    const uint32_t w = __ldcg(ls + lane);
     s.last = w & ~kDoneBit;
     s.done = (w & kDoneBit) != 0u;
 }
-__device__ __forceinline__ void store_state(float *dst, int lane, const PixState &s) {
-    __stcg(dst + 0 * 32 + lane, s.T);
-    __stcg(dst + 1 * 32 + lane, s.c0);
-    __stcg(dst + 2 * 32 + lane, s.c1);
-    __stcg(dst + 3 * 32 + lane, s.c2);
-    __stcg(dst + 4 * 32 + lane, s.n0);
-    __stcg(dst + 5 * 32 + lane, s.n1);
-    __stcg(dst + 6 * 32 + lane, s.n2);
-    __stcg(dst + 7 * 32 + lane, s.D);
-    __stcg(dst + 8 * 32 + lane, __uint_as_float(s.last | (s.done ? kDoneBit : 0u)));
+__device__ __forceinline__ void store_state(float *fs, uint32_t *ls, int lane, const PixState &s) {
+    __stcg(fs + 0 * 32 + lane, s.T);
+    __stcg(fs + 1 * 32 + lane, s.c0);
+    __stcg(fs + 2 * 32 + lane, s.c1);
+    __stcg(fs + 3 * 32 + lane, s.c2);
+    __stcg(fs + 4 * 32 + lane, s.n0);
+    __stcg(fs + 5 * 32 + lane, s.n1);
+    __stcg(fs + 6 * 32 + lane, s.n2);
+    __stcg(fs + 7 * 32 + lane, s.D);
+    __stcg(ls + lane, s.last | (s.done ? kDoneBit : 0u));
 }
 
 // Bits of the 8 x 4 block (bit 8y + x) covered by the block-relative
@@ -443,29 +488,31 @@ __device__ __forceinline__ void combine(PixState &cur, const PixState &ag, uint3
 template <int BT>
 __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ work,
-    uint32_t *__restrict__ work_counter, const uint32_t *__restrict__ table, char *__restrict__ store,
+    uint32_t *__restrict__ work_counter, uint32_t *__restrict__ table, char *__restrict__ store,
     const float4 *__restrict__ xy_depth, const float4 *__restrict__ conic_op, const ushort4 *__restrict__ rect,
     const float4 *__restrict__ rgb, const float4 *__restrict__ normal, float *__restrict__ out_rgb,
     float *__restrict__ out_nrm, float *__restrict__ out_depth, float *__restrict__ out_alpha,
     uint32_t *__restrict__ out_last, unsigned long long *__restrict__ pair_count, __grid_constant__ const Views P) {
     constexpr int NBX = BT / kBW, NB = blocks_of(BT);
-    constexpr int SW = kStateWords * 32;  // state floats of one (segment, block)
+    constexpr int SW = kStateFloats * 32;  // state floats of one (slot, block)
     const int lane = threadIdx.x & 31;
     const int lx = lane % kBW, ly = lane / kBW;
     const float lxf = (float)lx, lyf = (float)ly;
     const float tmin = P.t_min;
     const uint32_t n_work = work[0];
     constexpr uint32_t S = seg_len(BT);
-    // chained: one item per (tile, segment, block); otherwise one per
+    // chained: one item per (tile, segment, block) of the tiles with state
+    // slots, one per (tile, block) of the others; otherwise one per
     // (tile, block), whose warp runs the same segments in turn
     const bool chained = table && table[0] == 1u;
     const uint32_t *item_base = chained ? table + 1 : nullptr;
-    const uint32_t *seg_base = chained ? table + 2 + n_work : nullptr;
+    const uint32_t *slot_base = chained ? table + 2 + n_work : nullptr;
     const uint32_t total = chained ? item_base[n_work] : n_work * (uint32_t)NB;
-    const uint32_t total_segs = chained ? seg_base[n_work] : 0u;
+    const uint32_t max_slots = chained ? table[2 * n_work + 4] : 0u;
     float *states = (float *)store;
-    uint32_t *counters = chained ? (uint32_t *)(store + (size_t)total_segs * NB * kStateBytes) : nullptr;
-    uint32_t *ready = chained ? counters + (size_t)total_segs * NB : nullptr;
+    uint32_t *lastw = chained ? table + tbl_words(n_work) : nullptr;
+    uint32_t *counters = chained ? lastw + (size_t)max_slots * NB * 32 : nullptr;
+    uint32_t *ready = chained ? counters + (size_t)max_slots * NB : nullptr;
     uint32_t pairs = 0;  // (pixel, splat) pairs this lane evaluated
 
     for (;;) {
@@ -487,8 +534,11 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
             w = item / (uint32_t)NB;
             local = item % (uint32_t)NB;
         }
-        const uint32_t seg = local / (uint32_t)NB;
-        const int blk = (int)(local % (uint32_t)NB);
+        // the tile's first state slot; kNoSlot: its blocks run alone
+        const uint32_t sbase = chained ? __ldg(slot_base + w) : kNoSlot;
+        const bool tch = sbase != kNoSlot;
+        const uint32_t seg = tch ? local / (uint32_t)NB : 0u;
+        const int blk = (int)(tch ? local % (uint32_t)NB : local);
         const int64_t tile = work[2 + w];
         const int vi = view_of_tile(P, tile);
         const View &V = P.v[vi];
@@ -519,13 +569,14 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
         sa.tmin = P.t_min;
         auto seg_lo = [&](uint32_t si) { return r.x + si * S; };
         auto seg_hi = [&](uint32_t si) { return min(r.y, r.x + (si + 1) * S); };
-        // (segment, block) index of the chain's bookkeeping
-        auto sidx = [&](uint32_t si) -> size_t { return ((size_t)__ldg(seg_base + w) + si) * NB + blk; };
+        // (state slot, block) index of the chain's bookkeeping (tiles of
+        // two or more segments only)
+        auto sidx = [&](uint32_t si) -> size_t { return ((size_t)sbase + si) * NB + blk; };
 
         PixState cur;       // the inclusive state through segment m
         uint32_t m = seg;
         fresh_state(cur, inside);
-        if (!chained) {
+        if (!tch) {
             // the chain in one warp: segment 0 exact, every later one
             // speculated from T = 1 and combined, as the chained schedule does
             composite_segment(true, seg_lo(0), seg_hi(0), sa, cur, pairs, nullptr);
@@ -545,7 +596,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
             PixState pr;
             fresh_state(pr, inside);
             bool known = __all_sync(0xffffffffu, ld_acquire_u32(ready + pi) != 0u);
-            if (known) load_state(states + pi * SW, lane, pr);
+            if (known) load_state(states + pi * SW, lastw + pi * 32, lane, pr);
             // pixels the predecessor shows done, or whose stop it shows to lie
             // in the part already walked, drop out (their result no longer
             // depends on this aggregate; the latter publish T = 0)
@@ -557,32 +608,32 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
             const uint32_t reached = composite_segment(false, s0, s1, sa, ag, pairs, known ? nullptr : ready + pi);
             if (!known && reached < s1) {
                 (void)ld_acquire_u32(ready + pi);
-                load_state(states + pi * SW, lane, pr);
+                load_state(states + pi * SW, lastw + pi * 32, lane, pr);
                 rewalk = !pr.done && !ag.done && pr.T * ag.T < tmin;
                 ag.done = ag.done || pr.done || rewalk;
                 composite_segment(false, reached, s1, sa, ag, pairs, nullptr);
             }
             if (rewalk) ag.T = 0.f;
             const size_t si = sidx(seg);
-            store_state(states + si * SW, lane, ag);
+            store_state(states + si * SW, lastw + si * 32, lane, ag);
             // the second to arrive (this aggregate or the predecessor's
             // inclusive state) continues the chain
             if (arrive(counters + si, lane) == 0u) continue;
-            load_state(states + pi * SW, lane, cur);  // the predecessor's inclusive state
+            load_state(states + pi * SW, lastw + pi * 32, lane, cur);  // the predecessor's inclusive state
             combine(cur, ag, s0, s1, sa, pairs);
         }
         // publish the chain forward: while the successor's aggregate is
         // already stored, combine it too
-        while (chained && m + 1 < nseg) {
+        while (tch && m + 1 < nseg) {
             const size_t mi = sidx(m);
-            store_state(states + mi * SW, lane, cur);
+            store_state(states + mi * SW, lastw + mi * 32, lane, cur);
             __threadfence();
             __syncwarp();
             if (lane == 0) st_release_u32(ready + mi, kIncl);  // polled by the successor
             const size_t ni = sidx(m + 1);
             if (arrive(counters + ni, lane) == 0u) break;  // the successor continues
             PixState ag;
-            load_state(states + ni * SW, lane, ag);
+            load_state(states + ni * SW, lastw + ni * 32, lane, ag);
             ++m;
             combine(cur, ag, seg_lo(m), seg_hi(m), sa, pairs);
         }
@@ -675,15 +726,16 @@ static cudaError_t launch_blend(const p2e_gaussians *g, const p2e_projected *pro
     fill_empty_kernel<<<sms * 8, 256, 0, st>>>((const uint2 *)bins->ranges, total_pix, rgb, nrm, depth,
                                                alpha, last, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // segment chaining: tables in vals[1 - result], states, counters and
-    // flags in keys[1 - result] (decided on the device by the item table)
+    // segment chaining: the item table, the state words 'last | done',
+    // counters and flags in vals[1 - result], the state floats in
+    // keys[1 - result] (decided on the device by the item table)
     const int other = 1 - bins->result;
     const bool allow = bins->capacity > 0 && bins->keys[other] && bins->vals[other];
     uint32_t *table = allow ? bins->vals[other] : nullptr;
     char *store = allow ? (char *)bins->keys[other] : nullptr;
     if (allow) {
         render_items_kernel<<<1, 1024, 0, st>>>((const uint2 *)bins->ranges, bins->tile_work, bins->n_keys_dev,
-                                                bins->capacity, 1, BT, table, store);
+                                                bins->capacity, P.schedule == P2E_SCHEDULE_AUTO ? 1 : 0, BT, table);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int64_t grid = (int64_t)sms * per_sm[slot];

@@ -75,6 +75,7 @@ static p2e_status fill_views(const p2e_camera *cams, int32_t n_views, const p2e_
         return P2E_ERR_INVALID_ARG;
     for (int c = 0; c < 3; ++c)
         if (!fin(cfg->bg[c])) return P2E_ERR_INVALID_ARG;
+    if (cfg->schedule != P2E_SCHEDULE_AUTO && cfg->schedule != P2E_SCHEDULE_PER_BLOCK) return P2E_ERR_INVALID_ARG;
     memset(&P, 0, sizeof(P));
     P.n_views = n_views;
     P.tile = cfg->tile;
@@ -84,6 +85,7 @@ static p2e_status fill_views(const p2e_camera *cams, int32_t n_views, const p2e_
     P.alpha_max = cfg->alpha_max;
     P.t_min = cfg->t_min;
     for (int c = 0; c < 3; ++c) P.bg[c] = cfg->bg[c];
+    P.schedule = cfg->schedule;
     P.n = n;
     int64_t tb = 0, pb = 0;
     for (int v = 0; v < n_views; ++v) {
@@ -140,6 +142,7 @@ p2e_config p2e_default_config(void) {
     c.lowpass = 0.3f;
     c.sigma_mult = 3.0f;
     c.bg[0] = c.bg[1] = c.bg[2] = 0.0f;
+    c.schedule = P2E_SCHEDULE_AUTO;
     return c;
 }
 

@@ -25,6 +25,7 @@ struct Views {
     float lowpass, sigma_mult;
     float alpha_floor, alpha_max, t_min;
     float bg[3];
+    int32_t schedule;    // P2E_SCHEDULE_*
     int64_t n;           // Gaussians per view
     int64_t total_tiles;
     View v[P2E_MAX_VIEWS];

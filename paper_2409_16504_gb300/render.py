@@ -18,7 +18,7 @@ from . import _lib
 from ._lib import P2EBins, P2ECamera, P2EConfig, P2EGaussians, P2EProjected, check
 
 DEFAULT_CONFIG = dict(tile=16, alpha_floor=1.0 / 255.0, alpha_max=0.99, t_min=1e-4, lowpass=0.3,
-                      sigma_mult=3.0, bg=(0.0, 0.0, 0.0))
+                      sigma_mult=3.0, bg=(0.0, 0.0, 0.0), schedule=0)
 
 
 def _ptr(t: torch.Tensor | None):
@@ -41,6 +41,7 @@ def make_config(cfg: dict | None = None) -> P2EConfig:
     out.sigma_mult = c["sigma_mult"]
     for i in range(3):
         out.bg[i] = float(c["bg"][i])
+    out.schedule = int(c.get("schedule", 0))
     return out
 
 

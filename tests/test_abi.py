@@ -41,7 +41,7 @@ def test_host_helpers_without_gpu():
 def test_struct_layouts_match_header():
     # sizes of the POD structs as a C compiler lays them out
     assert C.sizeof(_lib.P2ECamera) == 4 * 12 + 4 * 4 + 4 * 2 + 4
-    assert C.sizeof(_lib.P2EConfig) == 4 + 5 * 4 + 3 * 4
+    assert C.sizeof(_lib.P2EConfig) == 4 + 5 * 4 + 3 * 4 + 4
     assert C.sizeof(_lib.P2EGaussians) == 5 * 8 + 8
     assert C.sizeof(_lib.P2EBins) == 2 * 8 + 2 * 8 + 8 + 8 + 8 + 8 + 8 + 8 + 8 + 8
     assert C.sizeof(_lib.P2EKernelProbe) == 3 * 8

@@ -168,27 +168,127 @@ def test_full_size_humanoid_800k_1024():
     print("800K max errors", errs)
 
 
+def _chain_info(r):
+    """(chained schedule in use, multi-segment tiles run by one warp per
+    block) from the item table the compositing leaves in the free value
+    buffer: word 0 and word 2 n_work + 3."""
+    v = r.bins.vals[1 - r.bins.struct.result]
+    n_work = int(r.bins.tile_work[0].item())
+    return int(v[0].item()), int(v[2 * n_work + 3].item())
+
+
 def test_segment_chains_schedule_independent():
     """Long tile lists are split into segments combined by the 'over' rule.
-    Chained across warps (states in the free key buffer) or run by one warp
-    per pixel block (capacity too small for the states) the arithmetic is
-    the same: the images are bit-identical."""
+    Chained across warps (states in the free key buffers) or run by one warp
+    per pixel block (P2E_SCHEDULE_PER_BLOCK): the arithmetic is the same,
+    the images are bit-identical."""
     from paper_2409_16504_gb300 import GaussianSet, Renderer
     g, cam = humanoid_scene(300_000, 1024, 1024, seed=4)
     gs = GaussianSet.from_numpy(g)
     big = Renderer(capacity=1 << 22)
     a = big.render(gs, [cam])
-    k = big.n_keys
     lengths = (big.bins.ranges.view(-1, 2)[:, 1] - big.bins.ranges.view(-1, 2)[:, 0]).cpu().numpy()
-    assert lengths.max() > 4 * 1024  # several segments per tile
-    tight = Renderer(capacity=k)    # no room for the segment states
-    b = tight.render(gs, [cam])
+    assert lengths.max() > 3 * 1024  # several segments per tile
+    one = Renderer({"schedule": 1}, capacity=1 << 22)
+    b = one.render(gs, [cam])
     torch.cuda.synchronize()
-    # the free half of the key buffers holds the schedule word: 1 chained, 0 not
-    mode = lambda r: int(r.bins.vals[1 - r.bins.struct.result][0].item())  # noqa: E731
-    assert mode(big) == 1 and mode(tight) == 0
+    assert _chain_info(big) == (1, 0)
+    assert _chain_info(one)[0] == 0
     for key in ("rgb", "normal", "depth", "alpha", "last"):
         assert torch.equal(getattr(a, key), getattr(b, key)), key
+
+
+def test_chaining_mixed_tile_by_tile_when_states_run_short():
+    """A field of small splats whose tile lists all run just past one
+    segment: two state slots per tile need about twice the key count, so at
+    a capacity equal to the key count the longest tiles chain and the rest
+    run one warp per block, in the same launch; the images are
+    bit-identical to both pure schedules."""
+    import scenes
+    from paper_2409_16504_gb300 import GaussianSet, Renderer
+    rng = np.random.default_rng(11)
+    n, W = 240_000, 256
+    cam = scenes.look_at_camera((0.0, 0.0, -2.0), (0, 0, 0), (0, 1, 0), 55, W, W)
+    mean = np.stack([rng.uniform(-1.0, 1.0, n), rng.uniform(-1.0, 1.0, n), rng.uniform(-0.05, 0.05, n)], 1)
+    g = dict(mean=mean.astype(np.float32),
+             scale=np.full((n, 3), 0.004, np.float32),
+             quat=rng.standard_normal((n, 4)).astype(np.float32),
+             opacity=rng.uniform(0.05, 0.4, n).astype(np.float32),
+             rgb=rng.random((n, 3)).astype(np.float32),
+             normal=rng.standard_normal((n, 3)).astype(np.float32))
+    gs = GaussianSet.from_numpy(g)
+    big = Renderer(capacity=1 << 21)
+    a = big.render(gs, [cam])
+    torch.cuda.synchronize()
+    k = big.n_keys
+    lengths = (big.bins.ranges.view(-1, 2)[:, 1] - big.bins.ranges.view(-1, 2)[:, 0]).cpu().numpy()
+    multi = lengths[lengths > 1024]
+    need = int(np.ceil(multi / 1024.0).sum()) * 1024
+    assert need > 1.1 * k, (need, k)  # the scene must make the states run short
+    mixed = Renderer(capacity=k)
+    b = mixed.render(gs, [cam])
+    one = Renderer({"schedule": 1}, capacity=1 << 21)
+    c = one.render(gs, [cam])
+    torch.cuda.synchronize()
+    assert _chain_info(big) == (1, 0)
+    ch, alone = _chain_info(mixed)
+    assert ch == 1 and 0 < alone < len(multi), (ch, alone, len(multi))
+    print(f"mixed schedule: {len(multi) - alone} of {len(multi)} multi-segment tiles chained, {k} keys")
+    for key in ("rgb", "normal", "depth", "alpha", "last"):
+        assert torch.equal(getattr(a, key), getattr(b, key)), key
+        assert torch.equal(getattr(a, key), getattr(c, key)), key
+
+
+def test_very_long_tile_list_chains():
+    """One 16 x 16 tile holding 300K faint splats (the stop rule never
+    fires, so every one of its 293 segments is walked and chained): the
+    chained images are bit-identical to one warp per block."""
+    import scenes
+    from paper_2409_16504_gb300 import GaussianSet, Renderer
+    rng = np.random.default_rng(5)
+    n = 300_000
+    cam = scenes.look_at_camera((0.0, 0.0, -2.0), (0, 0, 0), (0, 1, 0), 55, 16, 16)
+    mean = np.stack([rng.uniform(-1.0, 1.0, n), rng.uniform(-1.0, 1.0, n), rng.uniform(-0.2, 0.2, n)], 1)
+    g = dict(mean=mean.astype(np.float32),
+             scale=np.full((n, 3), 0.04, np.float32),
+             quat=rng.standard_normal((n, 4)).astype(np.float32),
+             opacity=rng.uniform(0.004, 0.0055, n).astype(np.float32),  # above the floor near the centre only
+             rgb=rng.random((n, 3)).astype(np.float32),
+             normal=rng.standard_normal((n, 3)).astype(np.float32))
+    gs = GaussianSet.from_numpy(g)
+    a_r = Renderer(capacity=1 << 20)
+    a = a_r.render(gs, [cam])
+    b_r = Renderer({"schedule": 1}, capacity=1 << 20)
+    b = b_r.render(gs, [cam])
+    torch.cuda.synchronize()
+    assert a_r.n_keys > 257 * 1024, a_r.n_keys
+    assert _chain_info(a_r) == (1, 0) and _chain_info(b_r)[0] == 0
+    assert float((a.alpha < 0.9999).float().mean()) > 0.5  # most pixels stay open to the end of the list
+    for key in ("rgb", "normal", "depth", "alpha", "last"):
+        assert torch.equal(getattr(a, key), getattr(b, key)), key
+
+
+def test_chained_schedule_fits_at_the_benchmark_capacity():
+    """At the benchmark's key capacity (2x the first view's keys + 4096)
+    every multi-segment tile of the 800K-point humanoid's views chains, for
+    24 camera positions on the 2.5 m sphere."""
+    import scenes
+    from paper_2409_16504_gb300 import GaussianSet, Renderer
+    g, cam = humanoid_scene(800_000, 1024, 1024)
+    gs = GaussianSet.from_numpy(g)
+    c = np.asarray(g["mean"], np.float64).mean(0)
+    rng = np.random.default_rng(102)
+    cams = [scenes.sphere_camera(c, 2.5, rng, 1024, 1024) for _ in range(24)]
+    r = Renderer(capacity=1 << 21)
+    r.render(gs, [cams[0]])
+    r = Renderer(capacity=int(r.n_keys * 2.0) + 4096)
+    keys = []
+    for cam in cams:
+        r.render(gs, [cam])
+        torch.cuda.synchronize()
+        keys.append(r.n_keys)
+        assert _chain_info(r) == (1, 0), (r.n_keys, r.capacity, _chain_info(r))
+    print(f"keys per view {min(keys)} .. {max(keys)} at capacity {r.capacity}: all chained")
 
 
 def test_depth_first_and_full_key_binning_agree():
