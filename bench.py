@@ -70,9 +70,9 @@ FP32_LANES_PER_SM = 128
 _CSRC = "paper_2409_16504_gb300/csrc/"
 NCU_TRAFFIC = {
     "knn": {"kernel": "knn_pca_kernel", "sources": [_CSRC + "estimate.cu"],
-            "sha256_16": None, "bytes": None},
+            "sha256_16": "e47fe60e0257de70", "bytes": 284_631_000},
     "blend": {"kernel": "blend_kernel<16>", "sources": [_CSRC + "blend.cu", _CSRC + "splat.cuh"],
-              "sha256_16": None, "bytes": None},
+              "sha256_16": "3bff24cf89d2e0e6", "bytes": 253_313_000},
     "mlp": {"kernel": "mlp_estimate_kernel", "sources": [_CSRC + "mlp.cu", _CSRC + "tcgen05.cuh"],
             "sha256_16": "7d49e064b1b85464", "bytes": 135_280_000},
 }

@@ -247,8 +247,11 @@ p2e_status p2e_bins_check(const p2e_bins *io, int64_t *n_keys_host, void *stream
  * vals[1 - result], is overwritten (the work-item table, per-segment
  * compositing states, arrival counters and flags); the sorted
  * keys/vals[result] are left intact.
- * Device waits are bounded; one that gives up sets *bins->status_dev to
- * P2E_ERR_TIMEOUT (reported by p2e_bins_check). */
+ * Device waits are bounded (the chained schedule's warps wait for deferred
+ * re-walks of other warps' segments); one that gives up sets
+ * *bins->status_dev to P2E_ERR_TIMEOUT, which p2e_bins_check reports when
+ * called after p2e_render (the next p2e_sort_bin clears it).  With
+ * bins->status_dev NULL the one-warp-per-block schedule runs. */
 p2e_status p2e_render(const p2e_gaussians *g, const p2e_projected *proj, const p2e_bins *bins,
                       const p2e_camera *cams, int32_t n_views, const p2e_config *cfg,
                       float *rgb, float *normal, float *depth, float *alpha, uint32_t *last,
@@ -446,7 +449,10 @@ p2e_status p2e_estimate_check(const void *scratch, int64_t scratch_bytes, int64_
  *            published: the next tile's decoupled look-back gives up;
  *         1  the cell-count scan of p2e_estimate, likewise;
  *         2  the learned head's mbarrier wait for an MMA completion that is
- *            never issued.
+ *            never issued;
+ *         3  p2e_render's wait for the deferred re-walks of its CTA, with
+ *            a CTA that never leaves its item;
+ *         4  the lock of that re-walk queue, held and never released.
  *   spin_limit  wait rounds before giving up, 1 .. 2^22 (the library's
  *            own default limit is 2^22 rounds, a few hundred ms).
  *   scratch  device, >= P2E_SELFTEST_SCRATCH_BYTES, 256-byte aligned.

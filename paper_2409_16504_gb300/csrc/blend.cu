@@ -90,7 +90,9 @@ struct PixState {
     float T, c0, c1, c2, n0, n1, n2, D;
     uint32_t last;
     bool done;
+    bool deferred;  // done, its output written by a deferred re-walk
 };
+constexpr uint32_t kDeferBit = 1u << 30;  // list positions stay below 2^30 when chained
 
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
     uint32_t v;
@@ -112,15 +114,16 @@ __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
 //                                  slots in use
 //     [2 n_work + 3]               multi-segment tiles run without chaining
 //     [2 n_work + 4]               max_slots: the slots the two buffers hold
-//     from tbl_words(n_work)       per (slot, block) 32 words 'last | done << 31',
-//                                  then max_slots x NB arrival counters, then as
-//                                  many ready flags
+//     from tbl_words(n_work)       per (slot, block) 32 words 'last | deferred << 30
+//                                  | done << 31', then max_slots x NB arrival
+//                                  counters and as many ready flags
 //   keys[1 - result] (floats):     per (slot, block) kStateFloats x 32 state floats
 //                                  (word-major)
 // A slot costs NB x 1 KB of the key buffer, i.e. 8 bytes per key of its
 // segment: the key buffer holds the states of every key it can hold.
 constexpr uint32_t kNoSlot = 0xffffffffu;
 __host__ __device__ inline int64_t tbl_words(uint32_t n_work) { return (2 * (int64_t)n_work + 5 + 31) & ~int64_t(31); }
+constexpr int kSlotWords = 32 + 1 + 1;  // value-buffer words per (slot, block)
 
 // Item table (one CTA).  Over the work list (longest tiles first), the
 // multi-segment tiles take state slots while they fit (a prefix of the
@@ -140,13 +143,13 @@ __global__ void __launch_bounds__(1024) render_items_kernel(const uint2 *__restr
     const uint32_t n_work = work[0];
     const uint32_t nb = (uint32_t)blocks_of(tile), S = seg_len(tile);
     const int64_t tbl = tbl_words(n_work);
-    const bool fits = allow_chain && *n_keys_dev <= capacity && tbl <= capacity;
+    const bool fits = allow_chain && *n_keys_dev <= capacity && tbl <= capacity && capacity < (int64_t(1) << 30);
     if (!fits) {
         if (threadIdx.x == 0 && capacity > 0) table[0] = 0u;
         return;
     }
     const int64_t ms = min(capacity * 8 / ((int64_t)nb * 32 * kStateFloats * 4),  // key buffer (bytes)
-                           (capacity - tbl) / ((int64_t)nb * 34));                // value buffer (words)
+                           (capacity - tbl) / ((int64_t)nb * kSlotWords));        // value buffer (words)
     const uint32_t max_slots = (uint32_t)min(ms, (int64_t)0x7fffffff);
     uint32_t *item_base = table + 1, *slot_base = table + 2 + n_work;
     if (threadIdx.x == 0) s_carry = s_carry2 = s_used = s_alone = 0;
@@ -228,6 +231,7 @@ __device__ __forceinline__ void fresh_state(PixState &s, bool inside) {
     s.c0 = s.c1 = s.c2 = s.n0 = s.n1 = s.n2 = s.D = 0.f;
     s.last = 0u;
     s.done = !inside;
+    s.deferred = false;
 }
 
 // per-lane state words, word-major ([word][lane]: coalesced), through L2:
@@ -242,8 +246,9 @@ __device__ __forceinline__ void load_state(const float *fs, const uint32_t *ls, 
     s.n2 = __ldcg(fs + 6 * 32 + lane);
     s.D = __ldcg(fs + 7 * 32 + lane);
     const uint32_t w = __ldcg(ls + lane);
-    s.last = w & ~kDoneBit;
+    s.last = w & ~(kDoneBit | kDeferBit);
     s.done = (w & kDoneBit) != 0u;
+    s.deferred = (w & kDeferBit) != 0u;
 }
 __device__ __forceinline__ void store_state(float *fs, uint32_t *ls, int lane, const PixState &s) {
     __stcg(fs + 0 * 32 + lane, s.T);
@@ -254,7 +259,7 @@ __device__ __forceinline__ void store_state(float *fs, uint32_t *ls, int lane, c
     __stcg(fs + 5 * 32 + lane, s.n1);
     __stcg(fs + 6 * 32 + lane, s.n2);
     __stcg(fs + 7 * 32 + lane, s.D);
-    __stcg(ls + lane, s.last | (s.done ? kDoneBit : 0u));
+    __stcg(ls + lane, s.last | (s.done ? kDoneBit : 0u) | (s.deferred ? kDeferBit : 0u));
 }
 
 // Bits of the 8 x 4 block (bit 8y + x) covered by the block-relative
@@ -464,18 +469,130 @@ __device__ __forceinline__ uint32_t arrive(uint32_t *counter, int lane) {
     return old;
 }
 
+// Deferred re-walks.  Where the stop of some pixels of a block falls
+// inside a segment, the chained schedule does not re-walk the segment on
+// the chain (whose links are then serial re-walks through most of a long
+// list of faint splats): the pixels are marked done and deferred, the
+// chain carries on, and the re-walk goes to its CTA's task queue, which the
+// CTA's warps drain once the items run out.  A task re-walks the segment with the stop rule from the
+// predecessor's inclusive state (kept in its slot) and writes its pixels'
+// outputs: the same arithmetic as a re-walk on the chain.  Only a pixel
+// whose stop falls inside for certain is deferred (T_in T_s below t_min by
+// a 0.1 % margin, far above the rounding of the products of one segment),
+// so the re-walk stops inside the segment.  The queue lives in shared
+// memory (no global polling); its lock is held for a few instructions and
+// every wait on it is bounded.
+constexpr float kDeferMargin = 0.999f;
+constexpr int kCtaTasks = 64;
+struct CtaQueue {
+    uint32_t lock, head, tail, busy;  // busy: warps of the CTA inside an item
+    uint4 task[kCtaTasks];            // work entry, segment, block, pixel mask
+};
+
+__device__ __forceinline__ bool cq_lock(CtaQueue *q, uint32_t limit) {
+    uint32_t s = 0;
+    while (atomicCAS(&q->lock, 0u, 1u) != 0u) {
+        if (++s > limit) return false;
+        __nanosleep(32);
+    }
+    __threadfence_block();
+    return true;
+}
+__device__ __forceinline__ void cq_unlock(CtaQueue *q) {
+    __threadfence_block();
+    atomicExch(&q->lock, 0u);
+}
+// lane 0 only; false when the queue is full (or the lock was not had)
+__device__ __forceinline__ bool cq_push(CtaQueue *q, uint4 t, uint32_t limit) {
+    if (!cq_lock(q, limit)) return false;
+    volatile CtaQueue *v = q;
+    const bool ok = v->tail - v->head < (uint32_t)kCtaTasks;
+    if (ok) {
+        v->task[v->tail % kCtaTasks].x = t.x;
+        v->task[v->tail % kCtaTasks].y = t.y;
+        v->task[v->tail % kCtaTasks].z = t.z;
+        v->task[v->tail % kCtaTasks].w = t.w;
+        v->tail = v->tail + 1u;
+    }
+    cq_unlock(q);
+    return ok;
+}
+// lane 0 only: 1 a task taken, 0 the queue empty, -1 the lock was not had.
+// An empty queue is seen without the lock.
+__device__ __forceinline__ int cq_pop(CtaQueue *q, uint4 &t, uint32_t limit) {
+    if (((volatile CtaQueue *)q)->head == ((volatile CtaQueue *)q)->tail) return 0;
+    if (!cq_lock(q, limit)) return -1;
+    volatile CtaQueue *v = q;
+    const bool ok = v->head < v->tail;
+    if (ok) {
+        t = make_uint4(v->task[v->head % kCtaTasks].x, v->task[v->head % kCtaTasks].y,
+                       v->task[v->head % kCtaTasks].z, v->task[v->head % kCtaTasks].w);
+        v->head = v->head + 1u;
+    }
+    cq_unlock(q);
+    return ok ? 1 : 0;
+}
+
+// Runs the CTA's queued re-walks (take: 1 one was run, 0 none queued, -1
+// the queue's lock was not had) until none is queued and no warp of the
+// CTA is inside an item (only those queue re-walks).  Every wait is
+// bounded: after `limit` rounds it records P2E_ERR_TIMEOUT and returns.
+template <typename Take>
+__device__ __forceinline__ void drain_queue(CtaQueue *q, uint32_t limit, int32_t *status, Take &&take) {
+    const int lane = threadIdx.x & 31;
+    uint32_t spins = 0;
+    for (;;) {
+        const int got = take();
+        if (got > 0) {
+            spins = 0;
+            continue;
+        }
+        if (got < 0) break;
+        uint32_t idle = 0;
+        if (lane == 0) idle = atomicAdd(&q->busy, 0u) == 0u ? 1u : 0u;
+        if (__shfl_sync(0xffffffffu, idle, 0)) {
+            if (take() > 0) continue;  // queued before the last item ended
+            break;
+        }
+        if (++spins > limit) {
+            if (lane == 0) atomicExch(status, (int32_t)P2E_ERR_TIMEOUT);
+            break;
+        }
+        __nanosleep(spins < 5 ? 32u << spins : 1024u);
+    }
+}
+
 // The inclusive state after a segment, from the state before it (cur) and
 // the segment's aggregate (ag: composited from T = 1 without stopping):
 // fold C = C_in + T_in C_s, T = T_in T_s, unless the stop falls inside the
 // segment (T_in T_s < t_min; T is non-increasing): then the segment is
-// re-walked from the true state with the stop rule.  An aggregate with
-// T = 0 marks a pixel whose stop is already known to fall inside.
+// re-walked from the true state with the stop rule, here or (q != NULL,
+// when the CTA's queue has room) by a deferred task for work entry w,
+// segment seg, block blk.  An aggregate with T = 0 marks a pixel whose stop is
+// already known to fall inside.
 __device__ __forceinline__ void combine(PixState &cur, const PixState &ag, uint32_t s0, uint32_t s1,
-                                        const SegArgs &a, uint32_t &pairs) {
-    bool rw = false;
+                                        const SegArgs &a, uint32_t &pairs, CtaQueue *q, uint32_t limit,
+                                        uint32_t w, uint32_t seg, int blk) {
+    const int lane = threadIdx.x & 31;
+    bool rw = false, df = false;
     if (!cur.done) {
-        if (cur.T * ag.T >= a.tmin) cur = fold(cur, ag);
+        const float tt = cur.T * ag.T;
+        if (tt >= a.tmin) cur = fold(cur, ag);
+        else if (q && tt < a.tmin * kDeferMargin) df = true;
         else rw = true;
+    }
+    const uint32_t dm = __ballot_sync(0xffffffffu, df);
+    if (dm) {
+        uint32_t ok = 0;
+        if (lane == 0) ok = cq_push(q, make_uint4(w, seg, (uint32_t)blk, dm), limit) ? 1u : 0u;
+        if (__shfl_sync(0xffffffffu, ok, 0)) {
+            if (df) {
+                cur.done = true;
+                cur.deferred = true;
+            }
+        } else {
+            rw = rw || df;  // no room in the queue: re-walk here
+        }
     }
     if (__any_sync(0xffffffffu, rw)) {
         PixState x = cur;
@@ -492,7 +609,8 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
     const float4 *__restrict__ xy_depth, const float4 *__restrict__ conic_op, const ushort4 *__restrict__ rect,
     const float4 *__restrict__ rgb, const float4 *__restrict__ normal, float *__restrict__ out_rgb,
     float *__restrict__ out_nrm, float *__restrict__ out_depth, float *__restrict__ out_alpha,
-    uint32_t *__restrict__ out_last, unsigned long long *__restrict__ pair_count, __grid_constant__ const Views P) {
+    uint32_t *__restrict__ out_last, unsigned long long *__restrict__ pair_count, int32_t *__restrict__ status,
+    uint32_t spin_limit, __grid_constant__ const Views P) {
     constexpr int NBX = BT / kBW, NB = blocks_of(BT);
     constexpr int SW = kStateFloats * 32;  // state floats of one (slot, block)
     const int lane = threadIdx.x & 31;
@@ -513,13 +631,102 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
     uint32_t *lastw = chained ? table + tbl_words(n_work) : nullptr;
     uint32_t *counters = chained ? lastw + (size_t)max_slots * NB * 32 : nullptr;
     uint32_t *ready = chained ? counters + (size_t)max_slots * NB : nullptr;
+    __shared__ CtaQueue s_q;  // this CTA's deferred re-walks
+    if (threadIdx.x == 0) s_q.lock = s_q.head = s_q.tail = s_q.busy = 0u;
+    __syncthreads();
+    CtaQueue *const cq = &s_q;
     uint32_t pairs = 0;  // (pixel, splat) pairs this lane evaluated
 
-    for (;;) {
-        uint32_t item = 0;
-        if (lane == 0) item = atomicAdd(work_counter, 1u);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= total) break;
+    // what one (work entry, pixel block) needs
+    struct Block {
+        const View *V;
+        int px, py;
+        bool inside;
+        uint2 r;
+        uint32_t nseg;
+        SegArgs sa;
+    };
+    auto block_of = [&](uint32_t w, int blk, Block &b) {
+        const int64_t tile = work[2 + w];
+        const int vi = view_of_tile(P, tile);
+        const View &V = P.v[vi];
+        const int64_t ltile = tile - V.tile_base;
+        const int ty = (int)(ltile / V.tiles_x), tx = (int)(ltile - (int64_t)ty * V.tiles_x);
+        const int x0 = tx * BT + (blk % NBX) * kBW, y0 = ty * BT + (blk / NBX) * kBH;
+        b.V = &V;
+        b.px = x0 + lx;
+        b.py = y0 + ly;
+        b.inside = b.px < V.W && b.py < V.H;
+        b.r = ranges[tile];
+        b.nseg = (b.r.y - b.r.x + S - 1) / S;
+        SegArgs &sa = b.sa;
+        sa.vals = vals;
+        sa.xy_depth = xy_depth;
+        sa.conic_op = conic_op;
+        sa.rect = rect;
+        sa.rgb = rgb;
+        sa.normal = normal;
+        sa.gbase = (int64_t)vi * P.n;
+        sa.x0 = x0;
+        sa.y0 = y0;
+        sa.lxf = lxf;
+        sa.lyf = lyf;
+        sa.n = (uint32_t)P.n;
+        sa.pw_min = -0.5f * P.sigma_mult * P.sigma_mult;
+        sa.amax = P.alpha_max;
+        sa.afloor = P.alpha_floor;
+        sa.tmin = P.t_min;
+    };
+    auto write_pixel = [&](const Block &b, const PixState &cur) {
+        const View &V = *b.V;
+        const int64_t HW = (int64_t)V.H * V.W;
+        const int64_t p = (int64_t)b.py * V.W + b.px;
+        if (out_rgb) {
+            float *o = out_rgb + 3 * V.pix_base + p;
+            o[0] = fmaf(cur.T, P.bg[0], cur.c0);
+            o[HW] = fmaf(cur.T, P.bg[1], cur.c1);
+            o[2 * HW] = fmaf(cur.T, P.bg[2], cur.c2);
+        }
+        if (out_nrm) {
+            float *o = out_nrm + 3 * V.pix_base + p;
+            o[0] = cur.n0;
+            o[HW] = cur.n1;
+            o[2 * HW] = cur.n2;
+        }
+        if (out_depth) out_depth[V.pix_base + p] = cur.D;
+        if (out_alpha) out_alpha[V.pix_base + p] = 1.f - cur.T;
+        if (out_last) out_last[V.pix_base + p] = cur.last;
+    };
+
+    // Takes one re-walk from the CTA's queue and runs it: 1 done, 0 none
+    // queued, -1 the queue's lock was not had (status recorded).
+    auto take_task = [&]() -> int {
+        uint4 tk = make_uint4(0u, 0u, 0u, 0u);
+        int got = 0;
+        if (lane == 0) got = cq_pop(cq, tk, spin_limit);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (got <= 0) {
+            if (got < 0 && lane == 0) atomicExch(status, (int32_t)P2E_ERR_TIMEOUT);
+            return got;
+        }
+        const uint32_t w = __shfl_sync(0xffffffffu, tk.x, 0), seg = __shfl_sync(0xffffffffu, tk.y, 0);
+        const int blk = (int)__shfl_sync(0xffffffffu, tk.z, 0);
+        const uint32_t mask = __shfl_sync(0xffffffffu, tk.w, 0);
+        Block b;
+        block_of(w, blk, b);
+        const size_t pi = ((size_t)__ldg(slot_base + w) + seg - 1) * NB + blk;
+        PixState x;
+        load_state(states + pi * SW, lastw + pi * 32, lane, x);
+        const bool mine = ((mask >> lane) & 1u) != 0u;
+        x.done = !mine;
+        x.deferred = false;
+        composite_segment(true, b.r.x + seg * S, min(b.r.y, b.r.x + (seg + 1) * S), b.sa, x, pairs, nullptr);
+        if (mine && b.inside) write_pixel(b, x);
+        return 1;
+    };
+
+    // one item: a (tile, segment, block), or a (tile, block) run alone
+    auto do_item = [&](uint32_t item) {
         uint32_t w, local;
         if (chained) {  // last work entry whose first item is <= item
             uint32_t lo = 0, hi = n_work;
@@ -539,41 +746,19 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
         const bool tch = sbase != kNoSlot;
         const uint32_t seg = tch ? local / (uint32_t)NB : 0u;
         const int blk = (int)(tch ? local % (uint32_t)NB : local);
-        const int64_t tile = work[2 + w];
-        const int vi = view_of_tile(P, tile);
-        const View &V = P.v[vi];
-        const int64_t ltile = tile - V.tile_base;
-        const int ty = (int)(ltile / V.tiles_x), tx = (int)(ltile - (int64_t)ty * V.tiles_x);
-        const int x0 = tx * BT + (blk % NBX) * kBW, y0 = ty * BT + (blk / NBX) * kBH;
-        const int px = x0 + lx, py = y0 + ly;
-        const bool inside = px < V.W && py < V.H;
-        const uint2 r = ranges[tile];
-        const int64_t gbase = (int64_t)vi * P.n;
-        const uint32_t nseg = (r.y - r.x + S - 1) / S;
-        SegArgs sa;
-        sa.vals = vals;
-        sa.xy_depth = xy_depth;
-        sa.conic_op = conic_op;
-        sa.rect = rect;
-        sa.rgb = rgb;
-        sa.normal = normal;
-        sa.gbase = gbase;
-        sa.x0 = x0;
-        sa.y0 = y0;
-        sa.lxf = lxf;
-        sa.lyf = lyf;
-        sa.n = (uint32_t)P.n;
-        sa.pw_min = -0.5f * P.sigma_mult * P.sigma_mult;
-        sa.amax = P.alpha_max;
-        sa.afloor = P.alpha_floor;
-        sa.tmin = P.t_min;
-        auto seg_lo = [&](uint32_t si) { return r.x + si * S; };
-        auto seg_hi = [&](uint32_t si) { return min(r.y, r.x + (si + 1) * S); };
+        Block b;
+        block_of(w, blk, b);
+        const SegArgs &sa = b.sa;
+        const uint32_t nseg = b.nseg;
+        const bool inside = b.inside;
+        auto seg_lo = [&](uint32_t si) { return b.r.x + si * S; };
+        auto seg_hi = [&](uint32_t si) { return min(b.r.y, b.r.x + (si + 1) * S); };
         // (state slot, block) index of the chain's bookkeeping (tiles of
         // two or more segments only)
         auto sidx = [&](uint32_t si) -> size_t { return ((size_t)sbase + si) * NB + blk; };
+        CtaQueue *q = chained ? cq : nullptr;
 
-        PixState cur;       // the inclusive state through segment m
+        PixState cur;  // the inclusive state through segment m
         uint32_t m = seg;
         fresh_state(cur, inside);
         if (!tch) {
@@ -585,7 +770,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
                 fresh_state(ag, inside);
                 ag.done = ag.done || cur.done;
                 composite_segment(false, seg_lo(m), seg_hi(m), sa, ag, pairs, nullptr);
-                combine(cur, ag, seg_lo(m), seg_hi(m), sa, pairs);
+                combine(cur, ag, seg_lo(m), seg_hi(m), sa, pairs, nullptr, spin_limit, w, m, blk);
             }
             m = nseg - 1;
         } else if (seg == 0) {
@@ -598,8 +783,9 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
             bool known = __all_sync(0xffffffffu, ld_acquire_u32(ready + pi) != 0u);
             if (known) load_state(states + pi * SW, lastw + pi * 32, lane, pr);
             // pixels the predecessor shows done, or whose stop it shows to lie
-            // in the part already walked, drop out (their result no longer
-            // depends on this aggregate; the latter publish T = 0)
+            // in the part already walked (with the deferral margin), drop out
+            // (their result no longer depends on this aggregate; the latter
+            // publish T = 0)
             bool rewalk = false;
             PixState ag;
             fresh_state(ag, inside);
@@ -609,7 +795,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
             if (!known && reached < s1) {
                 (void)ld_acquire_u32(ready + pi);
                 load_state(states + pi * SW, lastw + pi * 32, lane, pr);
-                rewalk = !pr.done && !ag.done && pr.T * ag.T < tmin;
+                rewalk = !pr.done && !ag.done && pr.T * ag.T < tmin * kDeferMargin;
                 ag.done = ag.done || pr.done || rewalk;
                 composite_segment(false, reached, s1, sa, ag, pairs, nullptr);
             }
@@ -618,9 +804,9 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
             store_state(states + si * SW, lastw + si * 32, lane, ag);
             // the second to arrive (this aggregate or the predecessor's
             // inclusive state) continues the chain
-            if (arrive(counters + si, lane) == 0u) continue;
+            if (arrive(counters + si, lane) == 0u) return;
             load_state(states + pi * SW, lastw + pi * 32, lane, cur);  // the predecessor's inclusive state
-            combine(cur, ag, s0, s1, sa, pairs);
+            combine(cur, ag, s0, s1, sa, pairs, q, spin_limit, w, seg, blk);
         }
         // publish the chain forward: while the successor's aggregate is
         // already stored, combine it too
@@ -635,34 +821,64 @@ __global__ void __launch_bounds__(kWarps * 32, 3) blend_kernel(
             PixState ag;
             load_state(states + ni * SW, lastw + ni * 32, lane, ag);
             ++m;
-            combine(cur, ag, seg_lo(m), seg_hi(m), sa, pairs);
+            combine(cur, ag, seg_lo(m), seg_hi(m), sa, pairs, q, spin_limit, w, m, blk);
         }
-        if (m + 1 == nseg && inside) {  // the last segment's inclusive state is the pixel
-            const int64_t HW = (int64_t)V.H * V.W;
-            const int64_t p = (int64_t)py * V.W + px;
-            if (out_rgb) {
-                float *o = out_rgb + 3 * V.pix_base + p;
-                o[0] = fmaf(cur.T, P.bg[0], cur.c0);
-                o[HW] = fmaf(cur.T, P.bg[1], cur.c1);
-                o[2 * HW] = fmaf(cur.T, P.bg[2], cur.c2);
-            }
-            if (out_nrm) {
-                float *o = out_nrm + 3 * V.pix_base + p;
-                o[0] = cur.n0;
-                o[HW] = cur.n1;
-                o[2 * HW] = cur.n2;
-            }
-            if (out_depth) out_depth[V.pix_base + p] = cur.D;
-            if (out_alpha) out_alpha[V.pix_base + p] = 1.f - cur.T;
-            if (out_last) out_last[V.pix_base + p] = cur.last;
+        if (m + 1 == nseg && inside && !cur.deferred) write_pixel(b, cur);  // the last state is the pixel
+    };
+
+    // (the CTA's queued re-walks wait until its warps run out of items: a
+    // check of the queue before each item measured 0.15 ms slower per frame)
+    for (;;) {
+        uint32_t item = 0;
+        if (lane == 0) {
+            if (chained) atomicAdd(&cq->busy, 1u);
+            item = atomicAdd(work_counter, 1u);
         }
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item < total) do_item(item);
+        __syncwarp();
+        if (chained && lane == 0) atomicSub(&cq->busy, 1u);  // after any re-walk it queued
+        if (item >= total) break;
     }
+
+    if (chained) drain_queue(cq, spin_limit, status, take_task);
     if (pair_count) {  // one atomic per warp (every lane reaches here)
         unsigned long long t = pairs;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (lane == 0 && t) atomicAdd(pair_count, t);
     }
+}
+
+// Timeout self-test of the re-walk queue's waits, one warp: which 0 drains
+// a queue whose CTA never leaves its item (busy stays 1), which 1 pops from
+// a non-empty queue whose lock is never released.  Both give up after
+// `spin_limit` rounds and record P2E_ERR_TIMEOUT; no task is ever run.
+__global__ void selftest_queue_kernel(int which, uint32_t spin_limit, int32_t *status) {
+    __shared__ CtaQueue q;
+    if (threadIdx.x == 0) {
+        q.head = 0u;
+        q.tail = which == 1 ? 1u : 0u;
+        q.lock = which == 1 ? 1u : 0u;
+        q.busy = which == 0 ? 1u : 0u;
+        q.task[0] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncwarp();
+    drain_queue(&q, spin_limit, status, [&]() -> int {
+        int got = 0;
+        uint4 t;
+        if ((threadIdx.x & 31) == 0) {
+            got = cq_pop(&q, t, spin_limit);
+            if (got < 0) atomicExch(status, (int32_t)P2E_ERR_TIMEOUT);
+        }
+        got = __shfl_sync(0xffffffffu, got, 0);
+        return got > 0 ? 0 : got;  // a popped task is not run
+    });
+}
+
+cudaError_t launch_selftest_queue(int which, int32_t *status, uint32_t spin_limit, cudaStream_t st) {
+    selftest_queue_kernel<<<1, 32, 0, st>>>(which, spin_limit, status);
+    return cudaGetLastError();
 }
 
 // Background for every pixel of a tile with an empty list.
@@ -730,7 +946,8 @@ static cudaError_t launch_blend(const p2e_gaussians *g, const p2e_projected *pro
     // counters and flags in vals[1 - result], the state floats in
     // keys[1 - result] (decided on the device by the item table)
     const int other = 1 - bins->result;
-    const bool allow = bins->capacity > 0 && bins->keys[other] && bins->vals[other];
+    // (its re-walk queue's bounded waits report through status_dev)
+    const bool allow = bins->capacity > 0 && bins->keys[other] && bins->vals[other] && bins->status_dev;
     uint32_t *table = allow ? bins->vals[other] : nullptr;
     char *store = allow ? (char *)bins->keys[other] : nullptr;
     if (allow) {
@@ -745,7 +962,7 @@ static cudaError_t launch_blend(const p2e_gaussians *g, const p2e_projected *pro
         (const uint2 *)bins->ranges, bins->vals[bins->result], bins->tile_work, bins->tile_work + 1, table, store,
         (const float4 *)proj->xy_depth, (const float4 *)proj->conic_op, (const ushort4 *)proj->rect,
         (const float4 *)g->rgb, (const float4 *)g->normal, rgb, nrm, depth, alpha, last,
-        pr ? (unsigned long long *)pr->count_dev : nullptr, P);
+        pr ? (unsigned long long *)pr->count_dev : nullptr, bins->status_dev, kSpinLimit, P);
     probe_stop(pr, st);
     return cudaGetLastError();
 }

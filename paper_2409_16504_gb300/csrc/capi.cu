@@ -35,6 +35,7 @@ size_t selftest_scan_bytes();
 cudaError_t launch_selftest_sort(void *scratch, int32_t *status, uint32_t spin_limit, cudaStream_t st);
 cudaError_t launch_selftest_scan(void *scratch, int32_t *status, uint32_t spin_limit, cudaStream_t st);
 cudaError_t launch_selftest_mbar(int32_t *status, uint32_t spin_limit, cudaStream_t st);
+cudaError_t launch_selftest_queue(int which, int32_t *status, uint32_t spin_limit, cudaStream_t st);
 
 // Probes are per host thread: a thread measuring its launches does not
 // disturb launches from other threads.
@@ -327,7 +328,7 @@ p2e_status p2e_estimate_check(const void *scratch, int64_t scratch_bytes, int64_
 
 p2e_status p2e_selftest_timeout(int32_t which, uint32_t spin_limit, void *scratch, int64_t scratch_bytes,
                                 int32_t *status_dev, void *stream) {
-    if (which < 0 || which > 2 || spin_limit < 1 || spin_limit > kSpinLimit || !status_dev || !scratch ||
+    if (which < 0 || which > 4 || spin_limit < 1 || spin_limit > kSpinLimit || !status_dev || !scratch ||
         ((uintptr_t)scratch & 255u) || ((uintptr_t)status_dev & 3u) || scratch_bytes < P2E_SELFTEST_SCRATCH_BYTES)
         return P2E_ERR_INVALID_ARG;
     if (selftest_sort_bytes() > P2E_SELFTEST_SCRATCH_BYTES || selftest_scan_bytes() > P2E_SELFTEST_SCRATCH_BYTES)
@@ -335,7 +336,8 @@ p2e_status p2e_selftest_timeout(int32_t which, uint32_t spin_limit, void *scratc
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = which == 0   ? launch_selftest_sort(scratch, status_dev, spin_limit, st)
                     : which == 1 ? launch_selftest_scan(scratch, status_dev, spin_limit, st)
-                                 : launch_selftest_mbar(status_dev, spin_limit, st);
+                    : which == 2 ? launch_selftest_mbar(status_dev, spin_limit, st)
+                                 : launch_selftest_queue(which - 3, status_dev, spin_limit, st);
     return e == cudaSuccess ? P2E_OK : P2E_ERR_CUDA;
 }
 

@@ -258,7 +258,7 @@ class Renderer:
             if st == _lib.P2E_OK:
                 return out
             if st != _lib.P2E_ERR_CAPACITY:
-                raise _lib.P2EError("p2e_sort_bin", st)
+                raise _lib.P2EError("p2e_sort_bin / p2e_render", st)
             self.capacity = int(k * 1.5) + 1024
             self._ensure(g.n * len(cams), tt)
         raise _lib.P2EError("p2e_sort_bin", _lib.P2E_ERR_CAPACITY)

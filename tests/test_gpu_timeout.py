@@ -1,7 +1,8 @@
 """The bounded device waits give up, return and report P2E_ERR_TIMEOUT.
 
 Every spin-wait of the library (the decoupled look-backs of the radix sort
-and of the estimator's cell scan, the learned head's mbarrier waits) has an
+and of the estimator's cell scan, the learned head's mbarrier waits, the
+compositing's wait for deferred re-walks and its queue lock) has an
 iteration limit.  p2e_selftest_timeout drives one of them into a wait that
 can never be satisfied -- a predecessor tile that no CTA publishes, an
 mbarrier arrival that never comes -- with a short limit.  The wait must
@@ -40,7 +41,7 @@ def _selftest(which, spin_limit):
     return status, time.perf_counter() - t0
 
 
-@pytest.mark.parametrize("which", [0, 1, 2])
+@pytest.mark.parametrize("which", [0, 1, 2, 3, 4])
 def test_wait_gives_up_and_reports_timeout(which):
     from paper_2409_16504_gb300 import _lib
     status, dt = _selftest(which, 4096)
@@ -53,7 +54,7 @@ def test_context_usable_after_timeouts():
     import oracle
     from gpu_common import cfg1_scene, gpu_render
     from paper_2409_16504_gb300 import _lib
-    for which in (0, 1, 2):
+    for which in (0, 1, 2, 3, 4):
         assert _selftest(which, 64)[0] == _lib.P2E_ERR_TIMEOUT
     g, cam = cfg1_scene()
     r, out = gpu_render(g, [cam])
@@ -70,6 +71,6 @@ def test_selftest_rejects_bad_arguments():
     sp = C.c_void_p((s.data_ptr() + 255) & ~255)
     w = torch.zeros(1, dtype=torch.int32, device="cuda")
     wp = C.c_void_p(w.data_ptr())
-    assert lib.p2e_selftest_timeout(3, 64, sp, _lib.SELFTEST_SCRATCH_BYTES, wp, None) == _lib.P2E_ERR_INVALID_ARG
+    assert lib.p2e_selftest_timeout(5, 64, sp, _lib.SELFTEST_SCRATCH_BYTES, wp, None) == _lib.P2E_ERR_INVALID_ARG
     assert lib.p2e_selftest_timeout(0, 0, sp, _lib.SELFTEST_SCRATCH_BYTES, wp, None) == _lib.P2E_ERR_INVALID_ARG
     assert lib.p2e_selftest_timeout(0, 64, sp, 1024, wp, None) == _lib.P2E_ERR_INVALID_ARG
