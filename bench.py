@@ -373,12 +373,14 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
         recs = []
+        keys = torch.zeros((), dtype=torch.int64, device=dev)  # summed key counts (device side)
         for i in range(args.steps):
             flush.fill_(i & 0xFF)
             for p in probes.values():
                 if p is not None:
                     p.arm(i)
             recs.append(frame(cams[args.warmup + i], path))
+            keys += rend.bins.counters[0]  # after the frame's last event: outside its timing
         for p in probes.values():
             if p is not None:
                 p.disarm()
@@ -388,7 +390,7 @@ def main():
         stage = np.array([[a.elapsed_time(b) for a, b in zip(r[:-1], r[1:])] for r in recs])
         kern = {k: (p.mean_ms() if p is not None else None) for k, p in probes.items()}
         pairs = probes["blend"].per_step_count()
-        return stage, kern, pairs
+        return stage, kern, pairs, float(keys.item()) / args.steps
 
     def latency(path, frames):
         """Per-frame device latency (estimate + project + sort + blend) over
@@ -409,10 +411,9 @@ def main():
     clk.start()
     results = {p: timed(p) for p in paths}
     clocks = clk.stop()
-    st_ok, n_keys = p2e_bins_check(rend.bins)
+    st_ok, last_keys = p2e_bins_check(rend.bins)
     if st_ok != 0:
-        raise RuntimeError(f"binning status {st_ok}: key capacity {rend.capacity} < {n_keys}")
-    assert n_keys > n // 2, n_keys  # the key count of the last frame, not a loop index
+        raise RuntimeError(f"binning / compositing status {st_ok} (key capacity {rend.capacity}, {last_keys} keys)")
 
     def summary(stage):
         fm = stage.sum(1)
@@ -424,7 +425,8 @@ def main():
     sums = {p: summary(results[p][0]) for p in paths}
     head_path = paths[0]
     hs = sums[head_path]
-    kern, pairs = results[head_path][1], results[head_path][2]
+    kern, pairs, n_keys = results[head_path][1], results[head_path][2], results[head_path][3]
+    assert n_keys > n // 2, n_keys  # mean keys per timed frame of the reported path
     lat = {p: latency(p, n_lat) for p in paths} if n_lat else {}
 
     # ---- kernel rooflines (achieved work per launch / CUDA-event duration)
@@ -464,7 +466,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": hs["ms"], "p50_ms": hs["p50"], "p99_ms": hs["p99"],
             "stage_ms": hs["stage"], "kernel_ms": kern, "path": head_path,
             "paths": {p: {"Mpix_s": v["value"], "p50_ms": v["p50"], "p99_ms": v["p99"], "stage_ms": v["stage"],
-                          "kernel_ms": results[p][1]} for p, v in sums.items()},
+                          "kernel_ms": results[p][1], "keys_per_frame": results[p][3]} for p, v in sums.items()},
             "keys_per_frame": n_keys, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(head_path), "points": N_POINTS, "resolution": RES,
