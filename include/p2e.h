@@ -321,6 +321,21 @@ p2e_status p2e_loss_eq5(const float *rgb, const float *normal, const float *gt_r
                         float w1, float w2, float w3, float *loss_dev, float *d_rgb,
                         float *d_normal, void *stream);
 
+/* p2e_loss_splat_area -- a rendering-cost term for training the estimator
+ * (not in the paper; an option of this implementation's training):
+ *   A = weight * mean_i (s_i0 s_i1) / (r_i0 r_i1)
+ * the footprint of each estimated splat (its two largest axes) relative to
+ * a reference estimate's, typically the kNN-PCA frame the network
+ * corrects: compositing screens and evaluates every splat over its
+ * footprint, so A tracks the frame's compositing work.  scale: the
+ * estimate's device float4[n] (s0, s1, s2, -); ref_scale: the reference's,
+ * both 16-byte aligned.  ADDS A to *loss_dev and dA/ds to d_scale (device
+ * float[3n], s0 s1 s2 per point, the layout p2e_render_backward writes).
+ * A point whose reference area is not positive and finite adds nothing.
+ * weight >= 0. */
+p2e_status p2e_loss_splat_area(const float *scale, const float *ref_scale, int64_t n, float weight,
+                               float *loss_dev, float *d_scale, void *stream);
+
 /* p2e_loss_ssim -- the structural term of an "L1 + SSIM" image loss on the
  * rendered colour (the training objective of the differentiable splatting
  * this renderer follows; the paper's Eq. 5 is the L1 + normal loss above):

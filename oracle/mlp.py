@@ -230,3 +230,23 @@ def linear_outputs(p: dict, x, scale_pca, quat_pca, opacity_pca, up: dict) -> fl
     out = apply_corrections(scale_pca, quat_pca, opacity_pca, y)
     return float((up["scale"] * out["scale"]).sum() + (up["quat"] * out["quat"]).sum() +
                  (up["opacity"] * out["opacity"]).sum() + (up["normal"] * out["normal"]).sum())
+
+
+def splat_area_loss(scale, ref_scale, weight: float):
+    """The rendering-cost term of the training loss (an option of this
+    implementation, not the paper's): A = weight * mean_i (s_i0 s_i1) /
+    (r_i0 r_i1) over the points, the footprint of each estimated splat's two
+    largest axes relative to the reference estimate's; points whose
+    reference area is not positive and finite count in the mean's n but add
+    nothing.  Returns (A, dA/ds) with dA/ds of shape (n, 3) (zero for s2)."""
+    s = np.asarray(scale, np.float64)[:, :3]
+    r = np.asarray(ref_scale, np.float64)[:, :3]
+    n = len(s)
+    ra = r[:, 0] * r[:, 1]
+    ok = np.isfinite(ra) & (ra > 0)
+    g = np.zeros(n)
+    g[ok] = s[ok, 0] * s[ok, 1] / ra[ok]
+    d = np.zeros((n, 3))
+    d[ok, 0] = weight / n * s[ok, 1] / ra[ok]
+    d[ok, 1] = weight / n * s[ok, 0] / ra[ok]
+    return weight * g.sum() / n, d

@@ -25,7 +25,8 @@ EXPORTS = ("p2e_default_config", "p2e_total_tiles", "p2e_scratch_bytes", "p2e_pr
            "p2e_sort_bin", "p2e_sort_bin_noalloc", "p2e_bins_check", "p2e_render",
            "p2e_render_backward", "p2e_estimate", "p2e_loss_eq5", "p2e_mlp_backward", "p2e_adam",
            "p2e_estimate_global", "p2e_relight", "p2e_point_raster", "p2e_set_kernel_probe",
-           "p2e_estimate_check", "p2e_selftest_timeout", "p2e_loss_ssim", "p2e_status_string")
+           "p2e_estimate_check", "p2e_selftest_timeout", "p2e_loss_ssim", "p2e_loss_splat_area",
+           "p2e_status_string")
 P2E_PROBE_KNN, P2E_PROBE_BLEND, P2E_PROBE_MLP = 0, 1, 2
 SELFTEST_SCRATCH_BYTES = 1 << 20
 P2E_MAX_LIGHTS = 8
@@ -138,6 +139,8 @@ def load(path: str | None = None):
         lib.p2e_estimate_check.argtypes = [vp, i64, i64, vp]
         lib.p2e_loss_ssim.restype = C.c_int
         lib.p2e_loss_ssim.argtypes = [vp, vp, C.POINTER(C.c_int32), i32, C.c_float, vp, vp, vp, i64, vp]
+        lib.p2e_loss_splat_area.restype = C.c_int
+        lib.p2e_loss_splat_area.argtypes = [vp, vp, i64, C.c_float, vp, vp, vp]
         lib.p2e_selftest_timeout.restype = C.c_int
         lib.p2e_selftest_timeout.argtypes = [i32, C.c_uint32, vp, i64, vp, vp]
         _lib = lib

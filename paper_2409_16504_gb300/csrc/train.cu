@@ -714,6 +714,46 @@ p2e_status p2e_loss_ssim(const float *rgb, const float *gt_rgb, const int32_t *v
     return cudaGetLastError() == cudaSuccess ? P2E_OK : P2E_ERR_CUDA;
 }
 
+// Area term: A = weight mean_i (s_i0 s_i1) / (r_i0 r_i1), the footprint of
+// each estimated splat relative to the reference estimate's; dA/ds_i0 =
+// (weight / n) g_i / s_i0 and likewise for s_i1 (g_i the ratio), added to
+// d_scale.  A point whose reference area is not positive and finite adds
+// nothing.  The loss is summed per block (one atomic per block).
+__global__ void __launch_bounds__(256) splat_area_kernel(const float4 *__restrict__ scale,
+                                                         const float4 *__restrict__ ref, int64_t n, float wn,
+                                                         float *__restrict__ loss_dev, float *__restrict__ d_scale) {
+    __shared__ float s_part[8];
+    float part = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 s = __ldg(scale + i), r = __ldg(ref + i);
+        const float ra = r.x * r.y;
+        if (!(ra > 0.f) || !(ra < INFINITY)) continue;
+        const float g = (s.x * s.y) / ra;
+        part += g;
+        d_scale[3 * i] += wn * (s.y / ra);
+        d_scale[3 * i + 1] += wn * (s.x / ra);
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_part[k];
+        atomicAdd(loss_dev, wn * t);
+    }
+}
+
+p2e_status p2e_loss_splat_area(const float *scale, const float *ref_scale, int64_t n, float weight, float *loss_dev,
+                               float *d_scale, void *stream) {
+    if (!scale || !ref_scale || !loss_dev || !d_scale || n < 1 || !(weight >= 0.f) || !(weight < INFINITY))
+        return P2E_ERR_INVALID_ARG;
+    if (((uintptr_t)scale & 15u) || ((uintptr_t)ref_scale & 15u)) return P2E_ERR_INVALID_ARG;
+    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)device_sms() * 8);
+    splat_area_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>((const float4 *)scale, (const float4 *)ref_scale, n,
+                                                              weight / (float)n, loss_dev, d_scale);
+    return cudaGetLastError() == cudaSuccess ? P2E_OK : P2E_ERR_CUDA;
+}
+
 p2e_status p2e_mlp_backward(const float *xyz, const float *rgb, int64_t n, const uint32_t *knn_idx,
                             const p2e_gaussians *pca, const void *mlp_weights, const float *d_scale,
                             const float *d_quat, const float *d_opacity, const float *d_normal, float *grad,

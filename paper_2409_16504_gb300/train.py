@@ -130,9 +130,11 @@ def loss_ssim(rgb: torch.Tensor, gt_rgb: torch.Tensor, sizes: list, weight: floa
 
 class Trainer:
     def __init__(self, n_max: int, seed: int = 0, lr: float = 1e-3, cfg: dict | None = None, device="cuda",
-                 params: dict | None = None, ssim_weight: float = 0.0):
+                 params: dict | None = None, ssim_weight: float = 0.0, area_weight: float = 0.0):
         """``ssim_weight`` > 0 adds that weight times the SSIM term
-        (p2e_loss_ssim) of the colour to the Eq. 5 loss."""
+        (p2e_loss_ssim) of the colour to the Eq. 5 loss; ``area_weight`` > 0
+        adds that weight times the splats' mean footprint relative to the
+        kNN-PCA splats' (p2e_loss_splat_area), a rendering-cost term."""
         self.device = device
         self.cfg = {**DEFAULT_CONFIG, **(cfg or {})}
         self.theta = flatten(params if params is not None else mlp.init_params(seed, device)).to(device)
@@ -152,6 +154,7 @@ class Trainer:
         self.g_pca = GaussianSet.empty(n_max, device)
         self.g_net = GaussianSet.empty(n_max, device)
         self.ssim_weight = float(ssim_weight)
+        self.area_weight = float(area_weight)
         self.ssim_scratch = None
 
     def params(self) -> dict:
@@ -190,6 +193,10 @@ class Trainer:
                                 d_normal=d_nrm)
         ps = g_pca.c_struct()
         lib = _lib.load()
+        if self.area_weight > 0:
+            check("p2e_loss_splat_area", lib.p2e_loss_splat_area(
+                _ptr(g.scale), _ptr(g_pca.scale), sc.n, self.area_weight, _ptr(self.loss_dev), _ptr(d["scale"]),
+                _stream()))
         check("p2e_mlp_backward", lib.p2e_mlp_backward(
             _ptr(sc.xyz), _ptr(sc.rgb), sc.n, _ptr(knn), C.byref(ps), _ptr(self.blob), _ptr(d["scale"]),
             _ptr(d["quat"]), _ptr(d["opacity"]), _ptr(d["normal"]), _ptr(self.grad), _stream()))
@@ -253,6 +260,8 @@ def main(argv=None):
     ap.add_argument("--eval-scenes", type=int, default=4)
     ap.add_argument("--out", default=mlp.TRAINED)
     ap.add_argument("--ssim", type=float, default=0.0, help="weight of the SSIM term added to the Eq. 5 loss")
+    ap.add_argument("--area", type=float, default=0.0,
+                    help="weight of the splat-footprint term (rendering cost) added to the loss")
     ap.add_argument("--augment", type=float, default=0.0,
                     help="fraction of training scenes with degraded inputs (10-bit voxels coarsened by "
                          "alpha in [0.25, 1], or a beta in [0.125, 1] random subset)")
@@ -279,7 +288,7 @@ def main(argv=None):
     pool = [Scene(0, 0, 0, 0, parts=p, gt=g) for p, g in zip(parts, gts[:len(parts)])]
     held = [Scene(0, 0, 0, 0, parts=p, gt=g) for p, g in zip(held_parts, gts[len(parts):])]
     print(f"scenes ready in {time.time() - t0:.1f} s (points {min(npts)}..{max(npts)})", flush=True)
-    tr = Trainer(max(npts + [len(p[1]) for p in held_parts]), lr=a.lr, ssim_weight=a.ssim)
+    tr = Trainer(max(npts + [len(p[1]) for p in held_parts]), lr=a.lr, ssim_weight=a.ssim, area_weight=a.area)
     before = [tr.evaluate(h, learned=False) for h in held]
     t1 = time.time()
     for it in range(a.steps):

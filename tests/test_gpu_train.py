@@ -16,7 +16,7 @@
   sign decisions are knife edges get zero upstream gradient on both sides.
   The 50K-point case runs several 128-point tiles per CTA (the TMEM
   gradient accumulators carried across tiles).
-* p2e_adam against numpy.
+* p2e_adam against numpy; p2e_loss_splat_area against the oracle.
 * A short end-to-end run (estimate -> render -> loss -> backward -> Adam)
   lowers the loss.
 """
@@ -175,6 +175,37 @@ def test_adam_matches_numpy():
     from paper_2409_16504_gb300 import mlp
     from paper_2409_16504_gb300.train import unflatten
     np.testing.assert_array_equal(blob.cpu().numpy(), mlp.pack(unflatten(t["th"])).cpu().numpy())
+
+
+def test_splat_area_term_matches_oracle():
+    """p2e_loss_splat_area against the oracle's FP64 term: the loss it adds
+    and the gradient it adds to d_scale, on 100K random scales (one
+    degenerate reference among them); within 1e-5 relative (fp32 sums)."""
+    from paper_2409_16504_gb300 import _lib
+    from paper_2409_16504_gb300.render import _ptr, _stream
+    rng = np.random.default_rng(4)
+    n = 100_000
+    s = np.zeros((n, 4), np.float32)
+    r = np.zeros((n, 4), np.float32)
+    s[:, :3] = rng.uniform(0.001, 0.03, (n, 3))
+    r[:, :3] = rng.uniform(0.001, 0.03, (n, 3))
+    r[7, 0] = 0.0
+    ts, tr_ = torch.from_numpy(s).cuda(), torch.from_numpy(r).cuda()
+    td = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    loss = torch.full((1,), 0.25, dtype=torch.float32, device="cuda")
+    lib = _lib.load()
+    assert lib.p2e_loss_splat_area(_ptr(ts), _ptr(tr_), n, 0.2, _ptr(loss), _ptr(td), _stream()) == 0
+    torch.cuda.synchronize()
+    a, d = om.splat_area_loss(s, r, 0.2)
+    assert abs(float(loss.item()) - (0.25 + a)) <= 1e-5 * (0.25 + a)
+    got = td.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(got, d, rtol=1e-5, atol=1e-6 * np.abs(d).max())
+    # a second call adds the same again (loss and gradient accumulate)
+    assert lib.p2e_loss_splat_area(_ptr(ts), _ptr(tr_), n, 0.2, _ptr(loss), _ptr(td), _stream()) == 0
+    torch.cuda.synchronize()
+    assert abs(float(loss.item()) - (0.25 + 2 * a)) <= 1e-5 * (0.25 + 2 * a)
+    np.testing.assert_allclose(td.cpu().numpy(), 2 * d, rtol=1e-5, atol=1e-6 * np.abs(d).max())
+    assert not got[7, :2].any()
 
 
 def test_short_training_lowers_loss():
