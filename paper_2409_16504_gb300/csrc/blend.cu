@@ -53,7 +53,7 @@ namespace p2e {
 
 constexpr int kBW = 8, kBH = 4;    // pixel block of one warp
 constexpr int kWarps = 8;          // warps per CTA
-constexpr int kStateFloats = 8;    // T, C0..2, N0..2, D (and a word last | done << 31 apart)
+constexpr int kStateFloats = 8;    // T, C0..2, N0..2, D (and a word last | deferred << 30 | done << 31 apart)
 constexpr uint32_t kDoneBit = 1u << 31;
 constexpr uint32_t kIncl = 2u;  // segment flag: inclusive state published
 

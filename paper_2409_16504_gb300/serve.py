@@ -329,11 +329,14 @@ def host_frames(cloud, frames: int) -> list:
 
 def run_load(seconds: float = 10.0, rate: float = 500.0, fps: float = 30.0, res=(1024, 2048),
              n_range=(300_000, 1_200_000), slots: int = 3, max_views: int = 8, seed: int = 5,
-             learned: bool = True, frames: int = 16) -> dict:
+             learned: bool = True, frames: int = 16, deadline: float | None = None) -> dict:
     """Poisson viewpoint requests at ``rate``/s (square resolutions drawn
     uniformly from ``res``) against a moving humanoid cloud whose frames
     (point count swinging over ``n_range`` every 4 s) are uploaded from
-    pinned host memory and estimated at ``fps``.  Returns latency stats."""
+    pinned host memory and estimated at ``fps``.  ``deadline`` (s): requests
+    still queued that long after arrival are dropped (a display shows the
+    latest pose).  Returns latency stats of the rendered requests and the
+    number dropped."""
     import torch
 
     import scenes
@@ -343,7 +346,7 @@ def run_load(seconds: float = 10.0, rate: float = 500.0, fps: float = 30.0, res=
     cloud = scenes.DynamicCloud(n_range, seed=seed, frames=frames)
     host = host_frames(cloud, frames)
     ex = GpuExecutor(n_range[1], slots, mlp_blob=blob)
-    sch = Scheduler(ex, slots=slots, max_views=max_views)
+    sch = Scheduler(ex, slots=slots, max_views=max_views, deadline=deadline)
     center = np.array([0.0, 0.5, 0.0])
     # warm-up: both buffers estimated (the largest frame last, so the slots'
     # key buffers are sized for it), every slot renders full batches of
@@ -380,6 +383,10 @@ def run_load(seconds: float = 10.0, rate: float = 500.0, fps: float = 30.0, res=
             break
         time.sleep(0.00005)
     torch.cuda.synchronize()
+    dropped = sum(1 for r in reqs if r.dropped)
+    reqs = [r for r in reqs if not r.dropped]
+    if not reqs:
+        raise RuntimeError(f"every one of {dropped} requests was dropped")
     lat = np.array([r.latency for r in reqs]) * 1e3
     by_res = {}
     for r_ in res:
@@ -394,7 +401,7 @@ def run_load(seconds: float = 10.0, rate: float = 500.0, fps: float = 30.0, res=
                 batches=sch.next_bid, mean_views_per_batch=len(reqs) / max(sch.next_bid, 1),
                 mpix_per_s=px / wall / 1e6, cloud_frames=fi, rerenders=ex.rerenders,
                 path="learned" if blob is not None else "pca", rate=rate, seconds=seconds,
-                points=list(n_range), fps=fps)
+                points=list(n_range), fps=fps, dropped=dropped, deadline_ms=None if deadline is None else 1e3 * deadline)
 
 
 def main(argv=None):
