@@ -61,6 +61,16 @@ MLP_FLOP_PER_POINT = 2 * (96 * 64 + 64 * 64 * 2 + 64 * 8)
 BLEND_FP32_PER_PAIR = 20
 BLEND_BYTES_PER_KEY = 4 + 16 + 16 + 8 + 16 + 16
 BLEND_BYTES_PER_PIXEL = 9 * 4
+#   projection (one kernel): per Gaussian 48 B read (mean_op, scale, quat) and
+#   44 B written (xy_depth, conic_op, rect, tile count)
+PROJECT_BYTES_PER_GAUSSIAN = 48 + 44
+#   binning (a stage of ~12 launches, depth-first order): per Gaussian the
+#   depth key built (8 B read + 12 B written), four 8-bit passes over the
+#   depth keys (12 B read + 12 B written each) and the emission's read of its
+#   record and sorted index (24 B); per tile key its emission (12 B), two passes
+#   over the tile bits (24 B each) and the range search (8 B)
+SORT_BYTES_PER_GAUSSIAN = 20 + 4 * 24 + 24
+SORT_BYTES_PER_KEY = 12 + 2 * 24 + 8
 FP32_LANES_PER_SM = 128
 
 # DRAM bytes per launch from one ncu capture of the kernel (dram__bytes_read
@@ -480,7 +490,20 @@ def main():
                               "hbm": {"achieved_gbs": hb, "frac": hb / hbm,
                                       "algorithmic_bytes_per_launch": BLEND_BYTES_PER_KEY * n_keys +
                                       BLEND_BYTES_PER_PIXEL * RES * RES}}
-    dom = max(rooflines, key=lambda k: rooflines[k]["ms"])
+    # stage rooflines from the stage events (projection is one launch; binning
+    # is a stage of several, reported as such)
+    a = PROJECT_BYTES_PER_GAUSSIAN * n / (hs["stage"]["project"] / 1e3) / 1e9
+    rooflines["project"] = {"kernel": "project_kernel", "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
+                            "frac": a / hbm, "traffic": None, "ms": hs["stage"]["project"],
+                            "algorithmic_bytes_per_launch": PROJECT_BYTES_PER_GAUSSIAN * n,
+                            "peak_source": src_peak, "timed": "stage events (one launch)"}
+    alg = SORT_BYTES_PER_GAUSSIAN * n + SORT_BYTES_PER_KEY * n_keys
+    a = alg / (hs["stage"]["sort_bin"] / 1e3) / 1e9
+    rooflines["sort_bin"] = {"kernel": "p2e_sort_bin stage (depth keys, 6 radix passes, emission, ranges)",
+                             "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+                             "traffic": None, "ms": hs["stage"]["sort_bin"], "algorithmic_bytes_per_call": alg,
+                             "peak_source": src_peak, "timed": "stage events (~12 launches)"}
+    dom = max((k for k in rooflines if k != "sort_bin"), key=lambda k: rooflines[k]["ms"])  # one kernel
 
     line = {"metric": METRIC, "value": hs["value"], "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": hs["ms"], "p50_ms": hs["p50"], "p99_ms": hs["p99"],
