@@ -81,8 +81,8 @@ _CSRC = "paper_2409_16504_gb300/csrc/"
 NCU_TRAFFIC = {
     "knn": {"kernel": "knn_pca_kernel", "sources": [_CSRC + "estimate.cu"],
             "sha256_16": "e47fe60e0257de70", "bytes": 284_631_000},
-    "blend": {"kernel": "blend_kernel<16>", "sources": [_CSRC + "blend.cu", _CSRC + "splat.cuh"],
-              "sha256_16": "ae1d3d0a5411ef65", "bytes": 253_313_000},
+    "blend": {"kernel": "blend_kernel<8>", "tile": 8, "sources": [_CSRC + "blend.cu", _CSRC + "splat.cuh"],
+              "sha256_16": "ae1d3d0a5411ef65", "bytes": 373_008_000},
     "mlp": {"kernel": "mlp_estimate_kernel", "sources": [_CSRC + "mlp.cu", _CSRC + "tcgen05.cuh"],
             "sha256_16": "7d49e064b1b85464", "bytes": 135_280_000},
 }
@@ -96,9 +96,13 @@ def source_digest(rels: list) -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(which: str):
+def ncu_traffic(which: str, tile: int | None = None):
+    """The captured DRAM bytes per launch, or None when the sources changed
+    since the capture or (for a tile-templated kernel) the tile differs."""
     e = NCU_TRAFFIC[which]
     if e["bytes"] is None or e["sha256_16"] != source_digest(e["sources"]):
+        return None
+    if tile is not None and e.get("tile", tile) != tile:
         return None
     return e["bytes"]
 
@@ -328,7 +332,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed steps (for profiler runs): no latency, end-to-end or serving runs")
-    ap.add_argument("--tile", type=int, default=16, choices=[8, 16, 32])
+    ap.add_argument("--tile", type=int, default=8, choices=[8, 16, 32],
+                    help="binning tile in pixels (8: measured fastest for the 1024^2 frames)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -364,9 +369,14 @@ def main():
     gs = GaussianSet.empty(n, dev)
     st = torch.cuda.current_stream()
     rend = Renderer({"tile": args.tile}, capacity=1 << 21, device=dev)
-    est(cx, cc, out=gs)
-    rend.render(gs, [cams[0]])
-    rend.capacity = int(rend.n_keys * 2.0) + 4096   # headroom for other viewpoints and the compositing states
+    # key buffers: twice the first view's keys under the estimate that needs
+    # the most (headroom for other viewpoints and the compositing states)
+    first = 0
+    for m in ([PCA, LEARNED] if mlp_blob is not None else [PCA]):
+        est(cx, cc, mode=m, mlp_blob=mlp_blob, out=gs)
+        rend.render(gs, [cams[0]])
+        first = max(first, rend.n_keys)
+    rend.capacity = int(first * 2.0) + 4096
     rend.render(gs, [cams[0]])
     img = Images([cams[0]], dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -484,7 +494,7 @@ def main():
         hb = (BLEND_BYTES_PER_KEY * n_keys + BLEND_BYTES_PER_PIXEL * RES * RES) / (kern["blend"] / 1e3) / 1e9
         rooflines["blend"] = {"kernel": f"blend_kernel<{args.tile}>", "bound": "alu", "achieved": a,
                               "peak": fp32_peak, "unit": "TFLOP/s", "frac": a / fp32_peak,
-                              "traffic": ncu_traffic("blend"), "ms": kern["blend"],
+                              "traffic": ncu_traffic("blend", args.tile), "ms": kern["blend"],
                               "pairs_per_launch": pairs, "fp32_ops_per_pair": BLEND_FP32_PER_PAIR,
                               "peak_derivation": f"{sms} SMs x {FP32_LANES_PER_SM} fp32 lanes x {sm_mhz:.0f} MHz",
                               "hbm": {"achieved_gbs": hb, "frac": hb / hbm,

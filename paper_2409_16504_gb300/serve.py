@@ -329,7 +329,7 @@ def host_frames(cloud, frames: int) -> list:
 
 def run_load(seconds: float = 10.0, rate: float = 500.0, fps: float = 30.0, res=(1024, 2048),
              n_range=(300_000, 1_200_000), slots: int = 3, max_views: int = 8, seed: int = 5,
-             learned: bool = True, frames: int = 16, deadline: float | None = None) -> dict:
+             learned: bool = True, frames: int = 16, deadline: float | None = None, tile: int = 16) -> dict:
     """Poisson viewpoint requests at ``rate``/s (square resolutions drawn
     uniformly from ``res``) against a moving humanoid cloud whose frames
     (point count swinging over ``n_range`` every 4 s) are uploaded from
@@ -345,7 +345,7 @@ def run_load(seconds: float = 10.0, rate: float = 500.0, fps: float = 30.0, res=
     blob = mlp.load_trained("cuda") if learned else None
     cloud = scenes.DynamicCloud(n_range, seed=seed, frames=frames)
     host = host_frames(cloud, frames)
-    ex = GpuExecutor(n_range[1], slots, mlp_blob=blob)
+    ex = GpuExecutor(n_range[1], slots, mlp_blob=blob, cfg={"tile": tile})
     sch = Scheduler(ex, slots=slots, max_views=max_views, deadline=deadline)
     center = np.array([0.0, 0.5, 0.0])
     # warm-up: both buffers estimated (the largest frame last, so the slots'
@@ -401,7 +401,7 @@ def run_load(seconds: float = 10.0, rate: float = 500.0, fps: float = 30.0, res=
                 batches=sch.next_bid, mean_views_per_batch=len(reqs) / max(sch.next_bid, 1),
                 mpix_per_s=px / wall / 1e6, cloud_frames=fi, rerenders=ex.rerenders,
                 path="learned" if blob is not None else "pca", rate=rate, seconds=seconds,
-                points=list(n_range), fps=fps, dropped=dropped, deadline_ms=None if deadline is None else 1e3 * deadline)
+                points=list(n_range), fps=fps, tile=tile, dropped=dropped, deadline_ms=None if deadline is None else 1e3 * deadline)
 
 
 def main(argv=None):
