@@ -269,9 +269,10 @@ def test_very_long_tile_list_chains():
 
 
 def test_chained_schedule_fits_at_the_benchmark_capacity():
-    """At the benchmark's key capacity (2x the first view's keys + 4096)
-    every multi-segment tile of the 800K-point humanoid's views chains, for
-    24 camera positions on the 2.5 m sphere."""
+    """At the benchmark's key capacity (2x the first view's keys + 4096) and
+    tile sizes (8 px for the frames, 16 px as the library's default) every
+    multi-segment tile of the 800K-point humanoid's views chains, for 24
+    camera positions on the 2.5 m sphere."""
     import scenes
     from paper_2409_16504_gb300 import GaussianSet, Renderer
     g, cam = humanoid_scene(800_000, 1024, 1024)
@@ -279,16 +280,17 @@ def test_chained_schedule_fits_at_the_benchmark_capacity():
     c = np.asarray(g["mean"], np.float64).mean(0)
     rng = np.random.default_rng(102)
     cams = [scenes.sphere_camera(c, 2.5, rng, 1024, 1024) for _ in range(24)]
-    r = Renderer(capacity=1 << 21)
-    r.render(gs, [cams[0]])
-    r = Renderer(capacity=int(r.n_keys * 2.0) + 4096)
-    keys = []
-    for cam in cams:
-        r.render(gs, [cam])
-        torch.cuda.synchronize()
-        keys.append(r.n_keys)
-        assert _chain_info(r) == (1, 0), (r.n_keys, r.capacity, _chain_info(r))
-    print(f"keys per view {min(keys)} .. {max(keys)} at capacity {r.capacity}: all chained")
+    for tile in (8, 16):
+        r = Renderer({"tile": tile}, capacity=1 << 22)
+        r.render(gs, [cams[0]])
+        r = Renderer({"tile": tile}, capacity=int(r.n_keys * 2.0) + 4096)
+        keys = []
+        for cam in cams:
+            r.render(gs, [cam])
+            torch.cuda.synchronize()
+            keys.append(r.n_keys)
+            assert _chain_info(r) == (1, 0), (tile, r.n_keys, r.capacity, _chain_info(r))
+        print(f"tile {tile}: keys per view {min(keys)} .. {max(keys)} at capacity {r.capacity}: all chained")
 
 
 def test_depth_first_and_full_key_binning_agree():
