@@ -9,7 +9,10 @@
 //        smallest) << 32 | index keys, stable; a pass whose digit is the
 //        same for every key is a copy), into buffer 1;
 //   scan_emit: single-pass exclusive scan of the tile counts in that order
-//        (decoupled look-back) fused with key emission, into buffer 0;
+//        (decoupled look-back) fused with key emission, into buffer 0: the
+//        CTA's keys are emitted by all its threads together (key k of the
+//        CTA by thread k mod 256, its position found by a binary search of
+//        the positions' running counts), so that the stores coalesce;
 //   1-2 radix passes on the tile bits only (stable), so each tile keeps the
 //        depth order of emission.  Two passes over the tile keys instead of
 //        six: the depth digits are sorted once per Gaussian, not per key.
@@ -194,31 +197,43 @@ __global__ void __launch_bounds__(kScanThreads) scan_emit_kernel(
             if (tile == S.scan_tiles - 1) *n_keys_dev = (int64_t)(prefix + total);
         }
     }
-    __syncthreads();
-    uint64_t off = s_prefix + texcl;
+    // the tile's positions: running key counts (inclusive, from the tile's
+    // start) and Gaussians, so that the threads can emit the tile's keys
+    // together, key k by thread k mod kScanThreads (coalesced stores)
+    __shared__ uint32_t s_incl[kScanTile], s_src[kScanTile];
+    {
+        uint32_t run = (uint32_t)texcl;
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        const int64_t e = src[i];
-        if (cnt[i] != 0u) {
-            const int vi = (int)(e / P.n);
-            const View &V = P.v[vi];
-            const int64_t g = e - (int64_t)vi * P.n;
-            const ushort4 r = __ldg(rect + e);  // pixel rectangle -> tiles
-            const int B = P.tile;
-            const int tx0 = r.x / B, ty0 = r.y / B, tx1 = r.z / B, ty1 = r.w / B;
-            const uint32_t zb = __float_as_uint(__ldg(&xy_depth[e].z));
-            uint64_t o = off;
-            for (int ty = ty0; ty <= ty1; ++ty) {
-                const int64_t rowid = V.tile_base + (int64_t)ty * V.tiles_x;
-                for (int tx = tx0; tx <= tx1; ++tx, ++o) {
-                    if ((int64_t)o < capacity) {
-                        keys[o] = ((uint64_t)(rowid + tx) << 32) | zb;
-                        vals[o] = (uint32_t)g;
-                    }
-                }
-            }
+        for (int i = 0; i < kScanItems; ++i) {
+            run += cnt[i];
+            s_incl[threadIdx.x * kScanItems + i] = run;
+            s_src[threadIdx.x * kScanItems + i] = src[i];
         }
-        off += cnt[i];
+    }
+    __syncthreads();
+    const uint64_t base_off = s_prefix;
+    const int B = P.tile;
+    for (uint32_t k = threadIdx.x; k < (uint32_t)total; k += kScanThreads) {
+        int lo = 0, hi = kScanTile - 1;  // the first position whose running count exceeds k
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_incl[mid] > k) hi = mid;
+            else lo = mid + 1;
+        }
+        const uint32_t j = k - (lo > 0 ? s_incl[lo - 1] : 0u);  // the key's rank in its Gaussian's tiles
+        const int64_t e = s_src[lo];
+        const int vi = (int)(e / P.n);
+        const View &V = P.v[vi];
+        const int64_t g = e - (int64_t)vi * P.n;
+        const ushort4 r = __ldg(rect + e);  // pixel rectangle -> tiles
+        const int tx0 = r.x / B, ty0 = r.y / B, w = r.z / B - tx0 + 1;
+        const int ty = ty0 + (int)(j / (uint32_t)w), tx = tx0 + (int)(j % (uint32_t)w);
+        const uint32_t zb = __float_as_uint(__ldg(&xy_depth[e].z));
+        const uint64_t o = base_off + k;
+        if ((int64_t)o < capacity) {
+            keys[o] = ((uint64_t)(V.tile_base + (int64_t)ty * V.tiles_x + tx) << 32) | zb;
+            vals[o] = (uint32_t)g;
+        }
     }
 }
 
