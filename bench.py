@@ -72,6 +72,24 @@ PROJECT_BYTES_PER_GAUSSIAN = 48 + 44
 SORT_BYTES_PER_GAUSSIAN = 20 + 4 * 24 + 24
 SORT_BYTES_PER_KEY = 12 + 2 * 24 + 8
 FP32_LANES_PER_SM = 128
+#   backward compositing (the per-tile kernel of the differentiation), counted
+#   like the forward: per evaluated (pixel, splat) pair the offset and conic
+#   form in each of its two walks (2 x 12); per contributing pair exp +
+#   alpha and the transmittance in the front-to-back walk (5), and in the
+#   back-to-front walk exp + alpha (3), 1 - alpha, T_k, the weight, the
+#   seven-channel upstream dot (7), dL/dalpha (3), the running tail, the
+#   seven weighted channels (7) and the geometric gradients o, A, B, C, u, v
+#   (16): 37; per warp reduction of a splat's 13 channels, 16 adds in each of
+#   the 32 lanes.  HBM: per key its index and record in both walks
+#   (4 + 16 + 16 + 8, then 4 + 16 + 16 + 8 + 16 + 16 B), per pixel the
+#   upstream rgb and normal planes and `last` (28 B), per (view, Gaussian)
+#   its 13-float gradient slot (52 B)
+BWD_FP32_PER_EVAL = 2 * (4 + 8)
+BWD_FP32_PER_CONTRIB = 5 + 3 + 37
+BWD_FP32_PER_REDUCTION = 32 * 16
+BWD_BYTES_PER_KEY = (4 + 16 + 16 + 8) + (4 + 16 + 16 + 8 + 16 + 16)
+BWD_BYTES_PER_PIXEL = 12 + 12 + 4
+BWD_BYTES_PER_SLOT = 13 * 4
 
 # DRAM bytes per launch from one ncu capture of the kernel (dram__bytes_read
 # + dram__bytes_write, profiles/), valid while the kernel's sources are
@@ -290,7 +308,7 @@ class Probe:
     """CUDA events (and an optional device counter) that libp2e records
     around one kernel's launches, one event pair per step."""
 
-    def __init__(self, kernel: int, steps: int, dev, count: bool = False):
+    def __init__(self, kernel: int, steps: int, dev, counters: int = 0):
         import torch
         from paper_2409_16504_gb300 import _lib
         self.lib, self.kernel = _lib.load(), kernel
@@ -300,7 +318,7 @@ class Probe:
             a.record()
             b.record()
         torch.cuda.synchronize()
-        self.count = torch.zeros(1, dtype=torch.int64, device=dev) if count else None
+        self.count = torch.zeros(counters, dtype=torch.int64, device=dev) if counters else None
         self.armed = []
 
     def arm(self, i: int):
@@ -317,8 +335,8 @@ class Probe:
     def mean_ms(self) -> float:
         return float(np.mean([self.ev[i][0].elapsed_time(self.ev[i][1]) for i in self.armed]))
 
-    def per_step_count(self) -> float:
-        return float(self.count.item()) / max(len(self.armed), 1)
+    def per_step_count(self, i: int = 0) -> float:
+        return float(self.count[i].item()) / max(len(self.armed), 1)
 
 
 def main():
@@ -404,7 +422,7 @@ def main():
         """The K timed steps, with the kernel probes armed on every step."""
         probes = {"knn": Probe(_lib.P2E_PROBE_KNN, args.steps, dev) if path != "render" else None,
                   "mlp": Probe(_lib.P2E_PROBE_MLP, args.steps, dev) if path == "learned" else None,
-                  "blend": Probe(_lib.P2E_PROBE_BLEND, args.steps, dev, count=True)}
+                  "blend": Probe(_lib.P2E_PROBE_BLEND, args.steps, dev, counters=1)}
         for i in range(args.warmup):
             flush.fill_(i & 0xFF)
             frame(cams[i], path)
@@ -548,7 +566,24 @@ def main():
         line["beyond_frame"] = beyond_frame(torch, dev, est, cx, cc, gs, img, cams, flush, ev, st, hbm)
         # differentiation at scale: 200K points, 8 views at 512^2, Eq. 5 + SSIM
         from paper_2409_16504_gb300.train import time_differentiation
-        line["differentiation"] = time_differentiation(points=200_000, views=8, res=512, ssim_weight=0.2, reps=5)
+        bp = Probe(_lib.P2E_PROBE_BLEND_BWD, 5, dev, counters=3)
+        df = time_differentiation(points=200_000, views=8, res=512, ssim_weight=0.2, reps=5, probe=bp)
+        ms = bp.mean_ms()
+        n_eval, n_contrib, n_red = (bp.per_step_count(i) for i in range(3))
+        ops = BWD_FP32_PER_EVAL * n_eval + BWD_FP32_PER_CONTRIB * n_contrib + BWD_FP32_PER_REDUCTION * n_red
+        a = ops / (ms / 1e3) / 1e12
+        hb = BWD_BYTES_PER_KEY * df["keys"] + BWD_BYTES_PER_PIXEL * df["pixels"] + \
+            BWD_BYTES_PER_SLOT * df["points"] * df["views"]
+        line["rooflines"]["blend_bwd"] = {
+            "kernel": f"blend_bwd_kernel<{df['tile']}>", "bound": "alu", "achieved": a, "peak": fp32_peak,
+            "unit": "TFLOP/s", "frac": a / fp32_peak, "traffic": None, "ms": ms,
+            "workload": f"differentiation: {df['points']} points x {df['views']} views at {df['res']}^2",
+            "pairs_evaluated_per_launch": n_eval, "pairs_contributing_per_launch": n_contrib,
+            "warp_reductions_per_launch": n_red, "fp32_ops_per_launch": ops,
+            "peak_derivation": f"{sms} SMs x {FP32_LANES_PER_SM} fp32 lanes x {sm_mhz:.0f} MHz",
+            "hbm": {"achieved_gbs": hb / (ms / 1e3) / 1e9, "frac": hb / (ms / 1e3) / 1e9 / hbm,
+                    "algorithmic_bytes_per_launch": hb}}
+        line["differentiation"] = df
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(head_path)
     if rank == 0 and world == 1 and not args.no_serving and not args.no_extras:

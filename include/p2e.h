@@ -79,7 +79,11 @@ typedef struct {
  *               the key buffers (8 bytes per key of a chained segment), and
  *               has one warp per (tile, pixel block) take the rest;
  *               P2E_SCHEDULE_PER_BLOCK (1) has one warp composite all
- *               segments of every (tile, pixel block) in turn. */
+ *               segments of every (tile, pixel block) in turn.  In
+ *               p2e_render_backward AUTO walks tile lists longer than
+ *               4 x tile^2 splats as segments of that length in parallel
+ *               (gradients equal up to fp32 rounding order), PER_BLOCK
+ *               walks every list whole. */
 enum { P2E_SCHEDULE_AUTO = 0, P2E_SCHEDULE_PER_BLOCK = 1 };
 typedef struct {
     int32_t tile;
@@ -263,7 +267,14 @@ p2e_status p2e_render(const p2e_gaussians *g, const p2e_projected *proj, const p
  * rectangle, 3-sigma test, floor, stop) held fixed.  Per tile and pixel
  * the transmittance is recomputed from the tile's sorted list and `last`:
  * front to back for the final T, then back to front through the
- * contributing splats; no per-pixel lists are stored.  `alpha` (the
+ * contributing splats; no per-pixel lists are stored.  A list longer than
+ * 4 x tile^2 splats is split into segments of that length: a fold of each
+ * segment (its transmittance product and weighted sum per pixel) gives
+ * every segment's entering T and tail, and the segments' backward walks
+ * run in parallel.  The item table and the folds use the free halves of
+ * the bins' buffers (keys[1 - result], vals[1 - result], which
+ * p2e_render uses as scratch too); with cfg->schedule PER_BLOCK, or with
+ * no room there, lists are walked whole.  `alpha` (the
  * forward's alpha image) is not read and may be NULL: recovering T as
  * 1 - alpha would lose ~2.5e-4 relative accuracy on saturated pixels.
  * Inputs: the forward's arguments and outputs plus the upstream gradients
@@ -437,13 +448,18 @@ p2e_status p2e_point_raster(const float *xyz, const float *rgb, int64_t n, const
  *                                fast path; the few listed queries run after it)
  *            P2E_PROBE_BLEND     the compositing kernel of p2e_render
  *            P2E_PROBE_MLP       the learned head of p2e_estimate (mode 1)
+ *            P2E_PROBE_BLEND_BWD the per-tile kernel of p2e_render_backward
  *   probe    start_event / stop_event: cudaEvent_t (or NULL) recorded on
  *            the launching stream immediately before / after the kernel;
- *            count_dev: device uint64 (or NULL) the kernel adds its work
- *            count to (blend: the (pixel, splat) pairs it evaluated, every
- *            pass included; ignored by the other kernels).
- * The probe struct is copied; the events and counter stay caller-owned. */
-enum { P2E_PROBE_KNN = 0, P2E_PROBE_BLEND = 1, P2E_PROBE_MLP = 2, P2E_PROBE_COUNT = 3 };
+ *            count_dev: device uint64 counters (or NULL) the kernel adds
+ *            its work counts to.  BLEND: one, the (pixel, splat) pairs it
+ *            evaluated, every pass included.  BLEND_BWD: three, the pairs
+ *            evaluated by each of its two walks (front to back, back to
+ *            front: the same set), the contributing pairs among them, and
+ *            the warp reductions of per-splat gradients.  Ignored by the
+ *            other kernels.
+ * The probe struct is copied; the events and counters stay caller-owned. */
+enum { P2E_PROBE_KNN = 0, P2E_PROBE_BLEND = 1, P2E_PROBE_MLP = 2, P2E_PROBE_BLEND_BWD = 3, P2E_PROBE_COUNT = 4 };
 typedef struct {
     void *start_event;
     void *stop_event;

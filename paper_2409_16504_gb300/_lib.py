@@ -27,7 +27,7 @@ EXPORTS = ("p2e_default_config", "p2e_total_tiles", "p2e_scratch_bytes", "p2e_pr
            "p2e_estimate_global", "p2e_relight", "p2e_point_raster", "p2e_set_kernel_probe",
            "p2e_estimate_check", "p2e_selftest_timeout", "p2e_loss_ssim", "p2e_loss_splat_area",
            "p2e_status_string")
-P2E_PROBE_KNN, P2E_PROBE_BLEND, P2E_PROBE_MLP = 0, 1, 2
+P2E_PROBE_KNN, P2E_PROBE_BLEND, P2E_PROBE_MLP, P2E_PROBE_BLEND_BWD = 0, 1, 2, 3
 SELFTEST_SCRATCH_BYTES = 1 << 20
 P2E_MAX_LIGHTS = 8
 MLP_PARAMS = 15568

@@ -3,12 +3,13 @@
 // decision of the forward pass held fixed (differentiable splatting, used
 // to train the estimator end to end, Sec. 1 and 3.3).
 //
-// K7 (per tile, persistent over the non-empty-tile list): each pixel first
+// K7 (per tile, persistent over a list of work items): each pixel first
 // recomputes its final transmittance front to back over its tile list up to
 // the forward's `last` (the product of (1 - alpha_k) over the contributing
 // splats, re-decided with the forward's exact arithmetic, splat.cuh), then
 // walks the list back to front, recovering T_k = T_{k+1} / (1 - alpha_k).
-// No per-pixel lists are stored.  The final T is not taken from the alpha
+// No per-pixel lists are stored.  Lists longer than four splats per pixel
+// are cut into segments walked in parallel (see bwd_items_kernel).  The final T is not taken from the alpha
 // image: near saturation (T ~ 1e-4) the fp32 round trip alpha = 1 - T,
 // T = 1 - alpha loses ~3e-8 absolute, a relative error of ~2.5e-4 that the
 // division chain would carry to every splat of the pixel.  With
@@ -62,18 +63,218 @@ template <int B>
 struct BwdShape {
     static constexpr int NT = B * B;
     static constexpr int BATCH = NT < 256 ? NT : 256;
+    // a tile list longer than S splats (four per pixel) is walked in
+    // segments of S, each its own work item
+    static constexpr uint32_t S = 4u * NT;
 };
+
+// Segments of long tile lists.  Both walks of a pixel are sums and
+// products over its contributing splats in depth order, so they split at
+// segment boundaries: with, per segment m, the local transmittance
+// P_m = prod (1 - alpha_j) and the local weighted sum
+// F_m = sum alpha_j T'_j f_j (T' the transmittance from the segment's own
+// start), the transmittance entering segment s is prod_{m<s} P_m, the final
+// one prod_m P_m, and the running tail S at the end of segment s is
+// sum_{m>s} (prod_{l<m} P_l) F_m + T_final (gC.bg - gA).  A fold kernel
+// computes (P_m, F_m) for every segment and pixel; the gradient walk of
+// segment s starts from those, so a long list costs no serial walk.
+//
+// Item table (in the value buffer the sort left free): header words, then
+// (work index, segment) per item, the segmented tiles' items first (longest
+// lists start first); the folds (float2 per item and pixel) go in the free
+// key buffer.  Without room (a capacity below the key count, a missing
+// buffer) nothing is segmented.
+enum { kBwdItems = 0, kBwdOn = 1, kBwdCtrFold = 2, kBwdHdr = 4 };
+
+__global__ void __launch_bounds__(1024) bwd_items_kernel(const uint2 *__restrict__ ranges,
+                                                         const uint32_t *__restrict__ work,
+                                                         const int64_t *__restrict__ n_keys_dev,
+                                                         int64_t capacity, uint32_t S, uint32_t NT,
+                                                         uint32_t *__restrict__ table) {
+    __shared__ uint32_t s_sum[32], s_off[32];
+    __shared__ unsigned long long s_total;
+    __shared__ uint32_t s_carry;
+    const uint32_t n_work = work[0];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    if (threadIdx.x == 0) {
+        s_total = 0;
+        s_carry = 0;
+    }
+    __syncthreads();
+    auto nseg_of = [&](uint32_t w) -> uint32_t {
+        const uint2 r = ranges[work[2 + w]];
+        const uint32_t len = r.y - r.x;
+        return len > S ? (len + S - 1) / S : 0u;
+    };
+    unsigned long long mine = 0;
+    for (uint32_t w = threadIdx.x; w < n_work; w += blockDim.x) mine += nseg_of(w);
+    atomicAdd(&s_total, mine);
+    __syncthreads();
+    const unsigned long long total = s_total;
+    const bool fits = *n_keys_dev <= capacity && (long long)(kBwdHdr + 2 * total) <= capacity &&
+                      (long long)(total * NT) <= capacity;
+    if (threadIdx.x == 0) {
+        table[kBwdItems] = fits ? (uint32_t)total : 0u;
+        table[kBwdOn] = fits ? 1u : 0u;
+        table[kBwdCtrFold] = 0u;
+    }
+    if (!fits || total == 0) return;
+    for (uint32_t b0 = 0; b0 < n_work; b0 += blockDim.x) {
+        const uint32_t w = b0 + threadIdx.x;
+        const uint32_t v = w < n_work ? nseg_of(w) : 0u;
+        // exclusive block scan of v
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_sum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            const uint32_t t0 = lane < nw ? s_sum[lane] : 0u;
+            uint32_t t = t0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            s_off[lane] = t - t0;
+        }
+        __syncthreads();
+        const uint32_t base = s_carry + s_off[wid] + x - v;
+        for (uint32_t m = 0; m < v; ++m) {
+            table[kBwdHdr + 2 * (base + m)] = w;
+            table[kBwdHdr + 2 * (base + m) + 1] = m;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry = base + v;
+        __syncthreads();
+    }
+}
+
+// The upstream gradient of one pixel: rgb, normal, depth, alpha.
+__device__ __forceinline__ void load_upstream(const View &V, int64_t pix, int64_t HW, const float *d_rgb,
+                                              const float *d_nrm, const float *d_depth, const float *d_alpha,
+                                              float (&up)[8]) {
+    if (d_rgb)
+        for (int c = 0; c < 3; ++c) up[c] = d_rgb[3 * V.pix_base + c * HW + pix];
+    if (d_nrm)
+        for (int c = 0; c < 3; ++c) up[3 + c] = d_nrm[3 * V.pix_base + c * HW + pix];
+    if (d_depth) up[6] = d_depth[V.pix_base + pix];
+    if (d_alpha) up[7] = d_alpha[V.pix_base + pix];
+}
+
+// Fold of one segment per (item, pixel): (P_m, F_m) as defined above, the
+// discrete decisions exactly the forward's (splat.cuh).
+template <int B>
+__global__ void __launch_bounds__(BwdShape<B>::NT) bwd_fold_kernel(
+    const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ work,
+    uint32_t *__restrict__ table, float2 *__restrict__ fold,
+    const float4 *__restrict__ xy_depth, const float4 *__restrict__ conic_op, const ushort4 *__restrict__ rect,
+    const float4 *__restrict__ rgb, const float4 *__restrict__ normal, const uint32_t *__restrict__ last_img,
+    const float *__restrict__ d_rgb, const float *__restrict__ d_nrm, const float *__restrict__ d_depth,
+    __grid_constant__ const Views P) {
+    constexpr int NT = BwdShape<B>::NT, BATCH = BwdShape<B>::BATCH;
+    constexpr uint32_t S = BwdShape<B>::S;
+    __shared__ float4 s_off[BATCH], s_co[BATCH], s_cz[BATCH], s_nr[BATCH];
+    __shared__ ushort4 s_rc[BATCH];
+    __shared__ uint32_t s_item, s_end;
+    const int tid = threadIdx.x;
+    const int lx = tid % B, ly = tid / B;
+    const int wy0 = (tid & ~31) / B, wy1 = ((tid & ~31) + 31) / B;
+    const float lxf = (float)lx, lyf = (float)ly;
+    const float pw_min = -0.5f * P.sigma_mult * P.sigma_mult;
+    const float amax = P.alpha_max, afloor = P.alpha_floor;
+    const uint32_t n_items = table[kBwdItems];
+    for (;;) {
+        if (tid == 0) {
+            s_item = atomicAdd(table + kBwdCtrFold, 1u);
+            s_end = 0;
+        }
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= n_items) break;
+        const uint32_t w = table[kBwdHdr + 2 * item], seg = table[kBwdHdr + 2 * item + 1];
+        const int64_t tile = work[2 + w];
+        const int vi = view_of_tile(P, tile);
+        const View &V = P.v[vi];
+        const int64_t lt = tile - V.tile_base;
+        const int ty = (int)(lt / V.tiles_x), tx = (int)(lt - (int64_t)ty * V.tiles_x);
+        const int x0 = tx * B, y0 = ty * B;
+        const int px = x0 + lx, py = y0 + ly;
+        const bool inside = px < V.W && py < V.H;
+        const uint2 r = ranges[tile];
+        const uint32_t lo = r.x + seg * S, hi = min(r.y, lo + S);
+        const int64_t gbase = (int64_t)vi * P.n;
+        const int64_t HW = (int64_t)V.H * V.W;
+        const int64_t pix = (int64_t)py * V.W + px;
+        float up[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        uint32_t lim = lo;
+        if (inside) {
+            load_upstream(V, pix, HW, d_rgb, d_nrm, d_depth, nullptr, up);
+            lim = min(last_img[V.pix_base + pix], hi);
+            if (lim < lo) lim = lo;
+            atomicMax(&s_end, lim);
+        }
+        __syncthreads();
+        const uint32_t end = s_end;
+        float T = 1.f, F = 0.f;
+        for (uint32_t bstart = lo; bstart < end; bstart += BATCH) {
+            const int cnt = (int)min((uint32_t)BATCH, end - bstart);
+            if (tid < cnt) {
+                uint32_t g = __ldg(vals + bstart + tid);
+                if (g >= (uint32_t)P.n) g = 0;
+                const float4 xy = __ldg(xy_depth + gbase + g);
+                const float4 cc = __ldg(rgb + g);
+                s_off[tid] = splat_offset(xy, x0, y0);
+                s_co[tid] = __ldg(conic_op + gbase + g);
+                s_rc[tid] = __ldg(rect + gbase + g);
+                s_cz[tid] = make_float4(cc.x, cc.y, cc.z, xy.z);
+                s_nr[tid] = __ldg(normal + g);
+            }
+            __syncthreads();
+            if (inside) {
+                const int jend = (int)min((uint32_t)cnt, lim > bstart ? lim - bstart : 0u);
+                for (int j = 0; j < jend; ++j) {
+                    const ushort4 rc = s_rc[j];
+                    if ((int)rc.w < y0 + wy0 || (int)rc.y > y0 + wy1) continue;  // uniform over the warp
+                    const float4 o = s_off[j], co = s_co[j];
+                    float dx, dy;
+                    splat_delta(o, lxf, lyf, dx, dy);
+                    const float power = splat_power_d(co, dx, dy);
+                    if (power < pw_min) continue;
+                    float e;
+                    bool fr;
+                    const float alpha = splat_alpha(co.w, power, amax, e, fr);
+                    if (alpha < afloor) continue;
+                    const float4 cz = s_cz[j], nr = s_nr[j];
+                    const float f = up[0] * cz.x + up[1] * cz.y + up[2] * cz.z + up[3] * nr.x + up[4] * nr.y +
+                                    up[5] * nr.z + up[6] * cz.w;
+                    F = fmaf(alpha * T, f, F);
+                    T *= 1.f - alpha;
+                }
+            }
+            __syncthreads();
+        }
+        fold[(size_t)item * NT + tid] = make_float2(T, F);
+        __syncthreads();
+    }
+}
 
 template <int B>
 __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
     const uint32_t *__restrict__ work, uint32_t *__restrict__ work_counter,
+    const uint32_t *__restrict__ table, const float2 *__restrict__ fold,
     const float4 *__restrict__ xy_depth, const float4 *__restrict__ conic_op, const ushort4 *__restrict__ rect,
     const float4 *__restrict__ rgb, const float4 *__restrict__ normal,
     const float *__restrict__ alpha_img, const uint32_t *__restrict__ last_img,
     const float *__restrict__ d_rgb, const float *__restrict__ d_nrm, const float *__restrict__ d_depth,
-    const float *__restrict__ d_alpha, float *__restrict__ g2d, __grid_constant__ const Views P) {
+    const float *__restrict__ d_alpha, float *__restrict__ g2d, unsigned long long *__restrict__ count,
+    __grid_constant__ const Views P) {
     constexpr int NT = BwdShape<B>::NT, BATCH = BwdShape<B>::BATCH;
+    constexpr uint32_t S = BwdShape<B>::S;
     __shared__ float4 s_off[BATCH], s_co[BATCH], s_cz[BATCH], s_nr[BATCH];
     __shared__ ushort4 s_rc[BATCH];
     __shared__ uint32_t s_g[BATCH];
@@ -89,6 +290,13 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
     const float pw_min = -0.5f * P.sigma_mult * P.sigma_mult;
     const float amax = P.alpha_max, afloor = P.alpha_floor;
     const uint32_t n_work = work[0];
+    // items: the segments of long lists (table), then every tile whose list
+    // is not segmented, walked whole
+    const uint32_t n_multi = table ? table[kBwdItems] : 0u;
+    const bool seg_on = table && table[kBwdOn] != 0u;
+    // work counts for the probe: (pixel, splat) pairs evaluated in each of
+    // the two walks, the contributing ones among them, warp reductions
+    uint32_t n_eval = 0, n_contrib = 0, n_red = 0;
 
     for (;;) {
         if (tid == 0) {
@@ -97,8 +305,17 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
         }
         __syncthreads();
         const uint32_t item = s_item;
-        if (item >= n_work) break;
-        const int64_t tile = work[2 + item];
+        if (item >= n_multi + n_work) break;
+        const bool multi = item < n_multi;
+        const uint32_t w = multi ? table[kBwdHdr + 2 * item] : item - n_multi;
+        const uint32_t seg = multi ? table[kBwdHdr + 2 * item + 1] : 0u;
+        const int64_t tile = work[2 + w];
+        const uint2 r = ranges[tile];
+        if (!multi && seg_on && r.y - r.x > S) {  // walked as segments
+            __syncthreads();
+            continue;
+        }
+        const uint32_t lo = r.x + seg * S, hi = multi ? min(r.y, lo + S) : r.y;
         const int vi = view_of_tile(P, tile);
         const View &V = P.v[vi];
         const int64_t lt = tile - V.tile_base;
@@ -106,7 +323,6 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
         const int x0 = tx * B, y0 = ty * B;
         const int px = x0 + lx, py = y0 + ly;
         const bool inside = px < V.W && py < V.H;
-        const uint2 r = ranges[tile];
         const int64_t gbase = (int64_t)vi * P.n;
         const int64_t HW = (int64_t)V.H * V.W;
         const int64_t pix = (int64_t)py * V.W + px;
@@ -115,20 +331,34 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
         float T = 1.f;
         uint32_t lastp = 0;
         if (inside) {
-            if (d_rgb)
-                for (int c = 0; c < 3; ++c) up[c] = d_rgb[3 * V.pix_base + c * HW + pix];
-            if (d_nrm)
-                for (int c = 0; c < 3; ++c) up[3 + c] = d_nrm[3 * V.pix_base + c * HW + pix];
-            if (d_depth) up[6] = d_depth[V.pix_base + pix];
-            if (d_alpha) up[7] = d_alpha[V.pix_base + pix];
+            load_upstream(V, pix, HW, d_rgb, d_nrm, d_depth, d_alpha, up);
             lastp = last_img[V.pix_base + pix];
             if (lastp > r.y) lastp = r.y;  // only reachable with mismatched inputs
-            atomicMax(&s_end, lastp);
+            atomicMax(&s_end, min(lastp, hi));
         }
         __syncthreads();
-        const uint32_t end = s_end;
-        // final transmittance, front to back over [r.x, lastp)
-        for (uint32_t bstart = r.x; bstart < end; bstart += BATCH) {
+        const uint32_t end = max(s_end, lo);
+        const float cbg = up[0] * P.bg[0] + up[1] * P.bg[1] + up[2] * P.bg[2] - up[7];
+        float acc;
+        if (multi) {
+            // entering and final transmittance and the tail from the folds
+            const uint32_t nseg = (r.y - r.x + S - 1) / S, first = item - seg;
+            float tail = 0.f, t_in = 1.f, p_own = 1.f;
+            for (uint32_t m = 0; m < nseg; ++m) {
+                const float2 pf = fold[(size_t)(first + m) * NT + tid];
+                if (m == seg) {
+                    t_in = T;
+                    p_own = pf.x;
+                } else if (m > seg) {
+                    tail = fmaf(T, pf.y, tail);
+                }
+                T *= pf.x;
+            }
+            acc = tail + T * cbg;
+            T = t_in * p_own;
+        }
+        // final transmittance of a whole list, front to back over [r.x, lastp)
+        for (uint32_t bstart = lo; !multi && bstart < end; bstart += BATCH) {
             const int cnt = (int)min((uint32_t)BATCH, end - bstart);
             if (tid < cnt) {
                 uint32_t g = __ldg(vals + bstart + tid);
@@ -157,9 +387,10 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
             }
             __syncthreads();
         }
-        float acc = T * (up[0] * P.bg[0] + up[1] * P.bg[1] + up[2] * P.bg[2] - up[7]);
-        for (uint32_t bend = end; bend > r.x; bend = (bend - r.x > (uint32_t)BATCH) ? bend - BATCH : r.x) {
-            const uint32_t bstart = (bend - r.x > (uint32_t)BATCH) ? bend - BATCH : r.x;
+        if (!multi) acc = T * cbg;
+        // back to front over [lo, end)
+        for (uint32_t bend = end; bend > lo; bend = (bend - lo > (uint32_t)BATCH) ? bend - BATCH : lo) {
+            const uint32_t bstart = (bend - lo > (uint32_t)BATCH) ? bend - BATCH : lo;
             const int cnt = (int)(bend - bstart);
             for (int t = tid; t < cnt * QN; t += NT) (&s_acc[0][0])[t] = 0.f;
             if (tid < cnt) {
@@ -183,6 +414,7 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
                 for (int c = 0; c < QN; ++c) q[c] = 0.f;
                 bool contrib = false;
                 if (inside && bstart + (uint32_t)j < lastp) {
+                    ++n_eval;
                     const float4 o = s_off[j], co = s_co[j];
                     float dx, dy;
                     splat_delta(o, lxf, lyf, dx, dy);
@@ -193,6 +425,7 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
                         const float alpha = splat_alpha(co.w, power, amax, e, fr);
                         if (alpha >= afloor) {
                             contrib = true;
+                            ++n_contrib;
                             const float4 cz = s_cz[j], nr = s_nr[j];
                             const float om = 1.f - alpha;
                             const float Tk = T / om;
@@ -222,6 +455,7 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
+                    ++n_red;
                     // transposing butterfly: each step hands half of the
                     // channels a lane still holds to its partner, so 16
                     // channels take 8 + 4 + 2 + 1 + 1 shuffles; lane l ends
@@ -240,6 +474,14 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
             __syncthreads();
         }
         __syncthreads();
+    }
+    if (count) {
+        const uint32_t e = __reduce_add_sync(0xffffffffu, n_eval), c = __reduce_add_sync(0xffffffffu, n_contrib);
+        if (lane == 0) {
+            atomicAdd(count, (unsigned long long)e);
+            atomicAdd(count + 1, (unsigned long long)c);
+            atomicAdd(count + 2, (unsigned long long)n_red);
+        }
     }
 }
 
@@ -366,12 +608,33 @@ static cudaError_t launch_bwd(const p2e_gaussians *g, const p2e_projected *proj,
                               const Views &P, const float *alpha, const uint32_t *last,
                               const float *d_rgb, const float *d_normal, const float *d_depth,
                               const float *d_alpha, float *g2d, cudaStream_t st) {
-    const int grid = device_sms() * (B == 8 ? 8 : (B == 16 ? 2 : 1));
+    // persistent grids: as many CTAs as fit on an SM (64 registers a thread)
+    const int grid = device_sms() * (B == 8 ? 16 : (B == 16 ? 4 : 1));
+    const int other = 1 - bins->result;
+    const bool seg = P.schedule == P2E_SCHEDULE_AUTO && bins->capacity >= kBwdHdr && bins->keys[other] &&
+                     bins->vals[other] && bins->n_keys_dev;
+    uint32_t *table = seg ? bins->vals[other] : nullptr;
+    float2 *fold = seg ? (float2 *)bins->keys[other] : nullptr;
+    const p2e_kernel_probe *pr = kernel_probe(P2E_PROBE_BLEND_BWD);
+    probe_start(pr, st);
+    if (seg) {
+        bwd_items_kernel<<<1, 1024, 0, st>>>((const uint2 *)bins->ranges, bins->tile_work, bins->n_keys_dev,
+                                             bins->capacity, BwdShape<B>::S, BwdShape<B>::NT, table);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        bwd_fold_kernel<B><<<grid, BwdShape<B>::NT, 0, st>>>(
+            (const uint2 *)bins->ranges, bins->vals[bins->result], bins->tile_work, table, fold,
+            (const float4 *)proj->xy_depth, (const float4 *)proj->conic_op, (const ushort4 *)proj->rect,
+            (const float4 *)g->rgb, (const float4 *)g->normal, last, d_rgb, d_normal, d_depth, P);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     blend_bwd_kernel<B><<<grid, BwdShape<B>::NT, 0, st>>>(
-        (const uint2 *)bins->ranges, bins->vals[bins->result], bins->tile_work, bins->tile_work + 1,
+        (const uint2 *)bins->ranges, bins->vals[bins->result], bins->tile_work, bins->tile_work + 1, table, fold,
         (const float4 *)proj->xy_depth, (const float4 *)proj->conic_op, (const ushort4 *)proj->rect,
         (const float4 *)g->rgb,
-        (const float4 *)g->normal, alpha, last, d_rgb, d_normal, d_depth, d_alpha, g2d, P);
+        (const float4 *)g->normal, alpha, last, d_rgb, d_normal, d_depth, d_alpha, g2d,
+        pr ? (unsigned long long *)pr->count_dev : nullptr, P);
+    probe_stop(pr, st);
     return cudaGetLastError();
 }
 

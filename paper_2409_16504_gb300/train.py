@@ -218,12 +218,14 @@ class Trainer:
 
 
 def time_differentiation(points: int = 200_000, views: int = 8, res: int = 512, ssim_weight: float = 0.2,
-                         reps: int = 5, seed: int = 3, device="cuda", tile: int = 8) -> dict:
+                         reps: int = 5, seed: int = 3, device="cuda", tile: int = 8, probe=None) -> dict:
     """Forward and backward of the splatting at the differentiation scale:
     a ``points``-point humanoid (kNN-PCA Gaussians), ``views`` views at
     res x res, loss = Eq. 5 + ssim_weight x the SSIM term against the exact
     ray-cast views, gradients with respect to every Gaussian parameter.
-    Median CUDA-event milliseconds of each phase over ``reps`` runs."""
+    Median CUDA-event milliseconds of each phase over ``reps`` runs.
+    ``probe`` (optional, with ``arm(i)`` / ``disarm()``) is armed around
+    the backward of timed run i (a kernel probe of the library)."""
     sc = Scene(seed, points, views, res, device=device)
     tr = Trainer(points, ssim_weight=ssim_weight, device=device, cfg={"tile": tile})
     knn, g_pca, g, r, img = tr._forward(sc, learned=False)
@@ -237,8 +239,12 @@ def time_differentiation(points: int = 200_000, views: int = 8, res: int = 512, 
         e[1].record(st)
         d_rgb, d_nrm = tr._loss(sc, img)
         e[2].record(st)
+        if probe is not None and it >= 2:
+            probe.arm(it - 2)
         d = p2e_render_backward(g, r.proj, r.bins, sc.cams, r.cfg, img.alpha, img.last, d_rgb=d_rgb,
                                 d_normal=d_nrm)
+        if probe is not None:
+            probe.disarm()
         e[3].record(st)
         torch.cuda.synchronize()
         if it >= 2:
@@ -246,6 +252,7 @@ def time_differentiation(points: int = 200_000, views: int = 8, res: int = 512, 
     med = np.median(np.array(rows), 0)
     finite = all(bool(torch.isfinite(v).all()) for v in d.values())
     return dict(points=points, views=views, res=res, tile=tile, ssim_weight=ssim_weight, keys=r.n_keys,
+                pixels=views * res * res,
                 render_ms=float(med[0]), loss_ms=float(med[1]), backward_ms=float(med[2]),
                 total_ms=float(med.sum()), loss=float(tr.loss_dev.item()), gradients_finite=finite)
 

@@ -37,11 +37,15 @@ def _upstream(cams, g, cfg, seed):
     return ups
 
 
-def _gpu_grads(g, cams, cfg, ups):
+def _gpu_grads(g, cams, cfg, ups, lengths=None):
+    """The GPU gradients; ``lengths`` (a list) receives the tile list lengths."""
     from paper_2409_16504_gb300 import GaussianSet, Renderer, p2e_render_backward
     gs = GaussianSet.from_numpy(g)
-    r = Renderer(cfg, capacity=1 << 16)
+    r = Renderer(cfg, capacity=1 << 20)
     img = r.render(gs, cams)
+    if lengths is not None:
+        rg = r.bins.ranges.cpu().numpy().astype(np.int64)
+        lengths.extend((rg[:, 1] - rg[:, 0]).tolist())
 
     def planes(k0, k1):
         return torch.from_numpy(np.concatenate([u[k0:k1].reshape(-1) for u in ups]).astype(np.float32)).cuda()
@@ -97,6 +101,53 @@ def test_backward_opaque_humanoid(tile):
         assert np.abs(ref[k]).max() > 0
 
 
+@pytest.mark.parametrize("tile", [8, 16])
+def test_backward_segments_match_whole_walks(tile):
+    """Tile lists longer than 4 x tile^2 splats are walked as parallel
+    segments (schedule AUTO) or whole (PER_BLOCK): the opaque humanoid has
+    such lists, and both schedules agree with each other to fp32 rounding
+    order (1e-5 relative) and with the oracle (1e-4)."""
+    g, cams = _opaque_scene()
+    cfg = {**oracle.DEFAULT_CFG, "tile": tile, "bg": (0.2, 0.1, 0.3)}
+    ups = _upstream(cams, g, cfg, 60 + tile)
+    lens = []
+    seg = _gpu_grads(g, cams, {**cfg, "schedule": 0}, ups, lengths=lens)
+    lens = np.array(lens)
+    assert (lens > 4 * tile * tile).sum() >= 4, lens.max()
+    whole = _gpu_grads(g, cams, {**cfg, "schedule": 1}, ups)
+    ref = oracle.render_grad(g, cams, ups, cfg)
+    for k in oracle.GRAD_KEYS:
+        scale = np.abs(ref[k]).max()
+        assert np.abs(seg[k] - whole[k]).max() <= 1e-5 * scale + 1e-7, k
+        assert np.abs(seg[k] - ref[k]).max() <= 1e-4 * scale + 1e-6, k
+
+
+def test_backward_segments_on_a_very_long_list():
+    """Thousands of splats stacked on one 8-px tile (the list spans dozens of
+    256-splat segments, most pixels saturate early): segmented gradients
+    equal the oracle's."""
+    rng = np.random.default_rng(5)
+    n = 6000
+    cam = scenes.look_at_camera((0.0, 0.0, -2.0), (0, 0, 0), (0, 1, 0), 50, 24, 20)
+    g = dict(mean=np.column_stack([rng.uniform(-0.04, 0.04, n), rng.uniform(-0.04, 0.04, n),
+                                   rng.uniform(-0.5, 0.5, n)]),
+             scale=rng.uniform(0.008, 0.04, (n, 3)), quat=rng.standard_normal((n, 4)),
+             opacity=rng.uniform(0.02, 0.3, n), rgb=rng.uniform(0, 1, (n, 3)),
+             normal=rng.standard_normal((n, 3)))
+    g["normal"] /= np.linalg.norm(g["normal"], axis=1, keepdims=True)
+    g = {k: v.astype(np.float32) for k, v in g.items()}
+    cfg = {**oracle.DEFAULT_CFG, "tile": 8}
+    ups = _upstream([cam], g, cfg, 77)
+    lens = []
+    got = _gpu_grads(g, [cam], cfg, ups, lengths=lens)
+    assert max(lens) > 20 * 256, max(lens)
+    ref = oracle.render_grad(g, [cam], ups, cfg)
+    for k in oracle.GRAD_KEYS:
+        err = np.abs(got[k] - ref[k]).max()
+        tol = 1e-4 * np.abs(ref[k]).max() + 1e-6
+        assert err <= tol, f"{k}: max err {err:.3g} > {tol:.3g}"
+
+
 def test_autograd_function_equals_direct_call():
     from paper_2409_16504_gb300 import GaussianSet, render_differentiable
     g, _ = random_scene(31, 300, 48, 48)
@@ -124,3 +175,37 @@ def test_autograd_function_equals_direct_call():
     np.testing.assert_allclose(params[0].grad[:, 3].cpu().numpy(), direct["opacity"], rtol=1e-5, atol=1e-6)
     np.testing.assert_allclose(params[2].grad.cpu().numpy(), direct["quat"], rtol=1e-5, atol=1e-6)
     np.testing.assert_allclose(params[3].grad[:, :3].cpu().numpy(), direct["rgb"], rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_backward_probe_counts(tile):
+    """The work counters of the backward kernel's probe: its contributing
+    (pixel, splat) pairs are exactly the oracle's per-pixel contributor
+    counts summed (a scene with no knife-edge pixel), every reduction
+    carries 1..32 of them, and every contributing pair was evaluated."""
+    import ctypes as C
+    from paper_2409_16504_gb300 import GaussianSet, Renderer, _lib, p2e_render_backward
+    g, _ = random_scene(21, 400, 64, 64)
+    cams = _cams()
+    cfg = {**oracle.DEFAULT_CFG, "tile": tile}
+    refs = [oracle.render(g, c, cfg) for c in cams]
+    assert sum(int(r["flag"].sum()) for r in refs) == 0
+    want = sum(int(r["ncontrib"].sum()) for r in refs)
+    gs = GaussianSet.from_numpy(g)
+    r = Renderer(cfg, capacity=1 << 16)
+    img = r.render(gs, cams)
+    n_pix = sum(c["height"] * c["width"] for c in cams)
+    d_rgb = torch.ones(3 * n_pix, device="cuda")
+    count = torch.zeros(3, dtype=torch.int64, device="cuda")
+    lib = _lib.load()
+    p = _lib.P2EKernelProbe(None, None, count.data_ptr())
+    _lib.check("p2e_set_kernel_probe", lib.p2e_set_kernel_probe(_lib.P2E_PROBE_BLEND_BWD, C.byref(p)))
+    try:
+        p2e_render_backward(gs, r.proj, r.bins, cams, cfg, img.alpha, img.last, d_rgb=d_rgb)
+        torch.cuda.synchronize()
+    finally:
+        lib.p2e_set_kernel_probe(_lib.P2E_PROBE_BLEND_BWD, None)
+    n_eval, n_contrib, n_red = (int(v) for v in count.cpu())
+    assert n_contrib == want
+    assert n_eval >= n_contrib
+    assert n_contrib <= 32 * n_red and n_red <= n_contrib
