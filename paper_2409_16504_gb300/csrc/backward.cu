@@ -108,7 +108,9 @@ __global__ void __launch_bounds__(1024) bwd_items_kernel(const uint2 *__restrict
     };
     unsigned long long mine = 0;
     for (uint32_t w = threadIdx.x; w < n_work; w += blockDim.x) mine += nseg_of(w);
-    atomicAdd(&s_total, mine);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if (lane == 0 && mine) atomicAdd(&s_total, mine);  // one add per warp
     __syncthreads();
     const unsigned long long total = s_total;
     const bool fits = *n_keys_dev <= capacity && (long long)(kBwdHdr + 2 * total) <= capacity &&

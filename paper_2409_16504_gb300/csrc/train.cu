@@ -106,80 +106,109 @@ __global__ void __launch_bounds__(256) loss_eq5_kernel(const float *__restrict__
 //   C1 = 0.01^2, C2 = 0.03^2 (images in [0, 1]).
 // dS_p/dx_q = w(p - q) (A_p + 2 x_q B_p + y_q C_p), A = dS/dmx, B = dS/dExx,
 // C = dS/dExy, so dD/dx = -(w * A + 2 x (w * B) + y (w * C)) / N
-// (w symmetric).  The blurs are separable: a horizontal then a vertical
-// 11-tap pass, each its own kernel, over planes in scratch.
-constexpr int kSsimR = 5;  // window radius
+// (w symmetric).  The blurs are separable (11 taps along a row, then along
+// a column).  Two kernels, each over 32 x 16 output tiles of one (view,
+// channel) plane with its 5-pixel halo staged in shared memory (zeros
+// outside the image, which leave the window sums unchanged): the first
+// takes the five window sums, S and the maps A, B, C; the second blurs A,
+// B, C and adds the gradient.  Taps are summed in the same order (k = -5
+// .. 5, row pass first) in both, one fma per tap.
+constexpr int kSsimR = 5;                                  // window radius
+constexpr int kSsimTX = 32, kSsimTY = 16;                  // output tile
+constexpr int kSsimHX = kSsimTX + 2 * kSsimR, kSsimHY = kSsimTY + 2 * kSsimR;
+constexpr int kSsimThreads = 256;
 
 struct SsimViews {
     int32_t n_views;
     int32_t W[P2E_MAX_VIEWS], H[P2E_MAX_VIEWS];
-    int64_t base[P2E_MAX_VIEWS];  // first pixel of the view
+    int64_t base[P2E_MAX_VIEWS];     // first pixel of the view
+    int32_t tiles_x[P2E_MAX_VIEWS], tiles_y[P2E_MAX_VIEWS];
+    int64_t block_base[P2E_MAX_VIEWS + 1];  // first block of the view (3 planes of tiles)
     int64_t npix;
     float w[2 * kSsimR + 1];
 };
 
-// (view, local pixel) of element e of a [3][H][W]-per-view plane set
-__device__ __forceinline__ int ssim_view(const SsimViews &V, int64_t q) {
+// The plane and output tile of block b: view v, channel c, tile origin.
+struct SsimTile {
+    int v, c, x0, y0, W, H;
+    int64_t plane;  // offset of the (view, channel) plane
+};
+__device__ __forceinline__ SsimTile ssim_tile(const SsimViews &V, int64_t b) {
+    SsimTile t;
     int v = 0;
-    while (v + 1 < V.n_views && V.base[v + 1] <= q) ++v;
-    return v;
+    while (v + 1 < V.n_views && V.block_base[v + 1] <= b) ++v;
+    const int64_t local = b - V.block_base[v];
+    const int per_plane = V.tiles_x[v] * V.tiles_y[v];
+    t.v = v;
+    t.c = (int)(local / per_plane);
+    const int k = (int)(local - (int64_t)t.c * per_plane);
+    const int ty = k / V.tiles_x[v];
+    t.x0 = (k - ty * V.tiles_x[v]) * kSsimTX;
+    t.y0 = ty * kSsimTY;
+    t.W = V.W[v];
+    t.H = V.H[v];
+    t.plane = 3 * V.base[v] + (int64_t)t.c * t.W * t.H;
+    return t;
 }
 
-// pass 1 (horizontal) of the five products, one thread per (pixel, channel)
-__global__ void __launch_bounds__(256) ssim_h5_kernel(const float *__restrict__ x, const float *__restrict__ y,
-                                                      float *__restrict__ h5, __grid_constant__ const SsimViews V) {
-    const int64_t total = 3 * V.npix;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t q = e / 3;
-        const int c = (int)(e - 3 * q);
-        const int v = ssim_view(V, q);
-        const int64_t p = q - V.base[v];
-        const int W = V.W[v];
-        const int64_t HW = (int64_t)W * V.H[v];
-        const int64_t plane = 3 * V.base[v] + c * HW;
-        const int row = (int)(p / W), col = (int)(p - (int64_t)row * W);
+// Stage NP planes of the tile's halo region (zeros outside the image).
+template <int NP>
+__device__ __forceinline__ void ssim_stage(const SsimTile &t, const float *const (&src)[NP], int64_t stride,
+                                           float (*dst)[kSsimHY][kSsimHX]) {
+    for (int i = threadIdx.x; i < kSsimHY * kSsimHX; i += kSsimThreads) {
+        const int r = i / kSsimHX, c = i - r * kSsimHX;
+        const int gy = t.y0 - kSsimR + r, gx = t.x0 - kSsimR + c;
+        const bool in = gy >= 0 && gy < t.H && gx >= 0 && gx < t.W;
+        const int64_t o = t.plane + (int64_t)gy * t.W + gx;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) dst[p][r][c] = in ? src[p][(int64_t)p * stride + o] : 0.f;
+    }
+}
+
+// kernel 1: window sums, S (each block's sum added to an fp64 total) and
+// A, B, C per pixel
+__global__ void __launch_bounds__(kSsimThreads) ssim_stats_kernel(const float *__restrict__ x,
+                                                                  const float *__restrict__ y,
+                                                                  float *__restrict__ abc, double *s_total,
+                                                                  __grid_constant__ const SsimViews V) {
+    constexpr float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+    __shared__ float s_in[2][kSsimHY][kSsimHX];
+    __shared__ float s_row[5][kSsimHY][kSsimTX];
+    __shared__ float s_red[kSsimThreads / 32];
+    const SsimTile t = ssim_tile(V, blockIdx.x);
+    {
+        const float *const src[2] = {x, y};
+        ssim_stage<2>(t, src, 0, s_in);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSsimHY * kSsimTX; i += kSsimThreads) {
+        const int r = i / kSsimTX, c = i - r * kSsimTX;
         float s[5] = {0, 0, 0, 0, 0};
-        for (int k = -kSsimR; k <= kSsimR; ++k) {
-            const int cc = col + k;
-            if (cc < 0 || cc >= W) continue;
-            const float a = x[plane + (int64_t)row * W + cc], b = y[plane + (int64_t)row * W + cc];
-            const float wk = V.w[k + kSsimR];
+#pragma unroll
+        for (int k = 0; k <= 2 * kSsimR; ++k) {
+            const float a = s_in[0][r][c + k], b = s_in[1][r][c + k];
+            const float wk = V.w[k];
             s[0] = fmaf(wk, a, s[0]);
             s[1] = fmaf(wk, b, s[1]);
             s[2] = fmaf(wk, a * a, s[2]);
             s[3] = fmaf(wk, b * b, s[3]);
             s[4] = fmaf(wk, a * b, s[4]);
         }
-        const int64_t o = plane + p;
 #pragma unroll
-        for (int k = 0; k < 5; ++k) h5[k * 3 * V.npix + o] = s[k];
+        for (int j = 0; j < 5; ++j) s_row[j][r][c] = s[j];
     }
-}
-
-// pass 2 (vertical): the local statistics, S, and the derivative maps
-// A, B, C; adds -weight * S / N to the loss (one atomic per block)
-__global__ void __launch_bounds__(256) ssim_v5_kernel(const float *__restrict__ h5, float *__restrict__ abc,
-                                                      float weight, float *loss, __grid_constant__ const SsimViews V) {
-    constexpr float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
-    const int64_t total = 3 * V.npix;
+    __syncthreads();
     float acc = 0.f;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t q = e / 3;
-        const int c = (int)(e - 3 * q);
-        const int v = ssim_view(V, q);
-        const int64_t p = q - V.base[v];
-        const int W = V.W[v], H = V.H[v];
-        const int64_t HW = (int64_t)W * H;
-        const int64_t plane = 3 * V.base[v] + c * HW;
-        const int row = (int)(p / W), col = (int)(p - (int64_t)row * W);
+    for (int i = threadIdx.x; i < kSsimTY * kSsimTX; i += kSsimThreads) {
+        const int r = i / kSsimTX, c = i - r * kSsimTX;
+        const int gy = t.y0 + r, gx = t.x0 + c;
+        if (gy >= t.H || gx >= t.W) continue;
         float m[5] = {0, 0, 0, 0, 0};
-        for (int k = -kSsimR; k <= kSsimR; ++k) {
-            const int rr = row + k;
-            if (rr < 0 || rr >= H) continue;
-            const float wk = V.w[k + kSsimR];
-            const int64_t o = plane + (int64_t)rr * W + col;
 #pragma unroll
-            for (int j = 0; j < 5; ++j) m[j] = fmaf(wk, h5[j * 3 * V.npix + o], m[j]);
+        for (int k = 0; k <= 2 * kSsimR; ++k) {
+            const float wk = V.w[k];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) m[j] = fmaf(wk, s_row[j][r + k][c], m[j]);
         }
         const float mx = m[0], my = m[1];
         const float vx = m[2] - mx * mx, vy = m[3] - my * my, cxy = m[4] - mx * my;
@@ -187,84 +216,71 @@ __global__ void __launch_bounds__(256) ssim_v5_kernel(const float *__restrict__ 
         const float d1 = mx * mx + my * my + C1, d2 = vx + vy + C2;
         const float S = (n1 * n2) / (d1 * d2);
         acc += S;
-        const int64_t o = plane + p;
+        const int64_t o = t.plane + (int64_t)gy * t.W + gx;
         abc[o] = S * (2.f * my / n1 - 2.f * my / n2 - 2.f * mx / d1 + 2.f * mx / d2);
         abc[3 * V.npix + o] = -S / d2;
         abc[6 * V.npix + o] = 2.f * S / n2;
     }
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    __shared__ float sw[8];
-    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        float t = 0.f;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sw[k];
-        atomicAdd(loss, -weight * t / (float)total);
+        double tsum = 0.0;
+        for (int k = 0; k < kSsimThreads / 32; ++k) tsum += s_red[k];
+        atomicAdd(s_total, tsum);
     }
 }
 
-// pass 3 (horizontal) of A, B, C
-__global__ void __launch_bounds__(256) ssim_h3_kernel(const float *__restrict__ abc, float *__restrict__ h3,
-                                                      __grid_constant__ const SsimViews V) {
-    const int64_t total = 3 * V.npix;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t q = e / 3;
-        const int c = (int)(e - 3 * q);
-        const int v = ssim_view(V, q);
-        const int64_t p = q - V.base[v];
-        const int W = V.W[v];
-        const int64_t HW = (int64_t)W * V.H[v];
-        const int64_t plane = 3 * V.base[v] + c * HW;
-        const int row = (int)(p / W), col = (int)(p - (int64_t)row * W);
-        float s[3] = {0, 0, 0};
-        for (int k = -kSsimR; k <= kSsimR; ++k) {
-            const int cc = col + k;
-            if (cc < 0 || cc >= W) continue;
-            const float wk = V.w[k + kSsimR];
-            const int64_t o = plane + (int64_t)row * W + cc;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) s[j] = fmaf(wk, abc[j * 3 * V.npix + o], s[j]);
-        }
-        const int64_t o = plane + p;
-#pragma unroll
-        for (int j = 0; j < 3; ++j) h3[j * 3 * V.npix + o] = s[j];
-    }
+// loss += weight (1 - mean S), one add of the whole term
+__global__ void ssim_finish_kernel(float *loss, const double *s_total, float weight, int64_t n) {
+    if (threadIdx.x == 0) atomicAdd(loss, (float)((double)weight * (1.0 - *s_total / (double)n)));
 }
 
-// pass 4 (vertical): d_rgb += weight dD/dx
-__global__ void __launch_bounds__(256) ssim_grad_kernel(const float *__restrict__ x, const float *__restrict__ y,
-                                                        const float *__restrict__ h3, float weight,
-                                                        float *__restrict__ d_rgb, __grid_constant__ const SsimViews V) {
-    const int64_t total = 3 * V.npix;
-    const float scale = -weight / (float)total;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t q = e / 3;
-        const int c = (int)(e - 3 * q);
-        const int v = ssim_view(V, q);
-        const int64_t p = q - V.base[v];
-        const int W = V.W[v], H = V.H[v];
-        const int64_t HW = (int64_t)W * H;
-        const int64_t plane = 3 * V.base[v] + c * HW;
-        const int row = (int)(p / W), col = (int)(p - (int64_t)row * W);
+// kernel 2: d_rgb += weight dD/dx from the blurred A, B, C
+__global__ void __launch_bounds__(kSsimThreads) ssim_grad_kernel(const float *__restrict__ x,
+                                                                 const float *__restrict__ y,
+                                                                 const float *__restrict__ abc, float weight,
+                                                                 float *__restrict__ d_rgb,
+                                                                 __grid_constant__ const SsimViews V) {
+    __shared__ float s_in[3][kSsimHY][kSsimHX];
+    __shared__ float s_row[3][kSsimHY][kSsimTX];
+    const SsimTile t = ssim_tile(V, blockIdx.x);
+    {
+        const float *const src[3] = {abc, abc, abc};
+        ssim_stage<3>(t, src, 3 * V.npix, s_in);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSsimHY * kSsimTX; i += kSsimThreads) {
+        const int r = i / kSsimTX, c = i - r * kSsimTX;
         float s[3] = {0, 0, 0};
-        for (int k = -kSsimR; k <= kSsimR; ++k) {
-            const int rr = row + k;
-            if (rr < 0 || rr >= H) continue;
-            const float wk = V.w[k + kSsimR];
-            const int64_t o = plane + (int64_t)rr * W + col;
 #pragma unroll
-            for (int j = 0; j < 3; ++j) s[j] = fmaf(wk, h3[j * 3 * V.npix + o], s[j]);
+        for (int k = 0; k <= 2 * kSsimR; ++k) {
+            const float wk = V.w[k];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) s[j] = fmaf(wk, s_in[j][r][c + k], s[j]);
         }
-        const int64_t o = plane + p;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) s_row[j][r][c] = s[j];
+    }
+    __syncthreads();
+    const float scale = -weight / (float)(3 * V.npix);
+    for (int i = threadIdx.x; i < kSsimTY * kSsimTX; i += kSsimThreads) {
+        const int r = i / kSsimTX, c = i - r * kSsimTX;
+        const int gy = t.y0 + r, gx = t.x0 + c;
+        if (gy >= t.H || gx >= t.W) continue;
+        float s[3] = {0, 0, 0};
+#pragma unroll
+        for (int k = 0; k <= 2 * kSsimR; ++k) {
+            const float wk = V.w[k];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) s[j] = fmaf(wk, s_row[j][r + k][c], s[j]);
+        }
+        const int64_t o = t.plane + (int64_t)gy * t.W + gx;
         d_rgb[o] += scale * (s[0] + 2.f * x[o] * s[1] + y[o] * s[2]);
     }
 }
 
 size_t ssim_scratch_bytes(int64_t npix) { return (size_t)8 * 3 * (size_t)npix * sizeof(float); }
-
-__global__ void ssim_add_kernel(float *loss, float v) {
-    if (threadIdx.x == 0) atomicAdd(loss, v);
-}
 
 // ------------------------------------------------------------ MLP backward
 // One 128-point tile per step (the UMMA M dimension), persistent CTAs of
@@ -700,17 +716,22 @@ p2e_status p2e_loss_ssim(const float *rgb, const float *gt_rgb, const int32_t *v
     double ws = 0.0;
     for (int k = -kSsimR; k <= kSsimR; ++k) ws += exp(-(double)(k * k) / (2.0 * 1.5 * 1.5));
     for (int k = -kSsimR; k <= kSsimR; ++k) V.w[k + kSsimR] = (float)(exp(-(double)(k * k) / (2.0 * 1.5 * 1.5)) / ws);
-    float *h5 = (float *)scratch;                 // 5 planes x 3 channels
-    float *abc = h5 + (size_t)5 * 3 * tot;        // 3 planes x 3 channels
-    float *h3 = h5;                               // reused once the statistics are taken
+    float *abc = (float *)scratch;  // A, B, C: 3 planes x 3 channels, then the fp64 sum of S
+    double *s_total = (double *)((char *)scratch + (((size_t)9 * tot * sizeof(float) + 7) & ~(size_t)7));
+    int64_t blocks = 0;
+    for (int v = 0; v < n_views; ++v) {
+        V.tiles_x[v] = (V.W[v] + kSsimTX - 1) / kSsimTX;
+        V.tiles_y[v] = (V.H[v] + kSsimTY - 1) / kSsimTY;
+        V.block_base[v] = blocks;
+        blocks += 3 * (int64_t)V.tiles_x[v] * V.tiles_y[v];
+    }
+    V.block_base[n_views] = blocks;
+    if (blocks > 0x7fffffff) return P2E_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    const unsigned grid = (unsigned)std::min<int64_t>((3 * tot + 255) / 256, (int64_t)device_sms() * 8);
-    // the constant part of D: + weight (D = 1 - mean S)
-    ssim_add_kernel<<<1, 1, 0, st>>>(loss_dev, weight);
-    ssim_h5_kernel<<<grid, 256, 0, st>>>(rgb, gt_rgb, h5, V);
-    ssim_v5_kernel<<<grid, 256, 0, st>>>(h5, abc, weight, loss_dev, V);
-    ssim_h3_kernel<<<grid, 256, 0, st>>>(abc, h3, V);
-    ssim_grad_kernel<<<grid, 256, 0, st>>>(rgb, gt_rgb, h3, weight, d_rgb, V);
+    if (cudaMemsetAsync(s_total, 0, sizeof(double), st) != cudaSuccess) return P2E_ERR_CUDA;
+    ssim_stats_kernel<<<(unsigned)blocks, kSsimThreads, 0, st>>>(rgb, gt_rgb, abc, s_total, V);
+    ssim_finish_kernel<<<1, 32, 0, st>>>(loss_dev, s_total, weight, 3 * tot);
+    ssim_grad_kernel<<<(unsigned)blocks, kSsimThreads, 0, st>>>(rgb, gt_rgb, abc, weight, d_rgb, V);
     return cudaGetLastError() == cudaSuccess ? P2E_OK : P2E_ERR_CUDA;
 }
 
