@@ -79,12 +79,45 @@ struct BwdShape {
 // computes (P_m, F_m) for every segment and pixel; the gradient walk of
 // segment s starts from those, so a long list costs no serial walk.
 //
-// Item table (in the value buffer the sort left free): header words, then
-// (work index, segment) per item, the segmented tiles' items first (longest
-// lists start first); the folds (float2 per item and pixel) go in the free
-// key buffer.  Without room (a capacity below the key count, a missing
-// buffer) nothing is segmented.
+// Only the part of a list before the tile's walk end (the largest `last` of
+// its pixels) is walked, so only that part is segmented: segments past it
+// have no item.
+//
+// Item table (in the value buffer the sort left free): header words, the
+// walk end of every work tile, then (work index, segment) per item (the
+// segmented tiles' items, longest lists first); the folds (float2 per item
+// and pixel) go in the free key buffer.  Without room (a capacity below the
+// key count, a missing buffer) nothing is segmented.
 enum { kBwdItems = 0, kBwdOn = 1, kBwdCtrFold = 2, kBwdHdr = 4 };
+
+// Walk end of every work tile: the largest `last` of its pixels (at least
+// the list start), one warp per tile.
+template <int B>
+__global__ void __launch_bounds__(256) bwd_tile_end_kernel(const uint2 *__restrict__ ranges,
+                                                           const uint32_t *__restrict__ work,
+                                                           const uint32_t *__restrict__ last_img, int64_t capacity,
+                                                           uint32_t *__restrict__ table,
+                                                           __grid_constant__ const Views P) {
+    const uint32_t n_work = work[0];
+    if ((int64_t)kBwdHdr + n_work > capacity) return;  // no room: nothing is segmented
+    const int lane = threadIdx.x & 31;
+    const uint32_t nw = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n_work; w += nw) {
+        const int64_t tile = work[2 + w];
+        const int vi = view_of_tile(P, tile);
+        const View &V = P.v[vi];
+        const int64_t lt = tile - V.tile_base;
+        const int ty = (int)(lt / V.tiles_x), tx = (int)(lt - (int64_t)ty * V.tiles_x);
+        const uint2 r = ranges[tile];
+        uint32_t m = r.x;
+        for (int p = lane; p < B * B; p += 32) {
+            const int px = tx * B + p % B, py = ty * B + p / B;
+            if (px < V.W && py < V.H) m = max(m, min(last_img[V.pix_base + (int64_t)py * V.W + px], r.y));
+        }
+        m = __reduce_max_sync(0xffffffffu, m);
+        if (lane == 0) table[kBwdHdr + w] = m;
+    }
+}
 
 __global__ void __launch_bounds__(1024) bwd_items_kernel(const uint2 *__restrict__ ranges,
                                                          const uint32_t *__restrict__ work,
@@ -101,20 +134,22 @@ __global__ void __launch_bounds__(1024) bwd_items_kernel(const uint2 *__restrict
         s_carry = 0;
     }
     __syncthreads();
+    const bool room = (int64_t)kBwdHdr + n_work <= capacity;  // the walk ends were written
+    const uint32_t *tile_end = table + kBwdHdr;
     auto nseg_of = [&](uint32_t w) -> uint32_t {
-        const uint2 r = ranges[work[2 + w]];
-        const uint32_t len = r.y - r.x;
+        const uint32_t len = tile_end[w] - ranges[work[2 + w]].x;
         return len > S ? (len + S - 1) / S : 0u;
     };
     unsigned long long mine = 0;
-    for (uint32_t w = threadIdx.x; w < n_work; w += blockDim.x) mine += nseg_of(w);
+    for (uint32_t w = threadIdx.x; room && w < n_work; w += blockDim.x) mine += nseg_of(w);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
     if (lane == 0 && mine) atomicAdd(&s_total, mine);  // one add per warp
     __syncthreads();
     const unsigned long long total = s_total;
-    const bool fits = *n_keys_dev <= capacity && (long long)(kBwdHdr + 2 * total) <= capacity &&
-                      (long long)(total * NT) <= capacity;
+    const bool fits = room && *n_keys_dev <= capacity &&
+                      (long long)(kBwdHdr + n_work + 2 * total) <= capacity && (long long)(total * NT) <= capacity;
+    uint32_t *items = table + kBwdHdr + n_work;
     if (threadIdx.x == 0) {
         table[kBwdItems] = fits ? (uint32_t)total : 0u;
         table[kBwdOn] = fits ? 1u : 0u;
@@ -146,8 +181,8 @@ __global__ void __launch_bounds__(1024) bwd_items_kernel(const uint2 *__restrict
         __syncthreads();
         const uint32_t base = s_carry + s_off[wid] + x - v;
         for (uint32_t m = 0; m < v; ++m) {
-            table[kBwdHdr + 2 * (base + m)] = w;
-            table[kBwdHdr + 2 * (base + m) + 1] = m;
+            items[2 * (base + m)] = w;
+            items[2 * (base + m) + 1] = m;
         }
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) s_carry = base + v;
@@ -189,6 +224,7 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) bwd_fold_kernel(
     const float pw_min = -0.5f * P.sigma_mult * P.sigma_mult;
     const float amax = P.alpha_max, afloor = P.alpha_floor;
     const uint32_t n_items = table[kBwdItems];
+    const uint32_t *items = table + kBwdHdr + work[0];
     for (;;) {
         if (tid == 0) {
             s_item = atomicAdd(table + kBwdCtrFold, 1u);
@@ -197,7 +233,7 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) bwd_fold_kernel(
         __syncthreads();
         const uint32_t item = s_item;
         if (item >= n_items) break;
-        const uint32_t w = table[kBwdHdr + 2 * item], seg = table[kBwdHdr + 2 * item + 1];
+        const uint32_t w = items[2 * item], seg = items[2 * item + 1];
         const int64_t tile = work[2 + w];
         const int vi = view_of_tile(P, tile);
         const View &V = P.v[vi];
@@ -296,6 +332,8 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
     // is not segmented, walked whole
     const uint32_t n_multi = table ? table[kBwdItems] : 0u;
     const bool seg_on = table && table[kBwdOn] != 0u;
+    const uint32_t *tile_end = seg_on ? table + kBwdHdr : nullptr;
+    const uint32_t *items = seg_on ? table + kBwdHdr + n_work : nullptr;
     // work counts for the probe: (pixel, splat) pairs evaluated in each of
     // the two walks, the contributing ones among them, warp reductions
     uint32_t n_eval = 0, n_contrib = 0, n_red = 0;
@@ -309,11 +347,12 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
         const uint32_t item = s_item;
         if (item >= n_multi + n_work) break;
         const bool multi = item < n_multi;
-        const uint32_t w = multi ? table[kBwdHdr + 2 * item] : item - n_multi;
-        const uint32_t seg = multi ? table[kBwdHdr + 2 * item + 1] : 0u;
+        const uint32_t w = multi ? items[2 * item] : item - n_multi;
+        const uint32_t seg = multi ? items[2 * item + 1] : 0u;
         const int64_t tile = work[2 + w];
         const uint2 r = ranges[tile];
-        if (!multi && seg_on && r.y - r.x > S) {  // walked as segments
+        const uint32_t walk = seg_on ? tile_end[w] - r.x : r.y - r.x;  // length of the walked part
+        if (!multi && seg_on && (walk > S || walk == 0)) {  // walked as segments, or not at all
             __syncthreads();
             continue;
         }
@@ -344,7 +383,7 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
         float acc;
         if (multi) {
             // entering and final transmittance and the tail from the folds
-            const uint32_t nseg = (r.y - r.x + S - 1) / S, first = item - seg;
+            const uint32_t nseg = (walk + S - 1) / S, first = item - seg;
             float tail = 0.f, t_in = 1.f, p_own = 1.f;
             for (uint32_t m = 0; m < nseg; ++m) {
                 const float2 pf = fold[(size_t)(first + m) * NT + tid];
@@ -620,6 +659,8 @@ static cudaError_t launch_bwd(const p2e_gaussians *g, const p2e_projected *proj,
     const p2e_kernel_probe *pr = kernel_probe(P2E_PROBE_BLEND_BWD);
     probe_start(pr, st);
     if (seg) {
+        bwd_tile_end_kernel<B><<<device_sms() * 2, 256, 0, st>>>((const uint2 *)bins->ranges, bins->tile_work, last,
+                                                                 bins->capacity, table, P);
         bwd_items_kernel<<<1, 1024, 0, st>>>((const uint2 *)bins->ranges, bins->tile_work, bins->n_keys_dev,
                                              bins->capacity, BwdShape<B>::S, BwdShape<B>::NT, table);
         cudaError_t e = cudaGetLastError();
