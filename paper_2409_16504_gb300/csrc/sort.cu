@@ -105,6 +105,13 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+// A look-back word is read for its own value only (no data published with
+// it), so several can be in flight at once.
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
 __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -326,6 +333,7 @@ __global__ void __launch_bounds__(256) digit_hist_kernel(const uint64_t *__restr
 }
 
 constexpr uint32_t kSFlagAgg = 1u << 30, kSFlagPre = 2u << 30, kSValMask = (1u << 30) - 1;
+constexpr int kLookWindow = 16;  // predecessors read per look-back round trip
 
 struct __align__(16) SortSmem {
     uint64_t keys[kSortTile];
@@ -411,18 +419,36 @@ __global__ void __launch_bounds__(kSortThreads) radix_pass_kernel(
         st_release_u32(st, kSFlagPre | cnt);
     } else {
         st_release_u32(st, kSFlagAgg | cnt);
+        // the predecessors' words kLookWindow at a time (one round trip):
+        // add aggregates up to the first inclusive prefix, or up to the
+        // first tile not yet published and read again from there
         int64_t p = tile - 1;
         uint32_t spins = 0;
         while (p >= 0) {
-            const uint32_t w = ld_acquire_u32(sort_state + (size_t)p * kRadix + d);
-            if ((w >> 30) == 0) {
+            uint32_t w[kLookWindow];
+#pragma unroll
+            for (int i = 0; i < kLookWindow; ++i)
+                w[i] = p - i >= 0 ? ld_relaxed_u32(sort_state + (size_t)(p - i) * kRadix + d) : kSFlagPre;
+            int used = kLookWindow;
+            bool done = false;
+#pragma unroll
+            for (int i = kLookWindow - 1; i >= 0; --i) {  // find the first stop in window order
+                const uint32_t f = w[i] >> 30;
+                if (f != 1u) {
+                    used = i;
+                    done = f == 2u;
+                }
+            }
+            // w[0 .. used) are aggregates; w[used] (if done) the inclusive prefix
+#pragma unroll
+            for (int i = 0; i < kLookWindow; ++i)
+                if (i < used || (done && i == used)) prefix += w[i] & kSValMask;
+            if (done) break;
+            p -= used;
+            if (used < kLookWindow) {  // stopped at a tile not yet published
                 if (++spins > spin_limit) { atomicExch(status, (int32_t)P2E_ERR_TIMEOUT); break; }
                 backoff_lb(spins);
-                continue;
             }
-            prefix += w & kSValMask;
-            if ((w >> 30) == 2) break;
-            --p;
         }
         st_release_u32(st, kSFlagPre | (uint32_t)(prefix + cnt));
     }
