@@ -103,6 +103,11 @@ NCU_TRAFFIC = {
               "sha256_16": "ae1d3d0a5411ef65", "bytes": 373_008_000},
     "mlp": {"kernel": "mlp_estimate_kernel", "sources": [_CSRC + "mlp.cu", _CSRC + "tcgen05.cuh"],
             "sha256_16": "7d49e064b1b85464", "bytes": 135_280_000},
+    # the backward's compositing part (walk ends, item table, folds, gradient
+    # walks), one launch each, on the differentiation workload
+    "blend_bwd": {"kernel": "bwd_tile_end + bwd_items + bwd_fold + blend_bwd_kernel<8>", "tile": 8,
+                  "sources": [_CSRC + "backward.cu", _CSRC + "splat.cuh"],
+                  "sha256_16": "3fc5866c624d49e7", "bytes": 308_912_128},
 }
 
 
@@ -577,7 +582,7 @@ def main():
         line["rooflines"]["blend_bwd"] = {
             "kernel": f"bwd_items + bwd_fold + blend_bwd_kernel<{df['tile']}> (the backward's compositing)",
             "bound": "alu", "achieved": a, "peak": fp32_peak,
-            "unit": "TFLOP/s", "frac": a / fp32_peak, "traffic": None, "ms": ms,
+            "unit": "TFLOP/s", "frac": a / fp32_peak, "traffic": ncu_traffic("blend_bwd", df["tile"]), "ms": ms,
             "workload": f"differentiation: {df['points']} points x {df['views']} views at {df['res']}^2",
             "pairs_evaluated_per_launch": n_eval, "pairs_contributing_per_launch": n_contrib,
             "warp_reductions_per_launch": n_red, "fp32_ops_per_launch": ops,
