@@ -33,3 +33,65 @@ def test_differentiation_200k_8x512():
     l1 = float(tr.loss_dev.item())
     print(f"loss {l0:.5f} -> {l1:.5f} after a step on the colours")
     assert l1 < l0
+
+
+def test_backward_full_scale_windows_match_oracle():
+    """Element-wise parity at the differentiation's own size: the 200K-point
+    humanoid's kNN-PCA Gaussians, 8 views at 512^2, 8-px tiles (lists of
+    thousands of splats, walked as segments), with the upstream gradient
+    non-zero only inside 24 x 24 windows of three views, each around the
+    view's longest tile list and not aligned to the tiles.  Only splats that
+    reach a window get a gradient, and the oracle computes those exactly on
+    cropped cameras (the principal point moved by the window's origin) over
+    all 200K Gaussians.  Tolerance as the small scenes: 1e-4 of each
+    tensor's largest entry."""
+    import oracle
+    from paper_2409_16504_gb300 import Renderer, p2e_render_backward
+    from paper_2409_16504_gb300.estimate import PCA, Estimator, cloud_tensors
+    from paper_2409_16504_gb300.train import scene_parts
+    _, xyz, rgb, cams = scene_parts(3, 200_000, 8, 512)
+    cx, cc = cloud_tensors(xyz, rgb)
+    gs = Estimator(len(xyz))(cx, cc, mode=PCA)
+    cfg = {**oracle.DEFAULT_CFG, "tile": 8}
+    r = Renderer(cfg, capacity=1 << 23)
+    img = r.render(gs, cams)
+    torch.cuda.synchronize()
+    h = lambda t: t.cpu().numpy()  # noqa: E731
+    g = dict(mean=h(gs.mean_op[:, :3]), opacity=h(gs.mean_op[:, 3]), scale=h(gs.scale[:, :3]), quat=h(gs.quat),
+             rgb=h(gs.rgb[:, :3]), normal=h(gs.normal[:, :3]))
+    rg = r.bins.ranges.cpu().numpy().astype(np.int64)
+    lens = rg[:, 1] - rg[:, 0]
+    tiles_x, res, w = 512 // 8, 512, 24
+    per_view = tiles_x * tiles_x
+    rng = np.random.default_rng(11)
+    ups_full = [np.zeros((8, res, res)) for _ in cams]
+    crops, ups_crop, longest = [], [], 0
+    for v in (1, 4, 6):
+        lv = lens[v * per_view:(v + 1) * per_view]
+        t = int(np.argmax(lv))
+        longest = max(longest, int(lv[t]))
+        ty, tx = divmod(t, tiles_x)
+        x0 = int(np.clip(tx * 8 - 5, 0, res - w))
+        y0 = int(np.clip(ty * 8 - 7, 0, res - w))
+        crop = dict(cams[v], cx=cams[v]["cx"] - x0, cy=cams[v]["cy"] - y0, width=w, height=w)
+        u = rng.standard_normal((8, w, w))
+        u[:, oracle.render(g, crop, cfg)["flag"]] = 0.0  # knife edges: fp32 and fp64 may decide apart
+        ups_full[v][:, y0:y0 + w, x0:x0 + w] = u
+        crops.append(crop)
+        ups_crop.append(u)
+    assert longest > 4 * 256, longest  # the windows lie on lists walked as several segments
+
+    def planes(k0, k1):
+        return torch.from_numpy(np.concatenate([u[k0:k1].reshape(-1) for u in ups_full]).astype(np.float32)).cuda()
+
+    d = p2e_render_backward(gs, r.proj, r.bins, cams, cfg, img.alpha, img.last, d_rgb=planes(0, 3),
+                            d_normal=planes(3, 6), d_depth=planes(6, 7), d_alpha=planes(7, 8))
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy().astype(np.float64) for k, v in d.items()}
+    ref = oracle.render_grad(g, crops, ups_crop, cfg)
+    for k in oracle.GRAD_KEYS:
+        scale = np.abs(ref[k]).max()
+        err = np.abs(got[k] - ref[k]).max()
+        print(f"{k}: max |ref| {scale:.3g}, max err {err:.3g}")
+        assert scale > 0
+        assert err <= 1e-4 * scale + 1e-6, f"{k}: max err {err:.3g} > {1e-4 * scale + 1e-6:.3g}"
