@@ -85,9 +85,10 @@ struct BwdShape {
 //
 // Item table (in the value buffer the sort left free): header words, the
 // walk end of every work tile, then (work index, segment) per item (the
-// segmented tiles' items, longest lists first); the folds (float2 per item
-// and pixel) go in the free key buffer.  Without room (a capacity below the
-// key count, a missing buffer) nothing is segmented.
+// segmented tiles' items in the work list's order: longest length class
+// first); the folds (float2 per item and pixel) go in the free key buffer.
+// Without room (a capacity below the key count, a missing buffer) nothing
+// is segmented.
 enum { kBwdItems = 0, kBwdOn = 1, kBwdCtrFold = 2, kBwdHdr = 4 };
 
 // Walk end of every work tile: the largest `last` of its pixels (at least
