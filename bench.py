@@ -103,6 +103,13 @@ NCU_TRAFFIC = {
               "sha256_16": "ae1d3d0a5411ef65", "bytes": 373_008_000},
     "mlp": {"kernel": "mlp_estimate_kernel", "sources": [_CSRC + "mlp.cu", _CSRC + "tcgen05.cuh"],
             "sha256_16": "7d49e064b1b85464", "bytes": 135_280_000},
+    "project": {"kernel": "project_kernel", "sources": [_CSRC + "project.cu"],
+                "sha256_16": "aff9ed682ee64b66", "bytes": 40_470_000},
+    # the whole binning stage of one learned frame (12 launches: depth keys,
+    # six radix passes, emission, ranges, work list), the mean of the steady
+    # frames of one capture (~3.0M keys)
+    "sort_bin": {"kernel": "p2e_sort_bin stage", "tile": 8, "sources": [_CSRC + "sort.cu"],
+                 "sha256_16": "df8143ffee336acc", "bytes": 218_800_000},
     # the backward's compositing part (walk ends, item table, folds, gradient
     # walks), one launch each, on the differentiation workload
     "blend_bwd": {"kernel": "bwd_tile_end + bwd_items + bwd_fold + blend_bwd_kernel<8>", "tile": 8,
@@ -527,14 +534,15 @@ def main():
     # is a stage of several, reported as such)
     a = PROJECT_BYTES_PER_GAUSSIAN * n / (hs["stage"]["project"] / 1e3) / 1e9
     rooflines["project"] = {"kernel": "project_kernel", "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
-                            "frac": a / hbm, "traffic": None, "ms": hs["stage"]["project"],
+                            "frac": a / hbm, "traffic": ncu_traffic("project"), "ms": hs["stage"]["project"],
                             "algorithmic_bytes_per_launch": PROJECT_BYTES_PER_GAUSSIAN * n,
                             "peak_source": src_peak, "timed": "stage events (one launch)"}
     alg = SORT_BYTES_PER_GAUSSIAN * n + SORT_BYTES_PER_KEY * n_keys
     a = alg / (hs["stage"]["sort_bin"] / 1e3) / 1e9
     rooflines["sort_bin"] = {"kernel": "p2e_sort_bin stage (depth keys, 6 radix passes, emission, ranges)",
                              "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
-                             "traffic": None, "ms": hs["stage"]["sort_bin"], "algorithmic_bytes_per_call": alg,
+                             "traffic": ncu_traffic("sort_bin", args.tile), "ms": hs["stage"]["sort_bin"],
+                             "algorithmic_bytes_per_call": alg,
                              "peak_source": src_peak, "timed": "stage events (~12 launches)"}
     dom = max((k for k in rooflines if k != "sort_bin"), key=lambda k: rooflines[k]["ms"])  # one kernel
 
