@@ -209,3 +209,35 @@ def test_backward_probe_counts(tile):
     assert n_contrib == want
     assert n_eval >= n_contrib
     assert n_contrib <= 32 * n_red and n_red <= n_contrib
+
+
+@pytest.mark.parametrize("tile", [8, 16])
+def test_backward_empty_culled_and_unreached(tile):
+    """Degenerate inputs of the backward: no Gaussians, every Gaussian
+    culled (no keys, no work tiles), and splats that all fall below the
+    alpha floor (lists that no pixel walks: every walk end is the list
+    start).  The call succeeds and every gradient is zero."""
+    from paper_2409_16504_gb300 import GaussianSet, Renderer, p2e_render_backward
+    g, _ = random_scene(7, 300, 40, 40)
+    cams = _cams()
+    cfg = {**oracle.DEFAULT_CFG, "tile": tile}
+    n_pix = sum(c["height"] * c["width"] for c in cams)
+    faint = {k: v.copy() for k, v in g.items()}
+    faint["opacity"][:] = 1e-4  # alpha <= 1e-4 < 1/255 everywhere
+    culled = {k: v.copy() for k, v in g.items()}
+    culled["mean"][:] = (0.0, 0.0, -2.5)  # behind both cameras
+    empty = {k: v[:0] for k, v in g.items()}
+    for name, scene in (("empty", empty), ("culled", culled), ("faint", faint)):
+        gs = GaussianSet.from_numpy(scene)
+        r = Renderer(cfg, capacity=1 << 16)
+        img = r.render(gs, cams)
+        d = p2e_render_backward(gs, r.proj, r.bins, cams, cfg, img.alpha, img.last,
+                                d_rgb=torch.ones(3 * n_pix, device="cuda"),
+                                d_normal=torch.ones(3 * n_pix, device="cuda"),
+                                d_depth=torch.ones(n_pix, device="cuda"), d_alpha=torch.ones(n_pix, device="cuda"))
+        torch.cuda.synchronize()
+        if name == "faint":
+            assert r.n_keys > 0
+        for k, v in d.items():
+            assert v.shape[0] == len(scene["mean"]), (name, k)
+            assert not v.any(), (name, k)
