@@ -469,12 +469,14 @@ __global__ void __launch_bounds__(BwdShape<B>::NT) blend_bwd_kernel(
                             contrib = true;
                             ++n_contrib;
                             const float4 cz = s_cz[j], nr = s_nr[j];
+                            // 1 - alpha >= 1 - alpha_max: the fast division keeps
+                            // ~2 ulp per step over a chain of at most one segment
                             const float om = 1.f - alpha;
-                            const float Tk = T / om;
+                            const float Tk = __fdividef(T, om);
                             const float w = alpha * Tk;
                             const float f = up[0] * cz.x + up[1] * cz.y + up[2] * cz.z + up[3] * nr.x +
                                             up[4] * nr.y + up[5] * nr.z + up[6] * cz.w;
-                            const float dal = Tk * f - acc / om;
+                            const float dal = Tk * f - __fdividef(acc, om);
                             acc = fmaf(w, f, acc);
                             T = Tk;
                             q[QR] = w * up[0];
