@@ -444,8 +444,9 @@ p2e_status p2e_point_raster(const float *xyz, const float *rgb, int64_t n, const
  * probe = NULL.  This is the one piece of state the library keeps between
  * calls (thread-local, host memory only); with no probe set nothing is
  * recorded.
- *   kernel   P2E_PROBE_KNN       the kNN-PCA kernel of p2e_estimate (its
- *                                fast path; the few listed queries run after it)
+ *   kernel   P2E_PROBE_KNN       the kNN search of p2e_estimate (its fast
+ *                                path: the counting and selection kernels;
+ *                                the few listed queries and the PCA run after)
  *            P2E_PROBE_BLEND     the compositing kernel of p2e_render
  *            P2E_PROBE_MLP       the learned head of p2e_estimate (mode 1)
  *            P2E_PROBE_BLEND_BWD the per-tile kernel of p2e_render_backward

@@ -9,18 +9,19 @@
 //   grid      uniform cells (about two cells per point at most), counting
 //             sort of the points by cell (count, scan, scatter into a
 //             cell-ordered copy)
-//   knn+pca   one thread per point, points taken in cell order (a
+//   knn       one thread per point, points taken in cell order (a
 //             cell-ordered copy of the points): exact 16 nearest other
 //             points (ties by index) by a two-pass threshold search of the
-//             3x3x3 cell block (count within trial radii, then buffer and
-//             select); the few queries that block cannot certify go to a
-//             second kernel, one warp per query over the 5x5x5 block (ring
-//             search beyond it); then the neighbours' covariance, a cyclic Jacobi
-//             eigen-decomposition, scale = sqrt(lambda) (smallest axis at
-//             least 0.1 of the middle one), rotation in a canonical frame
-//             (normal = smallest axis turned away from the centroid, first
-//             axis with its largest component positive, e2 = e3 x e1) ->
-//             quaternion (Shepperd).
+//             3x3x3 cell block (a counting kernel finds the trial radius, a
+//             second kernel buffers and selects); the few queries that block
+//             cannot certify go to a third kernel, one warp per query over
+//             the 5x5x5 block (ring search beyond it)
+//   pca       one thread per point in index order: the neighbours'
+//             covariance, a cyclic Jacobi eigen-decomposition, scale =
+//             sqrt(lambda) (smallest axis at least 0.1 of the middle one),
+//             rotation in a canonical frame (normal = smallest axis turned
+//             away from the centroid, first axis with its largest component
+//             positive, e2 = e3 x e1) -> quaternion (Shepperd).
 #include <string.h>
 
 #include <algorithm>
@@ -537,70 +538,79 @@ __device__ __forceinline__ float dist2(const float4 &a, const float4 &p) {
     return fmaf(ex, ex, fmaf(ey, ey, ez * ez));
 }
 
-// Fast path, one thread per query point (points taken in cell order).
-// Exact 16 nearest other points, ties by index:
-//   pass 1  count the candidates within five trial radii (0.40 .. 0.75 cell
-//           sizes, branch free, on the FMA pipe) over only the cells of the
-//           3x3x3 block that the largest ball can reach, and pick the
-//           smallest radius T that holds 16 others (and at most kBuf);
-//   pass 2  keep the candidates within T (the cells that ball reaches) in
-//           shared memory as (distance bits, index) keys, check their count
-//           and select the 16 smallest keys.
+// Trial radii of the fast path, squared: (0.40 + 0.0875 k) cell sizes,
+// shrunk by a relative 1e-4 and 1e-6 so that a radius never reaches a cell
+// the block walk culls.
+__device__ __forceinline__ float trial_r2(const GridParams &g, int k) {
+    const float rr = (0.40f + 0.0875f * k) * g.h * (1.f - 1e-4f) - 1e-6f;
+    return rr * rr;
+}
+
+// Fast path, one thread per query point (points taken in cell order), in
+// two kernels.  Exact 16 nearest other points, ties by index:
+//   knn_count_kernel  pass 1: count the candidates within five trial radii
+//                     (0.40 .. 0.75 cell sizes, branch free, on the FMA
+//                     pipe) over only the cells of the 3x3x3 block that the
+//                     largest ball can reach, and record the smallest
+//                     squared radius T that holds 16 others (and at most
+//                     kBuf), or -1;
+//   knn_pca_kernel    pass 2: keep the candidates within T (the cells that
+//                     ball reaches) in shared memory as (distance bits,
+//                     index) keys, check their count and select the 16
+//                     smallest keys; then the PCA.
+// The counting pass needs neither the candidate buffer nor most of the
+// registers, so as a kernel of its own it runs at twice the resident warps
+// with all of L1 for the cell walk.  T goes through the cell-count array,
+// which the scatter has run down to zero and which holds at least n words.
 // A query for which no trial radius qualifies (about 0.5 % of the points of
 // a surface scan: sparse or ragged regions) is appended to a list (S.cell
 // reused, its length in S.ticket[12]) for knn_pca_slow_kernel, so that no
 // warp carries one lane's long search.
-__global__ void __launch_bounds__(kKnnThreads, 6) knn_pca_kernel(const float4 *__restrict__ xyz,
-                                                              const float4 *__restrict__ rgb, int64_t n,
-                                                              float opacity, EstScratch S,
-                                                              uint32_t *__restrict__ knn_out,
-                                                              float4 *__restrict__ mean_op,
-                                                              float4 *__restrict__ scale,
-                                                              float4 *__restrict__ quat,
-                                                              float4 *__restrict__ rgb_out,
-                                                              float4 *__restrict__ normal) {
+__global__ void __launch_bounds__(kKnnThreads, 12) knn_count_kernel(int64_t n, EstScratch S) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const GridParams g = *S.gp;
+    const float4 p = S.spts[t];
+    int c0[3];
+    cell_of(g, p.x, p.y, p.z, c0);
+    // counts kept in fp32 on the FMA pipe: fma(-d, 2^100, r 2^100) is
+    // (r - d) 2^100 rounded once (the scaling is exact): <= 0 when d >= r,
+    // and for d < r at least 2^100 times the fp32 spacing at r, >= 1 for
+    // any r above 2^-76, so the saturated value is 1 exactly when d < r
+    // (pass 2 counts the chosen radius exactly in any case)
+    float rB[kRadA], cf[kRadA];
+#pragma unroll
+    for (int k = 0; k < kRadA; ++k) {
+        rB[k] = trial_r2(g, k) * 0x1p100f;
+        cf[k] = 0.f;
+    }
+    for_block(g, S, c0, p, trial_r2(g, kRadA - 1), [&](const float4 &pj) {
+        const float d = dist2(pj, p);
+#pragma unroll
+        for (int k = 0; k < kRadA; ++k) cf[k] += __saturatef(fmaf(-d, 0x1p100f, rB[k]));
+    });
+    float T = -1.f;
+#pragma unroll
+    for (int k = kRadA - 1; k >= 0; --k)
+        if (cf[k] >= (float)(kK + 1) && cf[k] <= (float)(kBuf + 1)) T = trial_r2(g, k);
+    if (T < 0.f) S.cell[atomicAdd(S.ticket + 12, 1u)] = (uint32_t)t;
+    S.counts[t] = __float_as_uint(T);
+}
+
+__global__ void __launch_bounds__(kKnnThreads, 6) knn_select_kernel(int64_t n, EstScratch S,
+                                                                 uint32_t *__restrict__ knn_out) {
     // candidates as (fp32 distance bits << 32 | index): d >= 0, so the
     // unsigned order of the keys is the order by (distance, index)
     __shared__ uint64_t s_key[kBuf * kKnnThreads];
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
+    const float T = __uint_as_float(S.counts[t]);
+    if (T < 0.f) return;  // listed for the slow kernel by the counting pass
     const GridParams g = *S.gp;
     const float4 p = S.spts[t];
     const uint32_t i = __float_as_uint(p.w);
     int c0[3];
     cell_of(g, p.x, p.y, p.z, c0);
-    float rA[kRadA];
-#pragma unroll
-    for (int k = 0; k < kRadA; ++k) {
-        const float rr = (0.40f + 0.0875f * k) * g.h * (1.f - 1e-4f) - 1e-6f;
-        rA[k] = rr * rr;
-    }
-    float T = -1.f;
-    {
-        // counts kept in fp32 on the FMA pipe: fma(-d, 2^100, r 2^100) is
-        // (r - d) 2^100 rounded once (the scaling is exact): <= 0 when
-        // d >= r, and for d < r at least 2^100 times the fp32 spacing at r,
-        // >= 1 for any r above 2^-76, so the saturated value is 1 exactly when
-        // d < r (pass 2 counts the chosen radius exactly in any case)
-        float rB[kRadA], cf[kRadA];
-#pragma unroll
-        for (int k = 0; k < kRadA; ++k) {
-            rB[k] = rA[k] * 0x1p100f;
-            cf[k] = 0.f;
-        }
-        for_block(g, S, c0, p, rA[kRadA - 1], [&](const float4 &pj) {
-            const float d = dist2(pj, p);
-#pragma unroll
-            for (int k = 0; k < kRadA; ++k) cf[k] += __saturatef(fmaf(-d, 0x1p100f, rB[k]));
-        });
-#pragma unroll
-        for (int k = kRadA - 1; k >= 0; --k)
-            if (cf[k] >= (float)(kK + 1) && cf[k] <= (float)(kBuf + 1)) T = rA[k];
-    }
-    if (T < 0.f) {
-        S.cell[atomicAdd(S.ticket + 12, 1u)] = (uint32_t)t;
-        return;
-    }
     uint64_t *bk = s_key + threadIdx.x;
     int m = 0;  // candidates inside T (kept: the first kBuf)
     for_block(g, S, c0, p, T, [&](const float4 &pj) {
@@ -627,11 +637,43 @@ __global__ void __launch_bounds__(kKnnThreads, 6) knn_pca_kernel(const float4 *_
         bk[best_k * kKnnThreads] = bk[a * kKnnThreads];
         bk[a * kKnnThreads] = kbst;
     }
-    pca_out(g, p, i, opacity, [&](int k) {
-        const uint32_t j = (uint32_t)bk[k * kKnnThreads];
+    // the query's 16 neighbours, nearest first: one 64-byte row (16-byte
+    // aligned stores) of the original index's list
+    uint4 *row = reinterpret_cast<uint4 *>(knn_out + (int64_t)i * kK);
+#pragma unroll
+    for (int k = 0; k < kK / 4; ++k)
+        row[k] = make_uint4((uint32_t)bk[(4 * k) * kKnnThreads], (uint32_t)bk[(4 * k + 1) * kKnnThreads],
+                            (uint32_t)bk[(4 * k + 2) * kKnnThreads], (uint32_t)bk[(4 * k + 3) * kKnnThreads]);
+}
+
+// The neighbours' covariance, eigen-decomposition and canonical frame of
+// every point, taken in the order of the original indices so that the
+// Gaussians are written as whole 32-byte sectors (in cell order they were
+// half-sector writes scattered over the outputs, which HBM3e, having no
+// write mask, fills by reading each sector first); the neighbours come from
+// the lists the selection kernels wrote.
+__global__ void __launch_bounds__(256, 4) pca_kernel(const float4 *__restrict__ xyz, const float4 *__restrict__ rgb,
+                                                  int64_t n, float opacity, EstScratch S,
+                                                  const uint32_t *__restrict__ knn,
+                                                  float4 *__restrict__ mean_op, float4 *__restrict__ scale,
+                                                  float4 *__restrict__ quat, float4 *__restrict__ rgb_out,
+                                                  float4 *__restrict__ normal) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const GridParams g = *S.gp;
+    const float4 p = __ldg(xyz + i);
+    uint32_t nb[kK];
+    const uint4 *row = reinterpret_cast<const uint4 *>(knn + i * kK);
+#pragma unroll
+    for (int k = 0; k < kK / 4; ++k) {
+        const uint4 r = __ldg(row + k);
+        nb[4 * k] = r.x; nb[4 * k + 1] = r.y; nb[4 * k + 2] = r.z; nb[4 * k + 3] = r.w;
+    }
+    pca_out(g, p, (uint32_t)i, opacity, [&](int k) {
+        const uint32_t j = nb[k];
         const float4 q = __ldg(xyz + j);
         return make_float4(q.x, q.y, q.z, __uint_as_float(j));
-    }, rgb, knn_out, mean_op, scale, quat, rgb_out, normal);
+    }, rgb, nullptr, mean_op, scale, quat, rgb_out, normal);
 }
 
 constexpr int kSlowWarps = 4;   // one query per warp at a time
@@ -650,16 +692,8 @@ constexpr int kLad = 16;        // trial radii 0.40 .. 2.00 cell sizes (ratio ~1
 // Where no radius qualifies (fewer than 16 others within two cell sizes,
 // or many points at one distance), lane 0 searches rings of cells around
 // the query's cell until the 16th distance is below the distance to the
-// next ring.  Lane 0 computes the PCA and writes the outputs.
-__global__ void __launch_bounds__(kSlowWarps * 32) knn_pca_slow_kernel(const float4 *__restrict__ xyz,
-                                                                       const float4 *__restrict__ rgb,
-                                                                       float opacity, EstScratch S,
-                                                                       uint32_t *__restrict__ knn_out,
-                                                                       float4 *__restrict__ mean_op,
-                                                                       float4 *__restrict__ scale,
-                                                                       float4 *__restrict__ quat,
-                                                                       float4 *__restrict__ rgb_out,
-                                                                       float4 *__restrict__ normal) {
+// next ring.  The warp writes the query's neighbour list.
+__global__ void __launch_bounds__(kSlowWarps * 32) knn_slow_kernel(EstScratch S, uint32_t *__restrict__ knn_out) {
     __shared__ float s_d[kSlowWarps][kSlowBuf];
     __shared__ uint32_t s_j[kSlowWarps][kSlowBuf];
     __shared__ uint32_t s_nb[kSlowWarps][kK];
@@ -793,12 +827,7 @@ __global__ void __launch_bounds__(kSlowWarps * 32) knn_pca_slow_kernel(const flo
             for (int k = 0; k < kK; ++k) s_nb[w][k] = best.J(k);
         }
         __syncwarp();
-        if (lane == 0)
-            pca_out(g, p, i, opacity, [&](int k) {
-                const uint32_t j = s_nb[w][k];
-                const float4 q = __ldg(xyz + j);
-                return make_float4(q.x, q.y, q.z, __uint_as_float(j));
-            }, rgb, knn_out, mean_op, scale, quat, rgb_out, normal);
+        if (lane < kK) knn_out[(int64_t)i * kK + lane] = s_nb[w][lane];
         __syncwarp();
     }
 }
@@ -839,14 +868,15 @@ cudaError_t launch_estimate(const float *xyz, const float *rgb, int64_t n, int32
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     uint32_t *knn = knn_idx ? knn_idx : S.knn;
     const p2e_kernel_probe *pr = kernel_probe(P2E_PROBE_KNN);
+    const unsigned kgrid = (unsigned)((n + kKnnThreads - 1) / kKnnThreads);
     probe_start(pr, st);
-    knn_pca_kernel<<<(unsigned)((n + kKnnThreads - 1) / kKnnThreads), kKnnThreads, 0, st>>>(
-        (const float4 *)xyz, (const float4 *)rgb, n, pca_opacity, S, knn, (float4 *)out->mean_op,
-        (float4 *)out->scale, (float4 *)out->quat, (float4 *)out->rgb, (float4 *)out->normal);
+    knn_count_kernel<<<kgrid, kKnnThreads, 0, st>>>(n, S);
+    knn_select_kernel<<<kgrid, kKnnThreads, 0, st>>>(n, S, knn);
     probe_stop(pr, st);
     // the listed queries, one warp each (their number is on the device)
-    knn_pca_slow_kernel<<<num_sms * 8, kSlowWarps * 32, 0, st>>>(
-        (const float4 *)xyz, (const float4 *)rgb, pca_opacity, S, knn, (float4 *)out->mean_op,
+    knn_slow_kernel<<<num_sms * 8, kSlowWarps * 32, 0, st>>>(S, knn);
+    pca_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        (const float4 *)xyz, (const float4 *)rgb, n, pca_opacity, S, knn, (float4 *)out->mean_op,
         (float4 *)out->scale, (float4 *)out->quat, (float4 *)out->rgb, (float4 *)out->normal);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (mode == 1) return launch_mlp_estimate(S.pk, n, mlp, knn, out, (int32_t *)(S.ticket + 9), num_sms, st);
