@@ -99,7 +99,7 @@ _CSRC = "paper_2409_16504_gb300/csrc/"
 NCU_TRAFFIC = {
     # the kNN search's two launches per frame (counting, selection), summed
     "knn": {"kernel": "knn_count_kernel + knn_select_kernel", "sources": [_CSRC + "estimate.cu"],
-            "sha256_16": "c2e78871165733e6", "bytes": 32_422_000},
+            "sha256_16": "c39e882389eab2c2", "bytes": 32_422_000},
     "blend": {"kernel": "blend_kernel<8>", "tile": 8, "sources": [_CSRC + "blend.cu", _CSRC + "splat.cuh"],
               "sha256_16": "ae1d3d0a5411ef65", "bytes": 373_008_000},
     "mlp": {"kernel": "mlp_estimate_kernel", "sources": [_CSRC + "mlp.cu", _CSRC + "tcgen05.cuh"],

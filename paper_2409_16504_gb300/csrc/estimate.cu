@@ -554,18 +554,19 @@ __device__ __forceinline__ float trial_r2(const GridParams &g, int k) {
 //                     largest ball can reach, and record the smallest
 //                     squared radius T that holds 16 others (and at most
 //                     kBuf), or -1;
-//   knn_pca_kernel    pass 2: keep the candidates within T (the cells that
+//   knn_select_kernel pass 2: keep the candidates within T (the cells that
 //                     ball reaches) in shared memory as (distance bits,
-//                     index) keys, check their count and select the 16
-//                     smallest keys; then the PCA.
+//                     index) keys, check their count, select the 16
+//                     smallest keys and write them as the query's list
+//                     (pca_kernel computes the frames from the lists).
 // The counting pass needs neither the candidate buffer nor most of the
 // registers, so as a kernel of its own it runs at twice the resident warps
 // with all of L1 for the cell walk.  T goes through the cell-count array,
 // which the scatter has run down to zero and which holds at least n words.
 // A query for which no trial radius qualifies (about 0.5 % of the points of
 // a surface scan: sparse or ragged regions) is appended to a list (S.cell
-// reused, its length in S.ticket[12]) for knn_pca_slow_kernel, so that no
-// warp carries one lane's long search.
+// reused, its length in S.ticket[12]) for knn_slow_kernel, so that no warp
+// carries one lane's long search.
 __global__ void __launch_bounds__(kKnnThreads, 12) knn_count_kernel(int64_t n, EstScratch S) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
