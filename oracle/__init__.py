@@ -18,6 +18,8 @@ What each function follows (paper sections of arXiv 2409.16504):
   covariance prior of Sec. 2.1) and the per-point MLP reference
 * :mod:`oracle.raycast` -- exact ground-truth views of the analytic scenes
   (replaces the mesh rasterisation of Sec. 3.3)
+* :mod:`oracle.loss`    -- the training loss of Eq. 5 (Sec. 3.3) and its
+  gradient; :mod:`oracle.ssim` the SSIM term added to it
 """
 from __future__ import annotations
 

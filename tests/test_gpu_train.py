@@ -1,7 +1,7 @@
 """Training kernels of the learned estimator on the GPU.
 
-* p2e_loss_eq5 against Eq. 5 written out in numpy (FP64): loss and its
-  gradient within 1e-5 (fp32 sums over ~10^4 pixels).
+* p2e_loss_eq5 against the oracle's FP64 Eq. 5 (oracle/loss.py): loss and
+  its gradient within 1e-5 (fp32 sums over ~10^4 pixels).
 * p2e_mlp_backward (tcgen05: bf16 operands, fp32 accumulation) against the
   oracle's FP64 gradient with the forward's bf16 roundings held fixed, per
   parameter tensor: |gpu - oracle|_F <= 2e-2 |oracle|_F and, element by
@@ -28,32 +28,13 @@ import torch
 
 import oracle
 import oracle.mlp as om
+from oracle import loss as oracle_loss
 import scenes
 
 pytestmark = pytest.mark.gpu
 
 
-def _np_loss(rgb, nrm, grgb, gnrm, w=(1.0, 10.0, 0.1)):
-    w1, w2, w3 = w
-    N = rgb.shape[1]
-    d = rgb - grgb
-    c = np.cross(gnrm.T, nrm.T).T
-    cn = np.linalg.norm(c, axis=0)
-    nm = np.linalg.norm(nrm - gnrm, axis=0)
-    npl = np.linalg.norm(nrm + gnrm, axis=0)
-    minus = nm <= npl
-    loss = w1 * np.abs(d).mean() + w2 * (cn + w3 * np.where(minus, nm, npl)).mean()
-    g_rgb = w1 * np.sign(d) / (3 * N)
-    with np.errstate(invalid="ignore", divide="ignore"):
-        gc = np.where(cn > 0, np.cross(c.T, gnrm.T).T / cn, 0.0)
-        dd = np.where(minus, nrm - gnrm, nrm + gnrm)
-        dn = np.where(minus, nm, npl)
-        gm = np.where(dn > 0, dd / dn, 0.0)
-    g_n = w2 * (gc + w3 * gm) / N
-    return loss, g_rgb, g_n
-
-
-def test_loss_eq5_matches_numpy():
+def test_loss_eq5_matches_oracle():
     from paper_2409_16504_gb300 import _lib
     from paper_2409_16504_gb300.render import _ptr, _stream
     rng = np.random.default_rng(0)
@@ -79,7 +60,7 @@ def test_loss_eq5_matches_numpy():
     torch.cuda.synchronize()
     f32 = lambda k: [p.astype(np.float32).astype(np.float64) for p in planes[k]]  # noqa: E731
     cat = lambda k: np.concatenate(f32(k), axis=1)  # noqa: E731
-    ref, g_rgb, g_n = _np_loss(cat("rgb"), cat("nrm"), cat("grgb"), cat("gnrm"))
+    ref, g_rgb, g_n = oracle_loss.eq5(cat("rgb"), cat("nrm"), cat("grgb"), cat("gnrm"), w=(1.0, 10.0, 0.1))
     np.testing.assert_allclose(loss.item(), ref, rtol=1e-5)
     # planar per view -> channel-major per view, as the kernel writes it
     got_rgb = np.concatenate([d_rgb.cpu().numpy()[:3 * 37 * 29].reshape(3, -1),
