@@ -307,8 +307,9 @@ p2e_status p2e_render_backward(const p2e_gaussians *g, const p2e_projected *proj
  * c_j - c_i (R the canonical PCA frame, r_i the 16th-neighbour distance).
  * Outputs y[0..7] correct the PCA estimate in its frame:
  * s = s_pca exp(clip(y0..2, -4, 4)), q = q_pca (x) normalize(1 + y3, y4, y5, y6),
- * o = sigmoid(logit(pca_opacity) + y7), normal = third axis of R(q).  out: device Gaussian set (mean_op, scale, quat, rgb, normal) of n
- * entries (the const qualifiers of p2e_gaussians are cast away for output).
+ * o = sigmoid(logit(pca_opacity) + y7), normal = third axis of R(q).
+ * out: device Gaussian set (mean_op, scale, quat, rgb, normal) of n entries
+ * (the const qualifiers of p2e_gaussians are cast away for output).
  * knn_idx (optional, may be NULL): device uint32[n*16] neighbour indices,
  * 16-byte aligned, row i the 16 nearest other points of point i in
  * ascending distance (ties by index).
