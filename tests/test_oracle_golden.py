@@ -82,3 +82,20 @@ def test_eq3_projected_covariance(case):
     np.testing.assert_allclose(p["conic"][0], conic, rtol=1e-12, atol=1e-15)
     np.testing.assert_allclose(p["uv"][0], uv, rtol=0, atol=1e-12)
     assert p["xyz"][0].tolist() == gw[0:3]
+
+
+def test_knn_pca_square_grid():
+    """Sec. 2.1 prior (k = 16 kNN-PCA): a query amid 16 plane points at four
+    distances, ties in index order, covariance diag(1.875, 1.875, 0)."""
+    rows = _rows("knn_pca_square_grid.txt")
+    pts = sorted((int(r[1]), [_num(x) for x in r[2:5]]) for r in rows if r[0] == "point")
+    xyz = np.array([p for _, p in pts], np.float32)
+    exp = {r[0]: [_num(x) for x in r[1:]] for r in rows if r[0] != "point"}
+    q = int(exp["query"][0])
+    idx, d2 = oracle.knn(xyz)
+    assert idx[q].tolist() == [int(v) for v in exp["neighbours"]]
+    assert d2[q].tolist() == exp["d2"]
+    e = oracle.pca(xyz, idx)
+    np.testing.assert_allclose(e["lam"][q], exp["lambda"], rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(e["scale"][q], exp["scale"], rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(e["normal"][q], exp["normal"], atol=1e-14)
